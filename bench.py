@@ -1,0 +1,333 @@
+"""Benchmark: throughput of log I_v(x) and log K_v(x) on the paper-shaped sweep.
+
+Workload (one step): for each order v in {2^0, ..., 2^10}, 20M arguments
+x ~ U[1, 100] (float64), evaluated with one call per order (scalar v) and
+once more as a single mixed-order call over all 220M pairs (orders drawn at
+random per pair); both log I and log K.  880M evaluations per step, all
+through the C ABI in include/logbessel.h.  Inputs are generated on the GPU
+(seeded Philox) and stay resident; every call streams >= 160 MB of inputs,
+above the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  --impl reference times the extended-precision
+CPU oracle on the host cores instead (the only reference implementation of
+this method available here).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Gevals/s (log I_v and log K_v, FP64)"
+UNIT = "Gevals/s"
+WORKLOAD = "paper-shaped sweep: v=2^0..2^10 x 20M x~U[1,100] per order, log I + log K, per-order + mixed-order calls"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(n_per_v, seed):
+    from paper_2409_08729_gb300.workloads import sweep_pairs
+    v, x = sweep_pairs(n_per_v, seed=seed)
+    return v, x
+
+
+def time_oracle(n_per_v, seed=7):
+    """Oracle throughput (evals/s) over log I and log K on a sample of the sweep."""
+    import oracle
+    v, x = oracle_sample(n_per_v, seed)
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    oracle.log_i(v, x, threads=threads)
+    oracle.log_k(v, x, threads=threads)
+    dt = time.perf_counter() - t0
+    return 2 * v.size / dt, threads, v.size
+
+
+def reference_arm(args, rank, world):
+    """The oracle on the host cores, same metric and workload shape, bounded samples."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    per_v = args.ref_per_v
+    for _ in range(args.warmup):
+        time_oracle(max(per_v // 10, 10), seed=1)
+    rates = []
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        r, threads, n = time_oracle(per_v, seed=100 + s)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = 2 * per_v * 11 * args.steps / wall / 1e9
+    sample = "%d pairs per step (%d per order, log I + log K), drawn from the sweep" % (11 * per_v, per_v)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": 22 * per_v},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-per-v", type=int, default=20_000_000)
+    ap.add_argument("--mode", default="tight", choices=["tight", "paper_gpu"])
+    ap.add_argument("--cpu-per-v", type=int, default=20000, help="oracle sample per order for cpu_baseline")
+    ap.add_argument("--ref-per-v", type=int, default=4000, help="oracle sample per order per reference step")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import paper_2409_08729_gb300 as lb
+    from paper_2409_08729_gb300 import _binding as B
+    from paper_2409_08729_gb300 import workmodel as WM
+    from paper_2409_08729_gb300.workloads import SWEEP_ORDERS, sweep_device
+    lb.build_library()
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    L = B.lib()
+    mode = B.MODES[args.mode]
+    nv = len(SWEEP_ORDERS)
+    n1 = args.n_per_v
+    n_all = n1 * nv
+    x_all, v_mixed = sweep_device(n1, seed=1234 + rank, device=dev)
+    orders = torch.tensor(SWEEP_ORDERS, dtype=torch.float64, device=dev)
+    outs = torch.empty((4, n_all), dtype=torch.float64, device=dev)   # I per-order, I mixed, K per-order, K mixed
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def step(xa, vm, ob):
+        for kind, fn in ((0, L.logbessel_i), (1, L.logbessel_k)):
+            o_per, o_mix = ob[2 * kind], ob[2 * kind + 1]
+            for k in range(nv):
+                B.check(fn(B.LB_F64, orders[k:k + 1].data_ptr(), 0, xa[k * n1:(k + 1) * n1].data_ptr(),
+                           o_per[k * n1:(k + 1) * n1].data_ptr(), n1, mode, sp))
+            B.check(fn(B.LB_F64, vm.data_ptr(), 1, xa.data_ptr(), o_mix.data_ptr(), n_all, mode, sp))
+
+    evals_per_step = 4 * n_all
+
+    # FP64 roofline of this GPU, measured live
+    rates = B.measure_fp64(sp)
+
+    for _ in range(args.warmup):
+        step(x_all, v_mixed, outs)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs ----
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    B.profile_enable(True)
+    launches0 = B.launch_count()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(x_all, v_mixed, outs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = B.launch_count() - launches0
+    prof = B.profile_read()
+    B.profile_enable(False)
+    clocks = sampler.stop()
+    if pg:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = evals_per_step * args.steps * world / (ms / 1e3) / 1e9
+
+    # ---- end to end: pinned host inputs -> device -> host results, each step ----
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty(n_all, dtype=torch.float64, pin_memory=True)
+        hv = torch.empty(n_all, dtype=torch.float64, pin_memory=True)
+        hx.copy_(x_all)
+        hv.copy_(v_mixed)
+        ho = torch.empty((4, n_all), dtype=torch.float64, pin_memory=True)
+        dx = torch.empty_like(x_all)
+        dv = torch.empty_like(v_mixed)
+        # one untimed pass
+        dx.copy_(hx, non_blocking=True); dv.copy_(hv, non_blocking=True); step(dx, dv, outs)
+        ho.copy_(outs, non_blocking=True)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            dx.copy_(hx, non_blocking=True)
+            dv.copy_(hv, non_blocking=True)
+            step(dx, dv, outs)
+            ho.copy_(outs, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1)
+        if pg:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": evals_per_step * args.steps * world / (ems / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * n_all * 8, "d2h_bytes_per_step": 4 * n_all * 8}
+        del hx, hv, ho, dx, dv
+
+    # ---- roofline of the dominant kernel (FP64 pipe) ----
+    regions_k = lb.classify("k", v_mixed, x_all).cpu().numpy()
+    regions_i = lb.classify("i", v_mixed, x_all).cpu().numpy()
+    vm_h = v_mixed.cpu().numpy()
+    x_h = x_all.cpu().numpy()
+    per_order_k = np.repeat(np.asarray(SWEEP_ORDERS), n1)
+    peak_flops = 2.0 * rates["dfma"]
+    dominant = max(prof.items(), key=lambda kv: kv[1][2])
+    name, (nl, ntimed, kms) = dominant
+    roof = None
+    # algorithmic work of each kernel over the timed region (one step, then x steps)
+    per_order_t = orders.repeat_interleave(n1)
+    fb_mix = regions_k == 2
+    fb_per = lb.classify("k", per_order_t, x_all).cpu().numpy() == 2
+    ri_per = lb.classify("i", per_order_t, x_all).cpu().numpy()
+    rk_per = lb.classify("k", per_order_t, x_all).cpu().numpy()
+    del per_order_t
+    kint_slots = (WM.kint_slots(vm_h[fb_mix], x_h[fb_mix]).sum()
+                  + WM.kint_slots(per_order_k[fb_per], x_h[fb_per]).sum())
+    tiles_slots = 0.0
+    for regs, vv in ((regions_i, vm_h), (ri_per, per_order_k)):
+        tiles_slots += np.count_nonzero(regs == 0) * WM.mu20_slots() + np.count_nonzero(regs == 1) * WM.u13_slots()
+        sel = np.flatnonzero(regs == 2)
+        if sel.size:
+            sub = sel[np.random.default_rng(0).integers(0, sel.size, min(sel.size, 1_000_000))]
+            tiles_slots += WM.series_slots(vv[sub], x_h[sub]).mean() * sel.size
+    for regs in (regions_k, rk_per):
+        tiles_slots += np.count_nonzero(regs == 0) * WM.mu20_slots() + np.count_nonzero(regs == 1) * WM.u13_slots()
+    work_slots = {"lb_kint_kernel": kint_slots, "lb_tiles_kernel": tiles_slots}
+    if name in work_slots:
+        work = 2.0 * work_slots[name] * args.steps
+        roof = {"bound": "alu", "kernel": name, "achieved": work / (kms / 1e3) / 1e9,
+                "peak": peak_flops / 1e9, "unit": "GFLOP/s", "frac": (work / (kms / 1e3)) / peak_flops,
+                "traffic": None, "launches": nl, "avg_launch_ms": kms / max(ntimed, 1),
+                "peak_source": "FP64 DFMA rate measured live by logbessel_measure_fp64 (x2 flops/FMA)"}
+    other = {k: {"achieved_gflops": 2.0 * w * args.steps / (prof[k][2] / 1e3) / 1e9 if prof.get(k, (0, 0, 0))[2] else None}
+             for k, w in work_slots.items()}
+    mix = {}
+    for nm, rid in (("mu20", 0), ("u13", 1), ("fallback", 2)):
+        mix[nm] = {"i": float(np.mean(regions_i == rid)), "k": float(np.mean(regions_k == rid))}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "evals_per_step": evals_per_step, "n_per_order": n1,
+                       "mode": args.mode, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (>=160 MB per call), no flush"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+            "kernels": {k: {"launches": v[0], "ms": v[2], **other.get(k, {})} for k, v in prof.items()},
+            "region_mix_mixed_call": mix,
+            "fp64_rates": {k: v / 1e9 for k, v in rates.items()}}
+    if rank == 0:
+        r, threads, n = time_oracle(args.cpu_per_v)
+        line["cpu_baseline"] = {"value": r / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "%d pairs of the sweep (%d per order), log I + log K" % (n, args.cpu_per_v)}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

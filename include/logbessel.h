@@ -1,0 +1,182 @@
+/*
+ * logbessel.h -- C ABI of the GB300 log-Bessel library.
+ *
+ * Batched, overflow-free evaluation of log I_v(x) and log K_v(x), the
+ * logarithms of the modified Bessel functions of the first and second kind,
+ * over many (order v, argument x) pairs, with the region-dispatched log-scale
+ * algorithms of Plesner, Sorensen and Hauberg, "Accurate Computation of the
+ * Logarithm of Modified Bessel Functions on GPUs" (ICS 2024, arXiv 2409.08729).
+ *
+ * Conventions shared by every entry point:
+ *   - v, x and out are DEVICE pointers owned by the caller (for example the
+ *     data pointers of CUDA tensors).  They must be valid on the current
+ *     device for the duration of the enqueued work.  Element i reads
+ *     v[i * v_stride] and x[i] and writes out[i]; out must not alias v or x
+ *     unless it is exactly equal to x (element-wise in place is allowed).
+ *   - v_stride is 1 (one order per pair) or 0 (one order for all pairs).
+ *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     only enqueue work on that stream; they never synchronize.  Temporary
+ *     device memory comes from the stream-ordered allocator
+ *     (cudaMallocAsync) on that stream and is released on it.
+ *   - n == 0 returns LB_OK without launching anything.  n < 0, a NULL pointer
+ *     with n > 0, a v_stride other than 0/1, or an unknown dtype/mode returns
+ *     LB_EINVAL and enqueues nothing.  Launch failures return LB_ECUDA.  The
+ *     message of the last failure on the calling thread is available from
+ *     logbessel_last_error().
+ *   - Per-element domain results (never a status): see logbessel_i and
+ *     logbessel_k.  NaN in gives NaN out.
+ */
+#ifndef LOGBESSEL_H
+#define LOGBESSEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LB_OK = 0,
+  LB_EINVAL = 1,   /* bad argument; nothing was enqueued                     */
+  LB_ECUDA = 2,    /* a CUDA call or kernel launch failed                    */
+  LB_ENOMEM = 3,   /* temporary device memory could not be obtained          */
+  LB_ETIMEOUT = 4, /* a bounded device-side wait gave up (serving loop)      */
+  LB_ENOTSUP = 5   /* valid request that this build does not implement       */
+} lb_status;
+
+typedef enum {
+  LB_F64 = 0,      /* v, x, out are double                                   */
+  LB_F32 = 1       /* v, x, out are float (FP32-mixed evaluation)            */
+} lb_dtype;
+
+typedef enum {
+  /* Default.  The paper's GPU expressions (mu_20, U_13, power series or
+   * integral) with region thresholds moved so that the truncation error of
+   * each expression stays below 3e-16 of the error scale, and Gauss
+   * quadrature in place of Simpson's rule for the K integral. */
+  LB_TIGHT = 0,
+  /* The paper's GPU algorithm as printed: Algorithm 1 without the mu_3, U_4,
+   * U_6, U_9 branches (Sec. 4.3), Table "input ranges" thresholds, composite
+   * Simpson with N = 600 and the heuristic maxima for the K integral
+   * (Sec. 3.2), with the Simpson constant read as 1/(3N). */
+  LB_PAPER_GPU = 1,
+  /* Algorithm 1 in the paper's CPU order (all seven branches). */
+  LB_PAPER_CPU_ORDER = 2
+} lb_mode;
+
+/* Region ids written by logbessel_classify (Table "input ranges"). */
+typedef enum {
+  LB_R_MU20 = 0,      /* large-argument expansion, 20 terms (Eqs. "log Iv mu k", "log Kv mu k") */
+  LB_R_U13 = 1,       /* uniform large-order expansion, 13 terms (Eqs. "log Iv u k", "log Kv u k") */
+  LB_R_FALLBACK = 2,  /* power series for I (Eq. "log Iv"), integral for K (Eq. "log Kv integral") */
+  LB_R_SPECIAL = 3,   /* domain edge: NaN, zero or infinite input, negative order for I */
+  LB_R_MU3 = 4,       /* the remaining expressions of the CPU order */
+  LB_R_U4 = 5,
+  LB_R_U6 = 6,
+  LB_R_U9 = 7
+} lb_region;
+
+/*
+ * log I_v(x), the modified Bessel function of the first kind, for v >= 0,
+ * x >= 0 (paper Sec. 3.1; Algorithm 1).
+ *   v < 0 or x < 0 -> NaN;  x = 0 -> 0 if v = 0, else -inf;
+ *   x = +inf (v finite) -> +inf;  v = +inf (x finite) -> -inf;
+ *   v and x both infinite -> NaN.
+ */
+lb_status logbessel_i(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                      int64_t n, lb_mode mode, void* cuda_stream);
+
+/*
+ * log K_v(x), the modified Bessel function of the second kind, for real v
+ * (K_{-v} = K_v, so |v| is used) and x >= 0 (paper Sec. 3.2; Algorithm 1).
+ *   x < 0 -> NaN;  x = 0 -> +inf;  x = +inf (v finite) -> -inf;
+ *   v = +-inf (x finite, > 0) -> +inf;  v and x both infinite -> NaN.
+ */
+lb_status logbessel_k(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                      int64_t n, lb_mode mode, void* cuda_stream);
+
+/*
+ * d/dx log I_v(x) = I'_v(x) / I_v(x) and d/dx log K_v(x) = K'_v(x) / K_v(x):
+ * the adjoint of logbessel_i / logbessel_k, computed by differentiating each
+ * region's expression term by term with the same dispatch (the paper lists
+ * derivatives as future work, Sec. 7; the integrand derivative of the K
+ * integral is dF/dx = F (2v - 1)/(s + 2x)).  Same arguments as logbessel_i.
+ * Domain edges: x = 0 gives 0 (I, v = 0), +inf (I, v > 0), -inf (K);
+ * x = +inf gives +1 (I) and -1 (K); infinite or NaN order gives NaN.
+ * logbessel_k_dx supports LB_TIGHT only (LB_ENOTSUP otherwise).
+ */
+lb_status logbessel_i_dx(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                         int64_t n, lb_mode mode, void* cuda_stream);
+lb_status logbessel_k_dx(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                         int64_t n, lb_mode mode, void* cuda_stream);
+
+/*
+ * von Mises-Fisher log-normaliser in dimension d (paper Sec. 6.3):
+ *   deriv = 0:  log C_d(k) = (d/2 - 1) log k - (d/2) log(2 pi) - log I_{d/2-1}(k)
+ *   deriv = 1:  d/dk log C_d(k) = (d/2 - 1)/k - I'_{d/2-1}(k) / I_{d/2-1}(k)
+ * for every kappa[i] >= 0 (device array of n doubles), written to out[i].
+ * k = 0 gives the limit lgamma(d/2) - log 2 - (d/2) log pi (deriv: 0);
+ * k < 0 or NaN gives NaN.  d must be finite and >= 2 (LB_EINVAL otherwise).
+ * Uses LB_TIGHT evaluation; dtype must be LB_F64.
+ */
+lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void* out, int64_t n,
+                              int deriv, void* cuda_stream);
+
+/*
+ * Region id of every pair under the dispatch of `mode` (Table "input
+ * ranges"; Algorithm 1 and the GPU subset of Sec. 4.3).  kind = 0 for I,
+ * 1 for K (K classifies |v|).  region_out is a device array of n uint8_t.
+ */
+lb_status logbessel_classify(int kind, lb_dtype dtype, const void* v, int64_t v_stride,
+                             const void* x, uint8_t* region_out, int64_t n, lb_mode mode,
+                             void* cuda_stream);
+
+/*
+ * Evaluate ONE expression for every pair, bypassing the dispatch: region is
+ * an lb_region value (MU20, U13, FALLBACK, or with LB_PAPER_CPU_ORDER also
+ * MU3, U4, U6, U9).  For checking each expression on both sides of a region
+ * boundary.  Domain edges still give the values listed above.  `mode` selects
+ * the quadrature of the K integral (Gauss for LB_TIGHT, Simpson otherwise).
+ */
+lb_status logbessel_eval_region(int kind, lb_dtype dtype, const void* v, int64_t v_stride,
+                                const void* x, void* out, int64_t n, int region, lb_mode mode,
+                                void* cuda_stream);
+
+/*
+ * Kernel accounting (tracing).  Every kernel launch the library makes is
+ * counted; with profiling enabled each launch is also bracketed by two CUDA
+ * events recorded on its stream, and logbessel_profile_get sums the elapsed
+ * times per kernel.  Enabling resets the timers.  logbessel_profile_get waits
+ * for the recorded events (it synchronizes with the timed launches).
+ * slot: 0 = lb_tiles_kernel, 1 = lb_kint_kernel, 2 = lb_classify_kernel,
+ * 3 = small auxiliary kernels (logbessel_profile_slots() gives the count).  *name points to a static
+ * string.  Returns LB_EINVAL for a slot out of range.
+ */
+void logbessel_profile_enable(int on);
+int logbessel_profile_slots(void);
+lb_status logbessel_profile_get(int slot, const char** name, long long* launches,
+                                long long* timed_launches, double* total_ms);
+/* Total kernel launches made by this library in this process. */
+long long logbessel_launch_count(void);
+
+/*
+ * Measure the FP64-pipe roofline of the current GPU (microbenchmarks with
+ * every SM busy; runs about 0.2 s and synchronizes the stream).  rates is a
+ * host array of 6 doubles that receives operations per second for: DFMA,
+ * exp, log, division, sqrt, lgamma (double precision).  Returns LB_EINVAL for
+ * a NULL rates, LB_ENOMEM or LB_ECUDA on failure.
+ */
+lb_status logbessel_measure_fp64(double* rates, void* cuda_stream);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* logbessel_last_error(void);
+
+/* Library version string. */
+const char* logbessel_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOGBESSEL_H */

@@ -37,6 +37,8 @@
  *   K: v -> |v|; x < 0 -> NaN; x = 0 -> +inf; x = +inf -> -inf;
  *      v = +inf (x finite, > 0) -> +inf.
  *   Any NaN input, or v and x both infinite -> NaN.
+ * The I evaluators decline arguments x > 1e8 (NaN): the series would need
+ * more than ~1e5 terms.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread (no fast-math).
  */
@@ -350,9 +352,15 @@ static dd special_k(double v, double x, int* done) {
   return dd_from(0.0);
 }
 
+/* The series needs O(sqrt(x)) terms around its peak; beyond this argument
+ * the oracle declines (returns NaN) rather than run for hours. */
+#define ORACLE_I_XMAX 1e8
+
 static dd oracle_log_i_1(double v, double x) {
   int done; dd s = special_i(v, x, &done);
-  return done ? s : log_i_dd(dd_from(v), x);
+  if (done) return s;
+  if (x > ORACLE_I_XMAX) return dd_from(NAN);
+  return log_i_dd(dd_from(v), x);
 }
 static dd oracle_log_k_1(double v, double x) {
   int done; dd s = special_k(v, x, &done);
@@ -360,7 +368,7 @@ static dd oracle_log_k_1(double v, double x) {
 }
 /* d/dx log I_v = I_{v+1}/I_v + v/x */
 static double oracle_dlog_i_1(double v, double x) {
-  if (isnan(v) || isnan(x) || v < 0.0 || x < 0.0 || isinf(v) || isinf(x)) return NAN;
+  if (isnan(v) || isnan(x) || v < 0.0 || x < 0.0 || isinf(v) || isinf(x) || x > ORACLE_I_XMAX) return NAN;
   if (x == 0.0) return v == 0.0 ? 0.0 : INFINITY;   /* I_v ~ (x/2)^v / Gamma(v+1) */
   dd vv = dd_from(v);
   dd r = dd_exp(dd_sub(log_i_dd(dd_add_d(vv, 1.0), x), log_i_dd(vv, x)));
@@ -381,6 +389,7 @@ static double oracle_dlog_dv_1(int kind, double v, double x) {
   double h = 1e-6 * (fabs(v) > 1.0 ? fabs(v) : 1.0);
   if (!isfinite(v) || !isfinite(x) || x <= 0.0) return NAN;
   if (kind == 0) {
+    if (x > ORACLE_I_XMAX) return NAN;
     if (v < 0.0) return NAN;
     double lo = v - h > 0.0 ? v - h : v, hi = v + h;
     dd f1 = log_i_dd(dd_from(hi), x), f0 = log_i_dd(dd_from(lo), x);
@@ -395,7 +404,7 @@ static double oracle_dlog_dv_1(int kind, double v, double x) {
 }
 /* vMF log-normaliser log C_d(k) = (d/2-1) log k - (d/2) log(2 pi) - log I_{d/2-1}(k) */
 static double oracle_vmf_log_c_1(double d, double kappa) {
-  if (isnan(kappa) || kappa < 0.0 || !(d >= 2.0)) return NAN;
+  if (isnan(kappa) || kappa < 0.0 || !(d >= 2.0) || kappa > ORACLE_I_XMAX) return NAN;
   if (kappa == 0.0) {
     /* limit: I_nu(k) ~ (k/2)^nu / Gamma(nu+1), so log C = -log(2) - (d/2) log(pi) + lgamma(d/2) */
     dd nu1 = dd_from(0.5 * d);

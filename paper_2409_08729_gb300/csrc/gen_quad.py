@@ -1,0 +1,94 @@
+"""Generate the quadrature tables of the K-integral evaluator (needs mpmath).
+
+The paper evaluates log K_v(x) for small inputs from Rothwell's integral
+(paper Sec. 3.2, Eq. "log Kv integral"):
+
+  K_v(x) = sqrt(pi) e^{-x} / (Gamma(v+1/2) (2x)^v) * int_0^inf F(s) ds,
+  F(s) = e^{-s} (s (s + 2x))^{v-1/2},
+
+split at s = 1 into g(u) on [0, 1] (s = u^beta, beta = 2n/(2v+1), n = 8) and
+h(u) on [0, 1] (s = 1/u).  The paper integrates both with composite Simpson,
+N = 600.  These tables hold Gauss rules for the same two pieces instead:
+
+  g piece: Gauss-Legendre in u on [0, 1], 32, 64 or 128 nodes.
+  h piece: Gauss-Legendre in y = log s on [0, log 100] (s in [1, 100]),
+           32 or 48 nodes, for orders v <= 5;
+           Gauss-Laguerre in t = s - 1, 32 nodes, for orders v > 5.
+
+Writes kquad_tables.h beside this file.  Nodes and weights are computed in
+40-digit arithmetic and rounded to double.
+"""
+import os
+import sys
+
+import mpmath as mp
+
+mp.mp.dps = 40
+SMAX = 100
+
+
+def gauss_legendre01(N):
+    xs, ws = [], []
+    for k in range(1, N + 1):
+        x0 = mp.cos(mp.pi * (k - mp.mpf(0.25)) / (N + mp.mpf(0.5)))
+        for _ in range(200):
+            p0, p1 = mp.mpf(1), x0
+            for j in range(2, N + 1):
+                p0, p1 = p1, ((2 * j - 1) * x0 * p1 - (j - 1) * p0) / j
+            dp = N * (x0 * p1 - p0) / (x0 * x0 - 1)
+            dx = p1 / dp
+            x0 -= dx
+            if abs(dx) < mp.mpf(10) ** (-38):
+                break
+        xs.append((1 - x0) / 2)
+        ws.append(1 / ((1 - x0 * x0) * dp * dp))
+    order = sorted(range(N), key=lambda i: xs[i])
+    return [xs[i] for i in order], [ws[i] for i in order]
+
+
+def gauss_laguerre(N):
+    A = mp.matrix(N, N)
+    for k in range(N):
+        A[k, k] = 2 * k + 1
+        if k + 1 < N:
+            A[k, k + 1] = A[k + 1, k] = k + 1
+    E, Q = mp.eigsy(A)
+    pairs = sorted((E[i], Q[0, i] ** 2) for i in range(N))
+    return [p[0] for p in pairs], [p[1] for p in pairs]
+
+
+def arr(name, vals):
+    body = ",\n  ".join(", ".join(repr(float(v)) for v in vals[i:i + 4]) for i in range(0, len(vals), 4))
+    return "static __device__ const double %s[%d] = {\n  %s};\n" % (name, len(vals), body)
+
+
+def main():
+    out = sys.argv[1] if len(sys.argv) > 1 else os.path.join(os.path.dirname(os.path.abspath(__file__)), "kquad_tables.h")
+    parts = ["// Generated by gen_quad.py -- do not edit.",
+             "// Gauss rules for the g and h pieces of the K integral (see gen_quad.py).",
+             "#pragma once", "", "#define LB_KQ_SMAX %d" % SMAX, ""]
+    for N in (32, 64, 128):
+        u, w = gauss_legendre01(N)
+        parts.append("// g piece, Gauss-Legendre on [0,1], %d nodes: log u_j and log w_j" % N)
+        parts.append(arr("lb_kq_g%d_logu" % N, [mp.log(a) for a in u]))
+        parts.append(arr("lb_kq_g%d_logw" % N, [mp.log(a) for a in w]))
+    Y = mp.log(SMAX)
+    for N in (32, 48):
+        y, w = gauss_legendre01(N)
+        ys = [a * Y for a in y]
+        parts.append("// h piece, Gauss-Legendre in y = log s on [0, log %d], %d nodes:" % (SMAX, N))
+        parts.append("// s_j, y_j and log(w_j * log(%d)) + y_j - s_j (weight, Jacobian ds = s dy, e^{-s})" % SMAX)
+        parts.append(arr("lb_kq_hl%d_s" % N, [mp.exp(a) for a in ys]))
+        parts.append(arr("lb_kq_hl%d_y" % N, ys))
+        parts.append(arr("lb_kq_hl%d_c" % N, [mp.log(wj * Y) + yj - mp.exp(yj) for wj, yj in zip(w, ys)]))
+    t, lam = gauss_laguerre(32)
+    parts.append("// h piece, Gauss-Laguerre in t = s - 1, 32 nodes: 1 + t_j, log(1 + t_j), log(lambda_j) - 1")
+    parts.append(arr("lb_kq_hq32_s", [1 + a for a in t]))
+    parts.append(arr("lb_kq_hq32_y", [mp.log(1 + a) for a in t]))
+    parts.append(arr("lb_kq_hq32_c", [mp.log(a) - 1 for a in lam]))
+    with open(out, "w") as f:
+        f.write("\n".join(parts) + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,311 @@
+// lb_expr.cuh -- per-pair expressions of the log-Bessel algorithm (device code).
+//
+// Each function evaluates one of the paper's expressions for one (v, x) pair
+// in double precision:
+//   mu_K  : large-argument expansion (paper Sec. 3.1 Eq. "log Iv mu k",
+//           Sec. 3.2 Eq. "log Kv mu k")
+//   U_K   : uniform large-order expansion (Eqs. "log Iv u k", "log Kv u k")
+//   series: power series of I_v summed in log scale (Eqs. "Iv infinite series",
+//           "ak recurrence", "log Iv")
+// The K integral (Eq. "log Kv integral") is warp-cooperative and lives in
+// lb_kint.cuh.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+template <typename T> __host__ __device__ __forceinline__ T lb_fma(T a, T b, T c);
+template <> __host__ __device__ __forceinline__ double lb_fma<double>(double a, double b, double c) { return fma(a, b, c); }
+template <> __host__ __device__ __forceinline__ float lb_fma<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+#include "debye_uk.h"
+
+namespace lb {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kTwoPi = 6.283185307179586476925286766559005768;
+constexpr double kHalfLogPi = 0.5723649429247000870717136756012478;   // log(pi)/2
+
+enum Kind { KIND_I = 0, KIND_K = 1 };
+enum Region { R_MU20 = 0, R_U13 = 1, R_FALLBACK = 2, R_SPECIAL = 3, R_MU3 = 4, R_U4 = 5, R_U6 = 6, R_U9 = 7 };
+enum Mode { MODE_TIGHT = 0, MODE_PAPER_GPU = 1, MODE_PAPER_CPU = 2 };
+
+// ---------------------------------------------------------------------------
+// Domain edges (shared convention of the library): returns true and sets *r
+// when (v, x) is an edge case; K callers pass |v|.
+// ---------------------------------------------------------------------------
+template <int KIND>
+__device__ __forceinline__ bool special_value(double v, double x, double* r) {
+  if (KIND == KIND_I) {
+    if (isnan(v) || isnan(x) || v < 0.0 || x < 0.0 || (isinf(v) && isinf(x))) { *r = __longlong_as_double(0x7ff8000000000000LL); return true; }
+    if (isinf(x)) { *r = INFINITY; return true; }
+    if (isinf(v)) { *r = -INFINITY; return true; }
+    if (x == 0.0) { *r = (v == 0.0) ? 0.0 : -INFINITY; return true; }
+  } else {
+    if (isnan(v) || isnan(x) || x < 0.0 || (isinf(v) && isinf(x))) { *r = __longlong_as_double(0x7ff8000000000000LL); return true; }
+    if (isinf(x)) { *r = -INFINITY; return true; }
+    if (x == 0.0 || isinf(v)) { *r = INFINITY; return true; }
+  }
+  return false;
+}
+
+// Domain edges of the x-derivatives: d/dx log I_v at x = 0 is 0 for v = 0
+// (I_0 = 1 + x^2/4 + ...) and +inf otherwise (I_v ~ (x/2)^v / Gamma(v+1));
+// d/dx log K_v at x = 0 is -inf; at x = +inf the derivatives tend to +1 (I)
+// and -1 (K); an infinite order gives NaN.
+template <int KIND>
+__device__ __forceinline__ bool special_dx(double v, double x, double* r) {
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  if (isnan(v) || isnan(x) || x < 0.0 || isinf(v)) { *r = qnan; return true; }
+  if (KIND == KIND_I && v < 0.0) { *r = qnan; return true; }
+  if (isinf(x)) { *r = (KIND == KIND_I) ? 1.0 : -1.0; return true; }
+  if (x == 0.0) { *r = (KIND == KIND_I) ? (v == 0.0 ? 0.0 : INFINITY) : -INFINITY; return true; }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Region predicates (paper Table "input ranges", Algorithm 1).
+// ---------------------------------------------------------------------------
+// Paper thresholds as printed.  Comparisons are strict, so a pair exactly on
+// a threshold falls through to the next branch.
+__device__ __forceinline__ bool paper_mu3(double v, double x) {
+  return (x > 1400.0 && v < 3.05) || ((0.6229 * log(x) - 3.2318 > log(v)) && v > 3.1);
+}
+__device__ __forceinline__ bool paper_mu20(double v, double x) {
+  return (x > 30.0 && v < 15.3919) || ((0.5113 * log(x) + 0.7939 > log(v)) && x > 59.6925);
+}
+__device__ __forceinline__ bool paper_u4(double v, double x) { return (x > 274.2377 && v > 0.3) || v > 163.6993; }
+__device__ __forceinline__ bool paper_u6(double v, double x) { return (x > 84.4153 && v > 0.46) || v > 56.9971; }
+__device__ __forceinline__ bool paper_u9(double v, double x) { return (x > 35.9074 && v > 0.6) || v > 20.1534; }
+__device__ __forceinline__ bool paper_u13(double v, double x) { return (x > 19.6931 && v > 0.7) || v > 12.6964; }
+
+// Tight thresholds: the same two expressions, with the regions shrunk until
+// the truncation error of mu_20 and U_13 (measured against an
+// extended-precision reference on both sides of every boundary) is below
+// 3e-16 of the error scale.  The curved mu_20 boundary
+// 0.5113 log x + 0.7939 > log v is replaced by v^2 < 3.24 x, which follows
+// the actual validity limit of the large-argument series (its terms grow like
+// (v^2 / 2x)^k / k!) and needs no logarithm.
+__device__ __forceinline__ bool tight_mu20(double v, double x) {
+  return (x > 30.0 && v < 13.6) || (x > 59.6925 && v * v < 3.24 * x);
+}
+__device__ __forceinline__ bool tight_u13(double v, double x) { return (x > 25.0 && v > 0.7) || v > 16.0; }
+
+__device__ __forceinline__ int classify(double v, double x, int mode) {
+  if (mode == MODE_TIGHT) {
+    if (tight_mu20(v, x)) return R_MU20;
+    if (tight_u13(v, x)) return R_U13;
+    return R_FALLBACK;
+  }
+  if (mode == MODE_PAPER_CPU) {
+    if (paper_mu3(v, x)) return R_MU3;
+    if (paper_mu20(v, x)) return R_MU20;
+    if (paper_u4(v, x)) return R_U4;
+    if (paper_u6(v, x)) return R_U6;
+    if (paper_u9(v, x)) return R_U9;
+    if (paper_u13(v, x)) return R_U13;
+    return R_FALLBACK;
+  }
+  if (paper_mu20(v, x)) return R_MU20;
+  if (paper_u13(v, x)) return R_U13;
+  return R_FALLBACK;
+}
+
+// ---------------------------------------------------------------------------
+// mu_K expression (K terms after the leading 1):
+//   S = 1 + sum_{k=1}^{K} s^k prod_{j<=k} (mu - (2j-1)^2) / (k! (8x)^k),  mu = 4v^2
+//   log I = x - log(2 pi x)/2 + log|S|          (s = -1)
+//   log K = log(pi / (2x))/2 - x + log|S|       (s = +1)
+// S is formed by Horner's rule on the term ratios
+//   r_k = (mu - (2k-1)^2) / (8 x k),  S = 1 + s r_1 (1 + s r_2 (1 + ... (1 + s r_K))).
+// ---------------------------------------------------------------------------
+template <int KIND, int K>
+__device__ __forceinline__ double mu_expr(double v, double x) {
+  const double mu = 4.0 * v * v;
+  const double inv8x = 1.0 / (8.0 * x);
+  double P = 1.0;
+#pragma unroll
+  for (int k = K; k >= 1; --k) {
+    const double odd = (double)((2 * k - 1) * (2 * k - 1));
+    double r = (mu - odd) * (inv8x * (1.0 / (double)k));
+    if (KIND == KIND_I) r = -r;
+    P = fma(r, P, 1.0);
+  }
+  const double S = fabs(P);
+  if (KIND == KIND_I) return x + log(S * rsqrt(kTwoPi * x));
+  return log(S * sqrt(kPi / (2.0 * x))) - x;
+}
+
+// P_k(p) of the Debye polynomial u_k(t) = t^k P_k(t^2); k is a compile-time
+// constant after unrolling, so the switch folds away.
+template <typename T>
+__device__ __forceinline__ T debye_P(int k, T p) {
+  switch (k) {
+    case 1: return lb_debye_P1(p);
+    case 2: return lb_debye_P2(p);
+    case 3: return lb_debye_P3(p);
+    case 4: return lb_debye_P4(p);
+    case 5: return lb_debye_P5(p);
+    case 6: return lb_debye_P6(p);
+    case 7: return lb_debye_P7(p);
+    case 8: return lb_debye_P8(p);
+    case 9: return lb_debye_P9(p);
+    case 10: return lb_debye_P10(p);
+    case 11: return lb_debye_P11(p);
+    case 12: return lb_debye_P12(p);
+    default: return lb_debye_P13(p);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T debye_Q(int k, T p) {
+  switch (k) {
+    case 1: return lb_debye_Q1(p);
+    case 2: return lb_debye_Q2(p);
+    case 3: return lb_debye_Q3(p);
+    case 4: return lb_debye_Q4(p);
+    case 5: return lb_debye_Q5(p);
+    case 6: return lb_debye_Q6(p);
+    case 7: return lb_debye_Q7(p);
+    case 8: return lb_debye_Q8(p);
+    case 9: return lb_debye_Q9(p);
+    case 10: return lb_debye_Q10(p);
+    case 11: return lb_debye_Q11(p);
+    case 12: return lb_debye_Q12(p);
+    default: return lb_debye_Q13(p);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// U_K expression (paper Eqs. "log Iv u k", "log Kv u k"):
+//   x' = x/v, r = sqrt(1 + x'^2), t = 1/r, eta = r + log(x' / (1 + r)),
+//   S = 1 + sum_{k=1}^{K} (+-1)^k u_k(t) / v^k  (+ for I, alternating for K)
+//   log I = -log(2 pi v)/2 + v eta - log(1 + x'^2)/4 + log|S|
+//   log K =  log(pi/(2v))/2 - v eta - log(1 + x'^2)/4 + log|S|
+// with u_k(t) = t^k P_k(t^2) (Debye polynomials, generated exactly from the
+// recurrence of Eqs. "u0", "uk").  The two log terms are merged:
+// -log(2 pi v)/2 - log(r)/2 = log(1 / sqrt(2 pi v r)).
+// ---------------------------------------------------------------------------
+template <int KIND, int K>
+__device__ __forceinline__ double u_expr(double v, double x) {
+  const double xp = x / v;
+  double r;
+  if (xp < 1e150) r = sqrt(fma(xp, xp, 1.0));
+  else r = xp;                                   // 1 + x'^2 rounds to x'^2
+  const double t = 1.0 / r;
+  const double p = t * t;
+  double q = t / v;
+  if (KIND == KIND_K) q = -q;
+  // Horner in q over k = K..1:  S = 1 + q (P_1 + q (P_2 + ... + q P_K))
+  double acc = debye_P(K, p);
+#pragma unroll
+  for (int k = K - 1; k >= 1; --k) acc = fma(acc, q, debye_P(k, p));
+  const double S = fabs(fma(acc, q, 1.0));
+  const double eta = r + log(xp / (1.0 + r));
+  if (KIND == KIND_I) return fma(v, eta, log(S * rsqrt(kTwoPi * v * r)));
+  return fma(-v, eta, log(S * sqrt(kPi / (2.0 * v * r))));
+}
+
+// ---------------------------------------------------------------------------
+// Power series of I_v (fallback region of log I):
+//   a_0 = 1/Gamma(v+1), a_{k+1} = a_k x^2 / (4 (k+1)(k+v+1))      (Eq. "ak recurrence")
+//   log I_v(x) = v log(x/2) + log a_0 + log sum_k a_k / a_0       (Eq. "log Iv")
+// The log-sum-exp shift is a_0 instead of the peak term a_K: any shift is
+// exact, and in the fallback region (x <= 30) the largest ratio a_K/a_0 is
+// below e^x, far from overflow, so the terms can be summed in linear scale
+// without a logarithm per term.  The sum is 1 + T with T accumulated
+// separately and finished with log1p, so tiny x loses nothing.  Terms are
+// added until they fall below 2^-56 of the running sum after the peak index
+// K = (-v + sqrt(x^2 + v^2))/2 (Eq. "K"), as the truncation rule of Sec. 3.1
+// prescribes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double series_log_i(double v, double x) {
+  const double y = 0.25 * x * x;
+  const double kpk = 0.5 * (sqrt(fma(x, x, v * v)) - v);
+  double term = 1.0, T = 0.0;
+  double k = 1.0;
+  for (int it = 0; it < 400; ++it) {
+    term *= y / (k * (k + v));
+    T += term;
+    if (k > kpk && term <= 1.3877787807814457e-17 * (1.0 + T)) break;   // 2^-56
+    k += 1.0;
+  }
+  double res = log1p(T) - lgamma(v + 1.0);
+  if (v != 0.0) res = fma(v, log(0.5 * x), res);
+  return res;
+}
+
+// ---------------------------------------------------------------------------
+// x-derivatives of the same expressions (the adjoint of the forward path).
+// Each differentiates its expression term by term, so it is valid exactly
+// where the expression is; the paper lists derivatives as future work
+// (Sec. 7), and these follow directly from its Eqs.
+// ---------------------------------------------------------------------------
+
+// mu_K: log f = +-x - log(2 pi x)/2 + log S (I: +x, K: -x and +log(pi/2)/2),
+// S = 1 + sum_k c_k x^-k, so d/dx log f = +-1 - 1/(2x) - (sum_k k c_k x^-k) / (x S).
+template <int KIND, int K>
+__device__ __forceinline__ double mu_dx(double v, double x) {
+  const double mu = 4.0 * v * v;
+  const double inv8x = 1.0 / (8.0 * x);
+  double term = 1.0, S = 1.0, D = 0.0;
+#pragma unroll
+  for (int k = 1; k <= K; ++k) {
+    const double odd = (double)((2 * k - 1) * (2 * k - 1));
+    double r = (mu - odd) * (inv8x * (1.0 / (double)k));
+    if (KIND == KIND_I) r = -r;
+    term *= r;
+    S += term;
+    D = fma((double)k, term, D);
+  }
+  const double inv_x = 1.0 / x;
+  const double base = (KIND == KIND_I) ? 1.0 : -1.0;
+  return base - inv_x * (0.5 + D / S);
+}
+
+// U_K: with x' = x/v, t = (1 + x'^2)^-1/2, d(v eta)/dx = 1/(t x'),
+// d/dx [-log(1 + x'^2)/4] = -x' t^2 / (2v), dt/dx = -x' t^3 / v and
+// d/dt u_k(t) = t^(k-1) Q_k(t^2):
+//   d/dx log f = +-1/(t x') - (x' t^2 / v) (1/2 + SQ / S),
+//   S = 1 + sum q^k P_k(t^2), SQ = sum q^k Q_k(t^2), q = +-t/v.
+template <int KIND, int K>
+__device__ __forceinline__ double u_dx(double v, double x) {
+  const double xp = x / v;
+  double r;
+  if (xp < 1e150) r = sqrt(fma(xp, xp, 1.0));
+  else r = xp;
+  const double t = 1.0 / r;
+  const double p = t * t;
+  double q = t / v;
+  if (KIND == KIND_K) q = -q;
+  double accP = debye_P(K, p), accQ = debye_Q(K, p);
+#pragma unroll
+  for (int k = K - 1; k >= 1; --k) {
+    accP = fma(accP, q, debye_P(k, p));
+    accQ = fma(accQ, q, debye_Q(k, p));
+  }
+  const double S = fma(accP, q, 1.0);
+  const double SQ = accQ * q;
+  const double lead = r / xp;                       // 1/(t x') = sqrt(1 + x'^2)/x'
+  const double corr = (xp * p / v) * (0.5 + SQ / S);
+  return (KIND == KIND_I) ? lead - corr : -lead - corr;
+}
+
+// Series: log I = v log(x/2) - lgamma(v+1) + log(1 + T), T = sum_{k>=1} a_k/a_0
+// with a_k/a_0 proportional to x^(2k):  d/dx log I = v/x + (2/x) (sum k a_k/a_0) / (1 + T).
+__device__ __forceinline__ double series_dx(double v, double x) {
+  const double y = 0.25 * x * x;
+  const double kpk = 0.5 * (sqrt(fma(x, x, v * v)) - v);
+  double term = 1.0, T = 0.0, D = 0.0;
+  double k = 1.0;
+  for (int it = 0; it < 400; ++it) {
+    term *= y / (k * (k + v));
+    T += term;
+    D = fma(k, term, D);
+    if (k > kpk && term <= 1.3877787807814457e-17 * (1.0 + T)) break;
+    k += 1.0;
+  }
+  return (v + 2.0 * D / (1.0 + T)) / x;
+}
+
+}  // namespace lb

@@ -1,0 +1,480 @@
+// logbessel.cu -- kernels and C ABI of the GB300 log-Bessel library.
+//
+// Pipeline for one call (paper Sec. 4.3 sorts the pairs by expression before
+// launch so that warps do not diverge; here the grouping is done on chip):
+//
+//   1. lb_tiles_kernel: persistent CTAs walk tiles of LB_TILE pairs.  Each
+//      thread loads LB_ITEMS pairs (coalesced), handles domain edges, and
+//      classifies the rest (Table "input ranges").  The tile's pairs are
+//      binned per region into shared-memory index lists, and the block then
+//      works through each list with all its threads, so every warp runs one
+//      expression (mu_20, U_13, power series) at a time.  K pairs of the
+//      fallback region are appended to a global queue instead.
+//   2. lb_kint_kernel: one warp per queued K pair evaluates the integral with
+//      the nodes spread over the lanes (lb_kint.cuh).
+//
+// All arithmetic of the plain form is FP64.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <utility>
+#include <vector>
+#include <stdio.h>
+#include <string.h>
+#include <string>
+
+#include "logbessel.h"
+#include "lb_kint.cuh"
+
+#define LB_THREADS 256
+#define LB_ITEMS 4
+#define LB_TILE (LB_THREADS * LB_ITEMS)
+#define LB_VERSION "0.1.0"
+
+using namespace lb;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+template <int KIND, bool DX>
+__device__ __forceinline__ double eval_region(int r, double v, double x, int mode) {
+  if (DX) {
+    switch (r) {
+      case R_MU20: return mu_dx<KIND, 20>(v, x);
+      case R_U13: return u_dx<KIND, 13>(v, x);
+      case R_MU3: return mu_dx<KIND, 3>(v, x);
+      case R_U4: return u_dx<KIND, 4>(v, x);
+      case R_U6: return u_dx<KIND, 6>(v, x);
+      case R_U9: return u_dx<KIND, 9>(v, x);
+      default: return (KIND == KIND_I) ? series_dx(v, x) : __longlong_as_double(0x7ff8000000000000LL);
+    }
+  }
+  switch (r) {
+    case R_MU20: return mu_expr<KIND, 20>(v, x);
+    case R_U13: return u_expr<KIND, 13>(v, x);
+    case R_MU3: return mu_expr<KIND, 3>(v, x);
+    case R_U4: return u_expr<KIND, 4>(v, x);
+    case R_U6: return u_expr<KIND, 6>(v, x);
+    case R_U9: return u_expr<KIND, 9>(v, x);
+    default: return (KIND == KIND_I) ? series_log_i(v, x) : __longlong_as_double(0x7ff8000000000000LL);
+  }
+}
+
+// Tile kernel: classify, bin per region in shared memory, evaluate the
+// per-thread expressions, queue the K fallback pairs.
+template <int KIND, bool DX>
+__global__ void __launch_bounds__(LB_THREADS)
+lb_tiles_kernel(const double* __restrict__ v, int64_t v_stride, const double* __restrict__ x,
+                double* __restrict__ out, int64_t n, int mode, int forced_region,
+                unsigned int* __restrict__ qcount, uint32_t* __restrict__ queue) {
+  __shared__ double sv[LB_TILE];
+  __shared__ double sx[LB_TILE];
+  __shared__ uint16_t lists[8][LB_TILE];
+  __shared__ int counts[8];
+  __shared__ unsigned int qbase;
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t t0 = tile * LB_TILE;
+    if (tid < 8) counts[tid] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < LB_ITEMS; ++it) {
+      const int li = it * LB_THREADS + tid;
+      const int64_t i = t0 + li;
+      if (i < n) {
+        double vi = v[i * v_stride];
+        const double xi = x[i];
+        if (KIND == KIND_K) vi = fabs(vi);
+        double sp;
+        if (DX ? special_dx<KIND>(vi, xi, &sp) : special_value<KIND>(vi, xi, &sp)) {
+          out[i] = sp;
+        } else {
+          sv[li] = vi;
+          sx[li] = xi;
+          const int r = forced_region >= 0 ? forced_region : classify(vi, xi, mode);
+          const int pos = atomicAdd(&counts[r], 1);
+          lists[r][pos] = (uint16_t)li;
+        }
+      }
+    }
+    __syncthreads();
+    // Expressions evaluated one thread per pair, one region at a time.
+    for (int r = 0; r < 8; ++r) {
+      if (r == R_SPECIAL) continue;
+      if (KIND == KIND_K && r == R_FALLBACK) continue;
+      const int c = counts[r];
+      for (int j = tid; j < c; j += LB_THREADS) {
+        const int li = lists[r][j];
+        out[t0 + li] = eval_region<KIND, DX>(r, sv[li], sx[li], mode);
+      }
+    }
+    if (KIND == KIND_K) {
+      const int c = counts[R_FALLBACK];
+      if (c > 0) {
+        if (tid == 0) qbase = atomicAdd(qcount, (unsigned int)c);
+        __syncthreads();
+        const unsigned int b = qbase;
+        for (int j = tid; j < c; j += LB_THREADS) queue[b + j] = (uint32_t)(t0 + lists[R_FALLBACK][j]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// K integral: one warp per queued pair; the 32 pairs of a batch share the
+// per-pair prefactor work (each lane computes one prefactor).
+template <bool GAUSS, bool DX>
+__global__ void __launch_bounds__(LB_THREADS, 2)
+lb_kint_kernel(const double* __restrict__ v, int64_t v_stride, const double* __restrict__ x,
+               double* __restrict__ out, const unsigned int* __restrict__ qcount,
+               const uint32_t* __restrict__ queue) {
+  const unsigned int cnt = *qcount;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = warp * 32; b < (int64_t)cnt; b += nwarps * 32) {
+    const int64_t q = b + lane;
+    const bool valid = q < (int64_t)cnt;
+    const int64_t idx = valid ? (int64_t)queue[q] : 0;
+    const double vi = valid ? fabs(v[idx * v_stride]) : 1.0;
+    const double xi = valid ? x[idx] : 1.0;
+    // log-prefactor log(sqrt(pi) e^{-x} / (Gamma(v+1/2) (2x)^v)), or its x-derivative -v/x - 1
+    const double pre = DX ? -(vi / xi + 1.0) : kint_prefactor(vi, xi);
+    const int m = (int)min((int64_t)32, (int64_t)cnt - b);
+    double mine = 0.0;
+    for (int e = 0; e < m; ++e) {
+      const double ve = __shfl_sync(0xffffffffu, vi, e);
+      const double xe = __shfl_sync(0xffffffffu, xi, e);
+      const double li = GAUSS ? kint_gauss<DX>(ve, xe, lane) : kint_log_simpson(ve, xe, lane);
+      if (lane == e) mine = li;
+    }
+    if (valid) out[idx] = pre + mine;
+  }
+}
+
+template <int KIND>
+__global__ void lb_classify_kernel(const double* __restrict__ v, int64_t v_stride,
+                                   const double* __restrict__ x, uint8_t* __restrict__ reg,
+                                   int64_t n, int mode) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double vi = v[i * v_stride];
+    const double xi = x[i];
+    if (KIND == KIND_K) vi = fabs(vi);
+    double sp;
+    reg[i] = special_value<KIND>(vi, xi, &sp) ? (uint8_t)R_SPECIAL : (uint8_t)classify(vi, xi, mode);
+  }
+}
+
+// von Mises-Fisher log-normaliser (paper Sec. 6.3):
+//   log C_d(k) = (d/2 - 1) log k - (d/2) log(2 pi) - log I_{d/2-1}(k),
+// applied in place to out[i] = log I_{d/2-1}(kappa[i]) (or, for DX, to
+// out[i] = d/dk log I_{d/2-1}, giving d/dk log C_d = (d/2-1)/k - I'/I).
+// At k = 0: log C_d(0) = lgamma(d/2) - log 2 - (d/2) log pi, the limit of
+// I_nu(k) ~ (k/2)^nu / Gamma(nu + 1).
+template <bool DX>
+__global__ void lb_vmf_finish_kernel(const double* __restrict__ kappa, double* __restrict__ out, int64_t n,
+                                     double d) {
+  const double nu = 0.5 * d - 1.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double k = kappa[i];
+    if (DX) {
+      out[i] = (k == 0.0) ? 0.0 : nu / k - out[i];
+    } else if (k == 0.0) {
+      out[i] = lgamma(0.5 * d) - 0.6931471805599453 - 0.5 * d * 1.1447298858494002;
+    } else {
+      out[i] = fma(nu, log(k), -0.5 * d * 1.8378770664093453) - out[i];
+    }
+  }
+}
+
+__global__ void lb_set_scalar_kernel(double* p, double value) { *p = value; }
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+thread_local std::string g_last_error;
+
+lb_status fail(lb_status st, const char* fmt, const char* a = "", long long b = 0) {
+  char buf[512];
+  snprintf(buf, sizeof buf, fmt, a, b);
+  g_last_error = buf;
+  return st;
+}
+
+lb_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return LB_ECUDA;
+  }
+  return LB_OK;
+}
+
+int sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev] == 0) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    cache[dev] = sms;
+  }
+  return cache[dev];
+}
+
+// ---------------------------------------------------------------------------
+// launch accounting and optional per-kernel CUDA-event timing
+// ---------------------------------------------------------------------------
+enum ProfSlotId { PS_TILES = 0, PS_KINT = 1, PS_CLASSIFY = 2, PS_AUX = 3, PS_NSLOTS = 4 };
+const char* const kSlotNames[PS_NSLOTS] = {"lb_tiles_kernel", "lb_kint_kernel", "lb_classify_kernel",
+                                           "lb_aux_kernels"};
+
+struct ProfState {
+  std::mutex mu;
+  bool on = false;
+  long long launches[PS_NSLOTS] = {0, 0, 0, 0};
+  long long timed[PS_NSLOTS] = {0, 0, 0, 0};
+  double ms[PS_NSLOTS] = {0, 0, 0, 0};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+};
+ProfState& prof() {
+  static ProfState p;
+  return p;
+}
+std::atomic<long long> g_total_launches{0};
+
+void prof_drain_locked(ProfState& P) {
+  for (auto& e : P.pending) {
+    float t = 0.f;
+    if (cudaEventSynchronize(e.second.second) == cudaSuccess &&
+        cudaEventElapsedTime(&t, e.second.first, e.second.second) == cudaSuccess) {
+      P.ms[e.first] += t;
+      P.timed[e.first] += 1;
+    }
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  P.pending.clear();
+}
+
+// Launch `body` (one kernel launch) on stream st under slot `slot`.
+template <typename F>
+lb_status launch(int slot, cudaStream_t st, F&& body) {
+  ProfState& P = prof();
+  cudaEvent_t a = nullptr, b = nullptr;
+  bool timed = false;
+  {
+    std::lock_guard<std::mutex> lk(P.mu);
+    timed = P.on;
+  }
+  if (timed && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)) timed = false;
+  if (timed) cudaEventRecord(a, st);
+  body();
+  lb_status s = check_launch(kSlotNames[slot]);
+  g_total_launches.fetch_add(1);
+  {
+    std::lock_guard<std::mutex> lk(P.mu);
+    P.launches[slot] += 1;
+    if (timed) {
+      cudaEventRecord(b, st);
+      P.pending.push_back({slot, {a, b}});
+    }
+  }
+  return s;
+}
+
+lb_status validate(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, const void* out,
+                   int64_t n, int mode) {
+  if (n < 0) return fail(LB_EINVAL, "n must be >= 0 (got %s%lld)", "", (long long)n);
+  if (dtype != LB_F64 && dtype != LB_F32) return fail(LB_EINVAL, "unknown dtype %s%lld", "", (long long)dtype);
+  if (mode < 0 || mode > 2) return fail(LB_EINVAL, "unknown mode %s%lld", "", (long long)mode);
+  if (v_stride != 0 && v_stride != 1) return fail(LB_EINVAL, "v_stride must be 0 or 1 (got %s%lld)", "", (long long)v_stride);
+  if (n > 0 && (!v || !x || !out)) return fail(LB_EINVAL, "NULL %s pointer with n = %lld", !v ? "v" : (!x ? "x" : "out"), (long long)n);
+  if (dtype == LB_F32) return fail(LB_ENOTSUP, "%sFP32 path not built in this version", "", 0);
+  return LB_OK;
+}
+
+// Largest chunk handled with one queue: the queue holds 32-bit offsets.
+const int64_t kChunk = (int64_t)1 << 26;
+
+template <int KIND, bool DX>
+lb_status run(const double* v, int64_t v_stride, const double* x, double* out, int64_t n, int mode,
+              int forced_region, cudaStream_t st) {
+  const int sms = sm_count();
+  if (KIND == KIND_I || (forced_region >= 0 && forced_region != R_FALLBACK)) {
+    const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
+    const int grid = (int)(ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4);
+    return launch(PS_TILES, st, [&] {
+      lb_tiles_kernel<KIND, DX><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region, nullptr, nullptr);
+    });
+  }
+  const int64_t cap = n < kChunk ? n : kChunk;
+  void* ws = nullptr;
+  const size_t bytes = 256 + (size_t)cap * sizeof(uint32_t);
+  cudaError_t e = cudaMallocAsync(&ws, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LB_ENOMEM, "cudaMallocAsync of %s%lld bytes failed", "", (long long)bytes);
+  }
+  unsigned int* qcount = (unsigned int*)ws;
+  uint32_t* queue = (uint32_t*)((char*)ws + 256);
+  lb_status status = LB_OK;
+  for (int64_t c0 = 0; c0 < n && status == LB_OK; c0 += kChunk) {
+    const int64_t cn = (n - c0) < kChunk ? (n - c0) : kChunk;
+    if (cudaMemsetAsync(qcount, 0, sizeof(unsigned int), st) != cudaSuccess) { status = check_launch("cudaMemsetAsync"); break; }
+    const double* vc = v + c0 * v_stride;
+    const double* xc = x + c0;
+    double* oc = out + c0;
+    const int64_t ntiles = (cn + LB_TILE - 1) / LB_TILE;
+    const int grid = (int)(ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4);
+    status = launch(PS_TILES, st, [&] {
+      lb_tiles_kernel<KIND, DX><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount, queue);
+    });
+    if (status != LB_OK) break;
+    const int kgrid = sms * 8;
+    status = launch(PS_KINT, st, [&] {
+      if (mode == MODE_TIGHT)
+        lb_kint_kernel<true, DX><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
+      else
+        lb_kint_kernel<false, false><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
+    });
+  }
+  cudaFreeAsync(ws, st);
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status logbessel_i(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                      int64_t n, lb_mode mode, void* cuda_stream) {
+  lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
+  if (s != LB_OK || n == 0) return s;
+  return run<KIND_I, false>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
+                            (cudaStream_t)cuda_stream);
+}
+
+lb_status logbessel_k(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                      int64_t n, lb_mode mode, void* cuda_stream) {
+  lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
+  if (s != LB_OK || n == 0) return s;
+  return run<KIND_K, false>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
+                            (cudaStream_t)cuda_stream);
+}
+
+lb_status logbessel_i_dx(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                         int64_t n, lb_mode mode, void* cuda_stream) {
+  lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
+  if (s != LB_OK || n == 0) return s;
+  return run<KIND_I, true>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
+                           (cudaStream_t)cuda_stream);
+}
+
+lb_status logbessel_k_dx(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                         int64_t n, lb_mode mode, void* cuda_stream) {
+  lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
+  if (s != LB_OK || n == 0) return s;
+  if (mode != LB_TIGHT) return fail(LB_ENOTSUP, "%sd/dx log K is implemented for LB_TIGHT only", "", 0);
+  return run<KIND_K, true>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
+                           (cudaStream_t)cuda_stream);
+}
+
+lb_status logbessel_classify(int kind, lb_dtype dtype, const void* v, int64_t v_stride,
+                             const void* x, uint8_t* region_out, int64_t n, lb_mode mode,
+                             void* cuda_stream) {
+  if (kind != 0 && kind != 1) return fail(LB_EINVAL, "kind must be 0 (I) or 1 (K), got %s%lld", "", (long long)kind);
+  lb_status s = validate(dtype, v, v_stride, x, region_out, n, (int)mode);
+  if (s != LB_OK || n == 0) return s;
+  const int grid = sm_count() * 4;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  return launch(PS_CLASSIFY, st, [&] {
+    if (kind == 0)
+      lb_classify_kernel<KIND_I><<<grid, LB_THREADS, 0, st>>>((const double*)v, v_stride, (const double*)x, region_out, n, (int)mode);
+    else
+      lb_classify_kernel<KIND_K><<<grid, LB_THREADS, 0, st>>>((const double*)v, v_stride, (const double*)x, region_out, n, (int)mode);
+  });
+}
+
+lb_status logbessel_eval_region(int kind, lb_dtype dtype, const void* v, int64_t v_stride,
+                                const void* x, void* out, int64_t n, int region, lb_mode mode,
+                                void* cuda_stream) {
+  if (kind != 0 && kind != 1) return fail(LB_EINVAL, "kind must be 0 (I) or 1 (K), got %s%lld", "", (long long)kind);
+  if (region < 0 || region > R_U9 || region == R_SPECIAL)
+    return fail(LB_EINVAL, "region %s%lld is not an expression", "", (long long)region);
+  lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
+  if (s != LB_OK || n == 0) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (kind == 0)
+    return run<KIND_I, false>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, region, st);
+  return run<KIND_K, false>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, region, st);
+}
+
+lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void* out, int64_t n, int deriv,
+                              void* cuda_stream) {
+  if (!(d >= 2.0) || !isfinite(d)) return fail(LB_EINVAL, "dimension d must be finite and >= 2 (got %s%lld)", "", (long long)d);
+  if (deriv != 0 && deriv != 1) return fail(LB_EINVAL, "deriv must be 0 or 1 (got %s%lld)", "", (long long)deriv);
+  lb_status s = validate(dtype, kappa, 0, kappa, out, n, 0);
+  if (s != LB_OK || n == 0) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* nu = nullptr;
+  if (cudaMallocAsync(&nu, sizeof(double), st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LB_ENOMEM, "cudaMallocAsync of %s%lld bytes failed", "", 8);
+  }
+  s = launch(PS_AUX, st, [&] { lb_set_scalar_kernel<<<1, 1, 0, st>>>(nu, 0.5 * d - 1.0); });
+  if (s == LB_OK)
+    s = deriv ? run<KIND_I, true>(nu, 0, (const double*)kappa, (double*)out, n, MODE_TIGHT, -1, st)
+              : run<KIND_I, false>(nu, 0, (const double*)kappa, (double*)out, n, MODE_TIGHT, -1, st);
+  if (s == LB_OK) {
+    const int grid = sm_count() * 4;
+    s = launch(PS_AUX, st, [&] {
+      if (deriv)
+        lb_vmf_finish_kernel<true><<<grid, LB_THREADS, 0, st>>>((const double*)kappa, (double*)out, n, d);
+      else
+        lb_vmf_finish_kernel<false><<<grid, LB_THREADS, 0, st>>>((const double*)kappa, (double*)out, n, d);
+    });
+  }
+  cudaFreeAsync(nu, st);
+  return s;
+}
+
+const char* logbessel_last_error(void) { return g_last_error.c_str(); }
+
+void logbessel_profile_enable(int on) {
+  ProfState& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  prof_drain_locked(P);
+  if (on) {
+    for (int i = 0; i < PS_NSLOTS; ++i) { P.ms[i] = 0.0; P.timed[i] = 0; }
+  }
+  P.on = on != 0;
+}
+
+int logbessel_profile_slots(void) { return PS_NSLOTS; }
+
+lb_status logbessel_profile_get(int slot, const char** name, long long* launches, long long* timed_launches,
+                                double* total_ms) {
+  if (slot < 0 || slot >= PS_NSLOTS) return fail(LB_EINVAL, "profile slot %s%lld out of range", "", (long long)slot);
+  ProfState& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  prof_drain_locked(P);
+  if (name) *name = kSlotNames[slot];
+  if (launches) *launches = P.launches[slot];
+  if (timed_launches) *timed_launches = P.timed[slot];
+  if (total_ms) *total_ms = P.ms[slot];
+  return LB_OK;
+}
+
+long long logbessel_launch_count(void) { return g_total_launches.load(); }
+
+const char* logbessel_version(void) { return LB_VERSION; }
+
+}  // extern "C"

@@ -95,3 +95,47 @@ def edge_pairs():
     vals_x = [0.0, 1e-300, 1e-6, 1.0, 25.0, 30.0, 1e5, 1e300, inf, nan, -1.0]
     V, X = np.meshgrid(np.array(vals_v), np.array(vals_x))
     return V.ravel(), X.ravel()
+
+
+def vmf_mean_resultant(d, kappa, n, seed=0, device="cuda", chunk=2048):
+    """Mean resultant length R = |mean of n unit vectors| drawn from the von
+    Mises-Fisher distribution on S^(d-1) with mean direction e_1.
+
+    Synthetic stand-in for the l2-normalised image features of paper Sec. 6.3.
+    The component w = mu^T x follows Wood's rejection sampler (Wood 1994,
+    "Simulation of the von Mises Fisher distribution"); the tangent part is
+    sqrt(1 - w^2) times a uniform direction orthogonal to e_1, drawn as a
+    normalised Gaussian vector.  Only the running sums are kept, so d = 32768
+    needs no n x d array.  Returns (R, mean of w)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    dm1 = float(d - 1)
+    k = float(kappa)
+    b = dm1 / (2.0 * k + np.sqrt(4.0 * k * k + dm1 * dm1))
+    x0 = (1.0 - b) / (1.0 + b)
+    c = k * x0 + dm1 * np.log(1.0 - x0 * x0)
+    beta = torch.distributions.Beta(torch.tensor(dm1 / 2, dtype=torch.float64, device=device),
+                                    torch.tensor(dm1 / 2, dtype=torch.float64, device=device))
+    ws = []
+    need = n
+    torch.manual_seed(seed)   # Beta sampling draws from the default generator
+    while need > 0:
+        m = max(2 * need, 1024)
+        z = beta.sample((m,))
+        w = (1.0 - (1.0 + b) * z) / (1.0 - (1.0 - b) * z)
+        u = torch.rand(m, dtype=torch.float64, device=device, generator=g)
+        ok = k * w + dm1 * torch.log1p(-x0 * w) - c >= torch.log(u)
+        w = w[ok][:need]
+        ws.append(w)
+        need -= w.numel()
+    w = torch.cat(ws)
+    tang = torch.zeros(d - 1, dtype=torch.float64, device=device)
+    for s0 in range(0, n, chunk):
+        wc = w[s0:s0 + chunk]
+        xi = torch.randn(wc.numel(), d - 1, dtype=torch.float64, device=device, generator=g)
+        xi = xi / xi.norm(dim=1, keepdim=True)
+        tang += (torch.sqrt(torch.clamp(1.0 - wc * wc, min=0.0))[:, None] * xi).sum(dim=0)
+    mean_w = w.mean()
+    xbar_norm2 = mean_w * mean_w + (tang / n).pow(2).sum()
+    return float(torch.sqrt(xbar_norm2)), float(mean_w)

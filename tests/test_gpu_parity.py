@@ -1,0 +1,136 @@
+"""CUDA path against the extended-precision oracle, element by element.
+
+Error metric: err = |got - ref| / max(|ref|, c), c = max(1, |x df/dx|, |v df/dv|)
+(f = log I or log K).  The floor c is the change of f caused by perturbing
+the inputs by one relative unit; log I and log K pass through zero inside the
+tested ranges (e.g. I_1(x) = 1 at x = 1.518), where a pure relative error is
+unbounded.  Gate: err <= 4e-15 for the FP64 path.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2409_08729_gb300 as lb
+from paper_2409_08729_gb300 import workloads as W
+
+TOL64 = 4e-15
+pytestmark = pytest.mark.gpu
+
+
+def _ref(kind, v, x):
+    ref = oracle.log_i(v, x) if kind == "i" else oracle.log_k(v, x)
+    return ref, oracle.error_scale(kind, v, x)
+
+
+def _run(kind, v, x, dev, mode="tight", scalar_v=False):
+    tx = torch.tensor(x, dtype=torch.float64, device=dev)
+    tv = float(v[0]) if scalar_v else torch.tensor(v, dtype=torch.float64, device=dev)
+    fn = lb.log_i if kind == "i" else lb.log_k
+    out = fn(tv, tx, mode=mode)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _report(kind, v, x, got, ref, scale, tol):
+    err = oracle.rel_err(got, ref, scale)
+    bad = np.flatnonzero(~(err <= tol))
+    if bad.size:
+        i = bad[np.argmax(err[bad])]
+        msg = "log %s: %d/%d pairs above %.1e; worst %.3e at v=%r x=%r (got %r, ref %r)" % (
+            kind.upper(), bad.size, err.size, tol, err[i], v[i], x[i], got[i], ref[i])
+        pytest.fail(msg)
+    return err
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_sweep_110k(cuda, kind):
+    """The 11-order sweep v = 2^0..2^10 x 10,000 x ~ U[1, 100] (seed 0), all pairs."""
+    v, x = W.sweep_pairs(10000, seed=0)
+    ref, scale = _ref(kind, v, x)
+    got = _run(kind, v, x, cuda)
+    _report(kind, v, x, got, ref, scale, TOL64)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_half_order_closed_form(cuda, kind):
+    """v = 1/2 on the sweep's arguments against the closed forms
+    I_{1/2}(x) = sqrt(2/(pi x)) sinh x, K_{1/2}(x) = sqrt(pi/(2x)) e^{-x}."""
+    _, x = W.sweep_pairs(1000, seed=0)
+    v = np.full_like(x, 0.5)
+    got = _run(kind, v, x, cuda)
+    if kind == "i":
+        ref = 0.5 * np.log(2 / (np.pi * x)) + x + np.log1p(-np.exp(-2 * x)) - np.log(2)
+    else:
+        ref = 0.5 * np.log(np.pi / (2 * x)) - x
+    scale = np.maximum(1.0, x)
+    _report(kind, v, x, got, ref, scale, TOL64)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+@pytest.mark.parametrize("n", [1, 31, 33, 1023, 1025, 4097, 70001])
+def test_ragged_sizes(cuda, kind, n):
+    v, x = W.robust_pairs(n, seed=n, vmax=1e3, xmin=1e-3, xmax=1e3)
+    ref, scale = _ref(kind, v, x)
+    got = _run(kind, v, x, cuda)
+    _report(kind, v, x, got, ref, scale, TOL64)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_robust_sweep(cuda, kind):
+    """v log-uniform to 1e5 (1% zero, 1% one half), x log-uniform on [1e-6, 1e5]."""
+    v, x = W.robust_pairs(20000, seed=11)
+    ref, scale = _ref(kind, v, x)
+    got = _run(kind, v, x, cuda)
+    _report(kind, v, x, got, ref, scale, TOL64)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_scalar_order(cuda, kind):
+    """One order for all pairs (v_stride = 0)."""
+    for v0 in (0.0, 0.3, 1.0, 7.5, 64.0):
+        x = np.exp(np.random.default_rng(3).uniform(np.log(1e-4), np.log(300.0), 3000))
+        v = np.full_like(x, v0)
+        ref, scale = _ref(kind, v, x)
+        got = _run(kind, v, x, cuda, scalar_v=True)
+        _report(kind, v, x, got, ref, scale, TOL64)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_region_boundaries(cuda, kind):
+    """Pairs straddling every threshold of the paper's table and of the tight dispatch."""
+    v, x = W.boundary_pairs(seed=5)
+    ref, scale = _ref(kind, v, x)
+    got = _run(kind, v, x, cuda)
+    _report(kind, v, x, got, ref, scale, TOL64)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_domain_edges(cuda, kind):
+    v, x = W.edge_pairs()
+    got = _run(kind, v, x, cuda)
+    huge = np.isfinite(x) & (x > 1e8) & np.isfinite(v) & (v >= 0 if kind == "i" else True)
+    ref = oracle.log_i(v, x) if kind == "i" else oracle.log_k(v, x)
+    # The oracle's series declines x > 1e8; there, log I = x - log(2 pi x)/2 +
+    # O(v^2/x) and log K = -x + log(pi/(2x))/2 + O(v^2/x) fix the value.
+    with np.errstate(divide="ignore", invalid="ignore"):
+        asym = np.where(kind == "i", x - 0.5 * np.log(2 * np.pi * x), 0.5 * np.log(np.pi / (2 * x)) - x)
+    ref = np.where(huge, asym, ref)
+    finite = np.isfinite(ref)
+    # non-finite results must match exactly (same infinity or NaN)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    assert np.array_equal(got[np.isinf(ref)], ref[np.isinf(ref)])
+    scale = np.ones(finite.sum())
+    sel = finite & ~huge
+    scale_sel = oracle.error_scale(kind, v[sel], x[sel])
+    err = oracle.rel_err(got[sel], ref[sel], scale_sel)
+    assert np.all(err <= TOL64), (v[sel][np.argmax(err)], x[sel][np.argmax(err)], err.max())
+    err_h = oracle.rel_err(got[huge], ref[huge], np.maximum(1.0, x[huge]))
+    assert np.all(err_h <= TOL64)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_zero_length(cuda, kind):
+    fn = lb.log_i if kind == "i" else lb.log_k
+    out = fn(torch.empty(0, dtype=torch.float64, device=cuda), torch.empty(0, dtype=torch.float64, device=cuda))
+    assert out.numel() == 0
