@@ -288,15 +288,23 @@ def main():
     del per_order_t
     kint_slots = (WM.kint_slots(vm_h[fb_mix], x_h[fb_mix]).sum()
                   + WM.kint_slots(per_order_k[fb_per], x_h[fb_per]).sum())
+    rng_w = np.random.default_rng(0)
+
+    def sampled_sum(fn, sel_idx, vv):
+        if sel_idx.size == 0:
+            return 0.0
+        sub = sel_idx[rng_w.integers(0, sel_idx.size, min(sel_idx.size, 1_000_000))]
+        return float(np.mean(fn(vv[sub], x_h[sub]))) * sel_idx.size
+
     tiles_slots = 0.0
-    for regs, vv in ((regions_i, vm_h), (ri_per, per_order_k)):
-        tiles_slots += np.count_nonzero(regs == 0) * WM.mu20_slots() + np.count_nonzero(regs == 1) * WM.u13_slots()
-        sel = np.flatnonzero(regs == 2)
-        if sel.size:
-            sub = sel[np.random.default_rng(0).integers(0, sel.size, min(sel.size, 1_000_000))]
-            tiles_slots += WM.series_slots(vv[sub], x_h[sub]).mean() * sel.size
-    for regs in (regions_k, rk_per):
-        tiles_slots += np.count_nonzero(regs == 0) * WM.mu20_slots() + np.count_nonzero(regs == 1) * WM.u13_slots()
+    for kind_regs in ((regions_i, vm_h, True), (ri_per, per_order_k, True),
+                      (regions_k, vm_h, False), (rk_per, per_order_k, False)):
+        regs, vv, is_i = kind_regs
+        for rid in (0, 1, 2, 4, 5, 6, 7):
+            if rid == 2 and not is_i:
+                continue
+            sel = np.flatnonzero(regs == rid)
+            tiles_slots += sampled_sum(lambda a, b, r=rid: WM.region_slots(r, a, b), sel, vv)
     work_slots = {"lb_kint_kernel": kint_slots, "lb_tiles_kernel": tiles_slots}
     if name in work_slots:
         work = 2.0 * work_slots[name] * args.steps
@@ -307,7 +315,7 @@ def main():
     other = {k: {"achieved_gflops": 2.0 * w * args.steps / (prof[k][2] / 1e3) / 1e9 if prof.get(k, (0, 0, 0))[2] else None}
              for k, w in work_slots.items()}
     mix = {}
-    for nm, rid in (("mu20", 0), ("u13", 1), ("fallback", 2)):
+    for nm, rid in (("mu20", 0), ("u13", 1), ("fallback", 2), ("u4", 5), ("u6", 6), ("u9", 7)):
         mix[nm] = {"i": float(np.mean(regions_i == rid)), "k": float(np.mean(regions_k == rid))}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

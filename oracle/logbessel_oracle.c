@@ -254,11 +254,20 @@ static dd log_i_dd(dd v, double x) {
 /* phi(t) = -x cosh t + log cosh(v t), t >= 0 in double-double */
 static dd k_phi(dd v, double x, dd t) {
   dd et = dd_exp(t);
+  if (isinf(et.hi)) return dd_from(-INFINITY);        /* x cosh t overflows: the integrand is 0 */
   dd cosh_t = dd_ldexp(dd_add(et, dd_div(dd_from(1.0), et)), -1);
   dd a = dd_mul(v, t);                                /* v t >= 0 */
   /* log cosh a = a - ln 2 + log1p(exp(-2a)) */
   dd lc = dd_add(dd_sub(a, DD_LN2), dd_log1p(dd_exp(dd_ldexp(dd_neg(a), 1))));
   return dd_sub(lc, dd_mul_d(cosh_t, x));
+}
+
+/* exp(phi(t) - phi_max); 0 where x cosh t overflows (double-double
+ * arithmetic on infinities would give NaN) */
+static dd k_term(dd v, double x, dd t, dd pmax) {
+  dd ph = k_phi(v, x, t);
+  if (isinf(ph.hi)) return dd_from(0.0);
+  return dd_exp(dd_sub(ph, pmax));
 }
 
 /* derivative of phi in plain double, used only to locate the peak */
@@ -300,7 +309,7 @@ static dd log_k_dd(dd v, double x) {
   dd sum = dd_from(0.0);
   for (int j = 0; j <= m; ++j) {
     dd tj = dd_add(dd_from(tlo), two_prod((double)j, h));
-    dd f = dd_exp(dd_sub(k_phi(v, x, tj), pmax));
+    dd f = k_term(v, x, tj, pmax);
     if (j == 0 || j == m) f = dd_ldexp(f, -1);
     sum = dd_add(sum, f);
   }
@@ -308,15 +317,15 @@ static dd log_k_dd(dd v, double x) {
   /* The trapezoid error for an analytic integrand behaves like exp(-c/h), so
    * each halving roughly squares it: once a halving changes the sum by less
    * than 1e-18 (relative), the new sum is accurate far beyond 1e-30.  The
-   * double-double noise floor of phi (terms up to |x cosh t| + |v t|) bounds
-   * what can be resolved at all. */
-  double noise = 1e-31 * (1.0 + fabs(pmax.hi) + x * cosh(thi) + vd * thi);
+   * double-double noise floor of phi where the integrand matters
+   * (|x cosh t| <= |phi_max| + 90 + v t there) bounds what can be resolved. */
+  double noise = 1e-31 * (1.0 + fabs(pmax.hi) + 100.0 + 2.0 * vd * thi);
   if (noise < 1e-18) noise = 1e-18;
   for (int level = 0; level < 16; ++level) {
     dd add = dd_from(0.0);
     for (int j = 0; j < m; ++j) {
       dd tj = dd_add(dd_from(tlo), two_prod((double)j + 0.5, h));
-      add = dd_add(add, dd_exp(dd_sub(k_phi(v, x, tj), pmax)));
+      add = dd_add(add, k_term(v, x, tj, pmax));
     }
     sum = dd_add(sum, add);
     m *= 2;

@@ -52,6 +52,8 @@ def lib():
         L.logbessel_profile_get.restype = i32
         L.logbessel_measure_fp64.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
         L.logbessel_measure_fp64.restype = i32
+        L.logbessel_math_eval.argtypes = [i32, vp, vp, i64, vp]
+        L.logbessel_math_eval.restype = i32
         L.logbessel_launch_count.argtypes = []
         L.logbessel_launch_count.restype = ctypes.c_longlong
         _lib = L
@@ -85,6 +87,6 @@ def launch_count():
 
 def measure_fp64(stream=None):
     """Measured FP64 rates of the current GPU: {'dfma','exp','log','div','sqrt','lgamma'} per second."""
-    rates = (ctypes.c_double * 6)()
+    rates = (ctypes.c_double * 8)()
     check(lib().logbessel_measure_fp64(rates, stream))
-    return dict(zip(("dfma", "exp", "log", "div", "sqrt", "lgamma"), list(rates)))
+    return dict(zip(("dfma", "exp", "log", "div", "sqrt", "lgamma", "fm_exp", "fm_log"), list(rates)))

@@ -58,8 +58,13 @@ def gauss_laguerre(N):
 
 
 def arr(name, vals):
+    """The table as double, plus a float copy named lb_kqf_* for the FP32 path."""
+    import struct
     body = ",\n  ".join(", ".join(repr(float(v)) for v in vals[i:i + 4]) for i in range(0, len(vals), 4))
-    return "static __device__ const double %s[%d] = {\n  %s};\n" % (name, len(vals), body)
+    fl = [struct.unpack("f", struct.pack("f", float(v)))[0] for v in vals]
+    bodyf = ",\n  ".join(", ".join(repr(v) + "f" for v in fl[i:i + 4]) for i in range(0, len(fl), 4))
+    return ("static __device__ const double %s[%d] = {\n  %s};\n" % (name, len(vals), body)
+            + "static __device__ const float %s[%d] = {\n  %s};\n" % (name.replace("lb_kq_", "lb_kqf_"), len(fl), bodyf))
 
 
 def main():

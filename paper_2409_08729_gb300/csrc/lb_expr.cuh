@@ -19,6 +19,7 @@ template <> __host__ __device__ __forceinline__ double lb_fma<double>(double a, 
 template <> __host__ __device__ __forceinline__ float lb_fma<float>(float a, float b, float c) { return fmaf(a, b, c); }
 
 #include "debye_uk.h"
+#include "lb_fastmath.cuh"
 
 namespace lb {
 
@@ -91,9 +92,16 @@ __device__ __forceinline__ bool tight_mu20(double v, double x) {
 }
 __device__ __forceinline__ bool tight_u13(double v, double x) { return (x > 25.0 && v > 0.7) || v > 16.0; }
 
+// With the pairs binned per expression on chip (no warp divergence), the
+// tight dispatch also uses the shorter uniform expansions of the paper's CPU
+// order, with order thresholds from the same error map: U_4 for v > 230,
+// U_6 for v > 70, U_9 for v > 28 (truncation <= 2e-16 for every x).
 __device__ __forceinline__ int classify(double v, double x, int mode) {
   if (mode == MODE_TIGHT) {
     if (tight_mu20(v, x)) return R_MU20;
+    if (v > 230.0) return R_U4;
+    if (v > 70.0) return R_U6;
+    if (v > 28.0) return R_U9;
     if (tight_u13(v, x)) return R_U13;
     return R_FALLBACK;
   }
@@ -119,21 +127,42 @@ __device__ __forceinline__ int classify(double v, double x, int mode) {
 // S is formed by Horner's rule on the term ratios
 //   r_k = (mu - (2k-1)^2) / (8 x k),  S = 1 + s r_1 (1 + s r_2 (1 + ... (1 + s r_K))).
 // ---------------------------------------------------------------------------
+// The number of terms actually summed is the smallest n <= K after which
+// the terms fall below 2^-56 (a later term is then below the rounding of S),
+// found with a single-precision pass and made uniform across the warp, so
+// the double-precision Horner loop never diverges.  All 32 lanes of the
+// warp must call it together.
 template <int KIND, int K>
 __device__ __forceinline__ double mu_expr(double v, double x) {
+  // single-precision estimate of the number of terms
+  int n = K;
+  {
+    const float muf = 4.0f * (float)v * (float)v, inv8xf = 1.0f / (8.0f * (float)x);
+    float t = 1.0f;
+#pragma unroll 1
+    for (int k = 1; k <= K; ++k) {
+      t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * inv8xf / (float)k;
+      if (fabsf(t) < 1.4e-17f) { n = k; break; }
+    }
+  }
+  n = __reduce_max_sync(0xffffffffu, n);
   const double mu = 4.0 * v * v;
   const double inv8x = 1.0 / (8.0 * x);
   double P = 1.0;
+  // Unrolled, so (2k-1)^2 and 1/k are constants; terms above n are skipped
+  // by a warp-uniform predicate.
 #pragma unroll
   for (int k = K; k >= 1; --k) {
-    const double odd = (double)((2 * k - 1) * (2 * k - 1));
-    double r = (mu - odd) * (inv8x * (1.0 / (double)k));
-    if (KIND == KIND_I) r = -r;
-    P = fma(r, P, 1.0);
+    if (k <= n) {
+      const double odd = (double)((2 * k - 1) * (2 * k - 1));
+      double r = (mu - odd) * (inv8x * (1.0 / (double)k));
+      if (KIND == KIND_I) r = -r;
+      P = fma(r, P, 1.0);
+    }
   }
   const double S = fabs(P);
-  if (KIND == KIND_I) return x + log(S * rsqrt(kTwoPi * x));
-  return log(S * sqrt(kPi / (2.0 * x))) - x;
+  if (KIND == KIND_I) return x + fm_log(S * rsqrt(kTwoPi * x));
+  return fm_log(S * sqrt(kPi / (2.0 * x))) - x;
 }
 
 // P_k(p) of the Debye polynomial u_k(t) = t^k P_k(t^2); k is a compile-time
@@ -201,9 +230,9 @@ __device__ __forceinline__ double u_expr(double v, double x) {
 #pragma unroll
   for (int k = K - 1; k >= 1; --k) acc = fma(acc, q, debye_P(k, p));
   const double S = fabs(fma(acc, q, 1.0));
-  const double eta = r + log(xp / (1.0 + r));
-  if (KIND == KIND_I) return fma(v, eta, log(S * rsqrt(kTwoPi * v * r)));
-  return fma(-v, eta, log(S * sqrt(kPi / (2.0 * v * r))));
+  const double eta = r + fm_log(xp / (1.0 + r));
+  if (KIND == KIND_I) return fma(v, eta, fm_log(S * rsqrt(kTwoPi * v * r)));
+  return fma(-v, eta, fm_log(S * sqrt(kPi / (2.0 * v * r))));
 }
 
 // ---------------------------------------------------------------------------
@@ -213,25 +242,43 @@ __device__ __forceinline__ double u_expr(double v, double x) {
 // The log-sum-exp shift is a_0 instead of the peak term a_K: any shift is
 // exact, and in the fallback region (x <= 30) the largest ratio a_K/a_0 is
 // below e^x, far from overflow, so the terms can be summed in linear scale
-// without a logarithm per term.  The sum is 1 + T with T accumulated
-// separately and finished with log1p, so tiny x loses nothing.  Terms are
-// added until they fall below 2^-56 of the running sum after the peak index
-// K = (-v + sqrt(x^2 + v^2))/2 (Eq. "K"), as the truncation rule of Sec. 3.1
-// prescribes.
+// without a logarithm per term.  Terms are kept until they fall below 2^-56
+// of the running sum after the peak index K = (-v + sqrt(x^2 + v^2))/2
+// (Eq. "K"), the truncation rule of Sec. 3.1; the count n is found with a
+// single-precision pass and made uniform across the warp.  The sum
+//   S = 1 + r_1 (1 + r_2 (1 + ... (1 + r_n))),  r_k = y / (k (k + v)),  y = x^2/4,
+// is then evaluated backwards as a fraction A/B (A <- d_k B + y A,
+// B <- d_k B with d_k = k (k + v)), so the double-precision loop has no
+// division; B stays below 1e250 for n <= 80 and v <= 16.  All 32 lanes of the
+// warp must call it together.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double series_log_i(double v, double x) {
-  const double y = 0.25 * x * x;
-  const double kpk = 0.5 * (sqrt(fma(x, x, v * v)) - v);
-  double term = 1.0, T = 0.0;
-  double k = 1.0;
-  for (int it = 0; it < 400; ++it) {
-    term *= y / (k * (k + v));
-    T += term;
-    if (k > kpk && term <= 1.3877787807814457e-17 * (1.0 + T)) break;   // 2^-56
-    k += 1.0;
+  int n = 1;
+  {
+    const float yf = 0.25f * (float)x * (float)x, vf = (float)v;
+    const float kpk = 0.5f * (sqrtf(fmaf((float)x, (float)x, vf * vf)) - vf);
+    float term = 1.0f, T = 0.0f;
+#pragma unroll 1
+    for (int k = 1; k <= 90; ++k) {
+      term *= yf / ((float)k * ((float)k + vf));
+      T += term;
+      n = k;
+      if ((float)k > kpk && term <= 1.4e-17f * (1.0f + T)) break;
+    }
   }
-  double res = log1p(T) - lgamma(v + 1.0);
-  if (v != 0.0) res = fma(v, log(0.5 * x), res);
+  n = __reduce_max_sync(0xffffffffu, n);
+  const double y = 0.25 * x * x;
+  double A = 1.0, B = 1.0;
+  double kd = (double)n;            // one conversion; the loop steps it by -1
+#pragma unroll 1
+  for (int k = n; k >= 1; --k) {
+    const double d = kd * (kd + v);
+    A = fma(d, B, y * A);
+    B *= d;
+    kd -= 1.0;
+  }
+  double res = fm_log(A / B) - lgamma(v + 1.0);
+  if (v != 0.0) res = fma(v, fm_log(0.5 * x), res);
   return res;
 }
 

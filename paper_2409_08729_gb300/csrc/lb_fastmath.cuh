@@ -1,0 +1,65 @@
+// lb_fastmath.cuh -- double-precision exp and log with few FP64 operations.
+//
+// On GB300 the FP64 pipe issues one warp instruction per 16 cycles per SM
+// (1/62 of FP32), and the log-Bessel kernels spend most of it in exp and
+// log.  These are table-driven implementations after P. T. P. Tang
+// ("Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic", ACM TOMS 15(2), 1989; "... of the logarithm
+// function ...", ACM TOMS 16(4), 1990): argument reduction with 128-entry
+// tables (gen_fastmath.py), a short polynomial, and exponent handling with
+// integer instructions, which run on other pipes.  About 12 (exp) and 15
+// (log) FP64 operations per call.  Both fall back to the libm function
+// outside their fast range (|y| >= 708 for exp; zero, negative, subnormal,
+// infinite or NaN arguments for log).  Accuracy is checked against the
+// double-double oracle and against CUDA's exp/log in the test suite.
+#pragma once
+
+#include "fastmath_tables.h"
+
+namespace lb {
+
+__device__ __forceinline__ double fm_exp(double y) {
+  if (!(fabs(y) < 708.0)) return exp(y);
+  const double shifter = 6755399441055744.0;                 // 1.5 * 2^52
+  const double t = fma(y, LB_FM_INV_L, shifter);             // rint(y * 128 / ln 2) in the low bits
+  const int k = __double2loint(t);
+  const double kd = t - shifter;
+  double r = fma(-kd, LB_FM_L_HI, y);                        // exact: kd * L_HI has <= 51 bits
+  r = fma(-kd, LB_FM_L_LO, r);                               // |r| <= ln2/256
+  // e^r - 1 = r + r^2 (1/2 + r (1/6 + r (1/24 + r/120)))   (|r|^6/720 < 6e-19)
+  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r * r, r);
+  const int j = k & 127;
+  const int m = k >> 7;
+  const double th = __ldg(lb_fm_exp_hi + j);
+  const double res = fma(th, p, __ldg(lb_fm_exp_lo + j)) + th;   // 2^(j/128) e^r
+  return __hiloint2double(__double2hiint(res) + (m << 20), __double2loint(res));
+}
+
+__device__ __forceinline__ double fm_log(double z) {
+  const int hi = __double2hiint(z);
+  const int lo = __double2loint(z);
+  if (hi < 0x00100000 || hi >= 0x7ff00000) return log(z);   // <= 0 (sign bit), subnormal, inf, NaN
+  const int j = (hi >> 13) & 127;                           // top 7 bits of the significand
+  const int e = ((hi >> 20) - 1023) + (j >= LB_FM_LOG_JSPLIT ? 1 : 0);
+  const double mant = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);   // in [1, 2)
+  const double r = fma(mant, __ldg(lb_fm_log_c + j), -1.0);                   // |r| < 2^-7
+  // log1p(r) = r - r^2 (1/2 - r (1/3 - r (1/4 - ... - r (1/8 - r/9))))   (|r|^9/9 < 2e-20)
+  double q = fma(r, -1.0 / 9.0, 1.0 / 8.0);
+  q = fma(q, -r, 1.0 / 7.0);
+  q = fma(q, -r, 1.0 / 6.0);
+  q = fma(q, -r, 1.0 / 5.0);
+  q = fma(q, -r, 0.25);
+  q = fma(q, -r, 1.0 / 3.0);
+  q = fma(q, -r, 0.5);
+  const double lp = fma(-r * r, q, r);
+  // e as a double with one add: 2^52 + 2^31 + e, minus the offset
+  const double ed = __hiloint2double(0x43300000, (int)(0x80000000u + (unsigned int)e)) - 4503601774854144.0;
+  const double small = fma(ed, LB_FM_LN2_LO, __ldg(lb_fm_log_lo + j)) + lp;
+  const double big = fma(ed, LB_FM_LN2_HI, __ldg(lb_fm_log_hi + j));        // exact product
+  return big + small;
+}
+
+}  // namespace lb

@@ -46,18 +46,7 @@ __device__ __forceinline__ double warp_sum(double a) {
 
 // log of the prefactor sqrt(pi) e^{-x} / (Gamma(v+1/2) (2x)^v)
 __device__ __forceinline__ double kint_prefactor(double v, double x) {
-  return kHalfLogPi - lgamma(v + 0.5) - fma(v, log(2.0 * x), x);
-}
-
-// log of one g-node term: log(w) + log g(u) with log u tabulated
-__device__ __forceinline__ double kint_g_term(double logw, double logu, double beta, double logbeta,
-                                              double vm, double tx) {
-  const double ub = exp(beta * logu);
-  return logw + logbeta - ub + fma(vm, log(tx + ub), 7.0 * logu);
-}
-// log of one h-node term in the variable s: c + (v - 1/2)(log s + log(s + 2x))
-__device__ __forceinline__ double kint_h_term(double c, double s, double y, double vm, double tx) {
-  return fma(vm, y + log(s + tx), c);
+  return kHalfLogPi - lgamma(v + 0.5) - fma(v, fm_log(2.0 * x), x);
 }
 
 // Warp-cooperative Gauss-rule evaluation; every lane returns the same value.
@@ -68,7 +57,7 @@ __device__ __forceinline__ double kint_h_term(double c, double s, double y, doub
 template <bool DX>
 __device__ __forceinline__ double kint_gauss(double v, double x, int lane) {
   const double beta = 16.0 / (2.0 * v + 1.0);
-  const double logbeta = log(beta);
+  const double logbeta = fm_log(beta);
   const double vm = v - 0.5, tx = 2.0 * x;
   // g piece
   const double* gu;
@@ -93,8 +82,8 @@ __device__ __forceinline__ double kint_gauss(double v, double x, int lane) {
     A[k] = 0.0;
     if (32 * k < ng) {
       const double logu = __ldg(gu + j);
-      const double ub = exp(beta * logu);
-      L[k] = __ldg(gw + j) + logbeta - ub + fma(vm, log(tx + ub), 7.0 * logu);
+      const double ub = fm_exp(beta * logu);
+      L[k] = __ldg(gw + j) + logbeta - ub + fma(vm, fm_log(tx + ub), 7.0 * logu);
       if (DX) A[k] = 1.0 / (tx + ub);
     }
   }
@@ -105,7 +94,7 @@ __device__ __forceinline__ double kint_gauss(double v, double x, int lane) {
     A[4 + k] = 0.0;
     if (j < nh) {
       const double sj = __ldg(hs + j);
-      L[4 + k] = fma(vm, __ldg(hy + j) + log(sj + tx), __ldg(hc + j));
+      L[4 + k] = fma(vm, __ldg(hy + j) + fm_log(sj + tx), __ldg(hc + j));
       if (DX) A[4 + k] = 1.0 / (sj + tx);
     }
   }
@@ -118,7 +107,7 @@ __device__ __forceinline__ double kint_gauss(double v, double x, int lane) {
   for (int k = 0; k < 6; ++k) {
     const bool live = (k < 4) ? (32 * k < ng) : (32 * (k - 4) < nh && L[k] > -INFINITY);
     if (live) {
-      const double e = exp(L[k] - m);
+      const double e = fm_exp(L[k] - m);
       s0 += e;
       if (DX) s1 = fma(e, A[k], s1);
     }
@@ -128,7 +117,7 @@ __device__ __forceinline__ double kint_gauss(double v, double x, int lane) {
     s1 = warp_sum(s1);
     return (2.0 * v - 1.0) * (s1 / s0);
   }
-  return m + log(s0);
+  return m + fm_log(s0);
 }
 
 // Warp-cooperative log int_0^1 (g + h) du by the paper's Simpson rule (N = 600).

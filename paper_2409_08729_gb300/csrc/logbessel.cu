@@ -26,6 +26,8 @@
 
 #include "logbessel.h"
 #include "lb_kint.cuh"
+#include "lb_expr32.cuh"
+#include "lb_fastmath.cuh"
 
 #define LB_THREADS 256
 #define LB_ITEMS 4
@@ -102,14 +104,21 @@ lb_tiles_kernel(const double* __restrict__ v, int64_t v_stride, const double* __
       }
     }
     __syncthreads();
-    // Expressions evaluated one thread per pair, one region at a time.
+    // Expressions evaluated one thread per pair, one region at a time.  The
+    // loop bound is uniform per warp (some expressions reduce across the
+    // warp); lanes past the end of a list recompute the warp's first entry
+    // and do not store.
+    const int lane = tid & 31;
     for (int r = 0; r < 8; ++r) {
       if (r == R_SPECIAL) continue;
       if (KIND == KIND_K && r == R_FALLBACK) continue;
       const int c = counts[r];
-      for (int j = tid; j < c; j += LB_THREADS) {
-        const int li = lists[r][j];
-        out[t0 + li] = eval_region<KIND, DX>(r, sv[li], sx[li], mode);
+      for (int j0 = tid - lane; j0 < c; j0 += LB_THREADS) {
+        const int j = j0 + lane;
+        const bool ok = j < c;
+        const int li = lists[r][ok ? j : j0];
+        const double val = eval_region<KIND, DX>(r, sv[li], sx[li], mode);
+        if (ok) out[t0 + li] = val;
       }
     }
     if (KIND == KIND_K) {
@@ -156,6 +165,120 @@ lb_kint_kernel(const double* __restrict__ v, int64_t v_stride, const double* __r
   }
 }
 
+// FP32-mixed form: same pipeline on float inputs (lb_expr32.cuh).
+template <int KIND>
+__device__ __forceinline__ float eval_region32(int r, float v, float x) {
+  switch (r) {
+    case R_MU20: return mu_expr32<KIND, 20>(v, x);
+    case R_U13: return u_expr32<KIND, 13>(v, x);
+    case R_MU3: return mu_expr32<KIND, 3>(v, x);
+    case R_U4: return u_expr32<KIND, 4>(v, x);
+    case R_U6: return u_expr32<KIND, 6>(v, x);
+    case R_U9: return u_expr32<KIND, 9>(v, x);
+    default: return (KIND == KIND_I) ? series_log_i32(v, x) : __int_as_float(0x7fc00000);
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(LB_THREADS)
+lb_tiles_kernel32(const float* __restrict__ v, int64_t v_stride, const float* __restrict__ x,
+                  float* __restrict__ out, int64_t n, int mode, int forced_region,
+                  unsigned int* __restrict__ qcount, uint32_t* __restrict__ queue) {
+  __shared__ float sv[LB_TILE];
+  __shared__ float sx[LB_TILE];
+  __shared__ uint16_t lists[8][LB_TILE];
+  __shared__ int counts[8];
+  __shared__ unsigned int qbase;
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t t0 = tile * LB_TILE;
+    if (tid < 8) counts[tid] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < LB_ITEMS; ++it) {
+      const int li = it * LB_THREADS + tid;
+      const int64_t i = t0 + li;
+      if (i < n) {
+        float vi = v[i * v_stride];
+        const float xi = x[i];
+        if (KIND == KIND_K) vi = fabsf(vi);
+        float sp;
+        if (special_value32<KIND>(vi, xi, &sp)) {
+          out[i] = sp;
+        } else {
+          sv[li] = vi;
+          sx[li] = xi;
+          const int r = forced_region >= 0 ? forced_region : classify32(vi, xi, mode);
+          const int pos = atomicAdd(&counts[r], 1);
+          lists[r][pos] = (uint16_t)li;
+        }
+      }
+    }
+    __syncthreads();
+    for (int r = 0; r < 8; ++r) {
+      if (r == R_SPECIAL) continue;
+      if (KIND == KIND_K && r == R_FALLBACK) continue;
+      const int c = counts[r];
+      for (int j = tid; j < c; j += LB_THREADS) {
+        const int li = lists[r][j];
+        out[t0 + li] = eval_region32<KIND>(r, sv[li], sx[li]);
+      }
+    }
+    if (KIND == KIND_K) {
+      const int c = counts[R_FALLBACK];
+      if (c > 0) {
+        if (tid == 0) qbase = atomicAdd(qcount, (unsigned int)c);
+        __syncthreads();
+        const unsigned int b = qbase;
+        for (int j = tid; j < c; j += LB_THREADS) queue[b + j] = (uint32_t)(t0 + lists[R_FALLBACK][j]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(LB_THREADS, 2)
+lb_kint_kernel32(const float* __restrict__ v, int64_t v_stride, const float* __restrict__ x,
+                 float* __restrict__ out, const unsigned int* __restrict__ qcount,
+                 const uint32_t* __restrict__ queue) {
+  const unsigned int cnt = *qcount;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = warp * 32; b < (int64_t)cnt; b += nwarps * 32) {
+    const int64_t q = b + lane;
+    const bool valid = q < (int64_t)cnt;
+    const int64_t idx = valid ? (int64_t)queue[q] : 0;
+    const float vi = valid ? fabsf(v[idx * v_stride]) : 1.0f;
+    const float xi = valid ? x[idx] : 1.0f;
+    const float pre = kint_prefactor32(vi, xi);
+    const int m = (int)min((int64_t)32, (int64_t)cnt - b);
+    float mine = 0.0f;
+    for (int e = 0; e < m; ++e) {
+      const float ve = __shfl_sync(0xffffffffu, vi, e);
+      const float xe = __shfl_sync(0xffffffffu, xi, e);
+      const float li = kint_gauss32(ve, xe, lane);
+      if (lane == e) mine = li;
+    }
+    if (valid) out[idx] = pre + mine;
+  }
+}
+
+template <int KIND>
+__global__ void lb_classify_kernel32(const float* __restrict__ v, int64_t v_stride,
+                                     const float* __restrict__ x, uint8_t* __restrict__ reg,
+                                     int64_t n, int mode) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float vi = v[i * v_stride];
+    const float xi = x[i];
+    if (KIND == KIND_K) vi = fabsf(vi);
+    float sp;
+    reg[i] = special_value32<KIND>(vi, xi, &sp) ? (uint8_t)R_SPECIAL : (uint8_t)classify32(vi, xi, mode);
+  }
+}
+
 template <int KIND>
 __global__ void lb_classify_kernel(const double* __restrict__ v, int64_t v_stride,
                                    const double* __restrict__ x, uint8_t* __restrict__ reg,
@@ -193,6 +316,26 @@ __global__ void lb_vmf_finish_kernel(const double* __restrict__ kappa, double* _
 }
 
 __global__ void lb_set_scalar_kernel(double* p, double value) { *p = value; }
+
+// Elementwise exp/log for checking the table-driven implementations against
+// the libm ones: which = 0 fm_exp, 1 fm_log, 2 exp, 3 log; and CUDA's
+// special-purpose Bessel functions of orders 0 and 1 (the comparison system
+// of paper Sec. 6.1): 4 log(cyl_bessel_i0), 5 log(cyl_bessel_i1).
+__global__ void lb_math_kernel(int which, const double* __restrict__ in, double* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = in[i];
+    double r;
+    switch (which) {
+      case 0: r = fm_exp(a); break;
+      case 1: r = fm_log(a); break;
+      case 2: r = exp(a); break;
+      case 3: r = log(a); break;
+      case 4: r = log(cyl_bessel_i0(a)); break;
+      default: r = log(cyl_bessel_i1(a)); break;
+    }
+    out[i] = r;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // host side
@@ -297,7 +440,6 @@ lb_status validate(lb_dtype dtype, const void* v, int64_t v_stride, const void* 
   if (mode < 0 || mode > 2) return fail(LB_EINVAL, "unknown mode %s%lld", "", (long long)mode);
   if (v_stride != 0 && v_stride != 1) return fail(LB_EINVAL, "v_stride must be 0 or 1 (got %s%lld)", "", (long long)v_stride);
   if (n > 0 && (!v || !x || !out)) return fail(LB_EINVAL, "NULL %s pointer with n = %lld", !v ? "v" : (!x ? "x" : "out"), (long long)n);
-  if (dtype == LB_F32) return fail(LB_ENOTSUP, "%sFP32 path not built in this version", "", 0);
   return LB_OK;
 }
 
@@ -350,6 +492,52 @@ lb_status run(const double* v, int64_t v_stride, const double* x, double* out, i
   return status;
 }
 
+lb_status run32(int kind, const float* v, int64_t v_stride, const float* x, float* out, int64_t n, int mode,
+                int forced_region, cudaStream_t st) {
+  const int sms = sm_count();
+  if (mode != MODE_TIGHT && kind == KIND_K && (forced_region < 0 || forced_region == R_FALLBACK))
+    return fail(LB_ENOTSUP, "%sthe FP32 K integral is implemented for LB_TIGHT only", "", 0);
+  if (kind == KIND_I || (forced_region >= 0 && forced_region != R_FALLBACK)) {
+    const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
+    const int grid = (int)(ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4);
+    return launch(PS_TILES, st, [&] {
+      if (kind == KIND_I)
+        lb_tiles_kernel32<KIND_I><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region, nullptr, nullptr);
+      else
+        lb_tiles_kernel32<KIND_K><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region, nullptr, nullptr);
+    });
+  }
+  const int64_t cap = n < kChunk ? n : kChunk;
+  void* ws = nullptr;
+  const size_t bytes = 256 + (size_t)cap * sizeof(uint32_t);
+  if (cudaMallocAsync(&ws, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LB_ENOMEM, "cudaMallocAsync of %s%lld bytes failed", "", (long long)bytes);
+  }
+  unsigned int* qcount = (unsigned int*)ws;
+  uint32_t* queue = (uint32_t*)((char*)ws + 256);
+  lb_status status = LB_OK;
+  for (int64_t c0 = 0; c0 < n && status == LB_OK; c0 += kChunk) {
+    const int64_t cn = (n - c0) < kChunk ? (n - c0) : kChunk;
+    if (cudaMemsetAsync(qcount, 0, sizeof(unsigned int), st) != cudaSuccess) { status = check_launch("cudaMemsetAsync"); break; }
+    const float* vc = v + c0 * v_stride;
+    const float* xc = x + c0;
+    float* oc = out + c0;
+    const int64_t ntiles = (cn + LB_TILE - 1) / LB_TILE;
+    const int grid = (int)(ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4);
+    status = launch(PS_TILES, st, [&] {
+      lb_tiles_kernel32<KIND_K><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount, queue);
+    });
+    if (status != LB_OK) break;
+    const int kgrid = sms * 8;
+    status = launch(PS_KINT, st, [&] {
+      lb_kint_kernel32<<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
+    });
+  }
+  cudaFreeAsync(ws, st);
+  return status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -358,6 +546,9 @@ lb_status logbessel_i(lb_dtype dtype, const void* v, int64_t v_stride, const voi
                       int64_t n, lb_mode mode, void* cuda_stream) {
   lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
   if (s != LB_OK || n == 0) return s;
+  if (dtype == LB_F32)
+    return run32(KIND_I, (const float*)v, v_stride, (const float*)x, (float*)out, n, (int)mode, -1,
+                 (cudaStream_t)cuda_stream);
   return run<KIND_I, false>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
                             (cudaStream_t)cuda_stream);
 }
@@ -366,6 +557,9 @@ lb_status logbessel_k(lb_dtype dtype, const void* v, int64_t v_stride, const voi
                       int64_t n, lb_mode mode, void* cuda_stream) {
   lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
   if (s != LB_OK || n == 0) return s;
+  if (dtype == LB_F32)
+    return run32(KIND_K, (const float*)v, v_stride, (const float*)x, (float*)out, n, (int)mode, -1,
+                 (cudaStream_t)cuda_stream);
   return run<KIND_K, false>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
                             (cudaStream_t)cuda_stream);
 }
@@ -374,6 +568,7 @@ lb_status logbessel_i_dx(lb_dtype dtype, const void* v, int64_t v_stride, const 
                          int64_t n, lb_mode mode, void* cuda_stream) {
   lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
   if (s != LB_OK || n == 0) return s;
+  if (dtype != LB_F64) return fail(LB_ENOTSUP, "%sthe derivatives are implemented for LB_F64 only", "", 0);
   return run<KIND_I, true>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
                            (cudaStream_t)cuda_stream);
 }
@@ -382,6 +577,7 @@ lb_status logbessel_k_dx(lb_dtype dtype, const void* v, int64_t v_stride, const 
                          int64_t n, lb_mode mode, void* cuda_stream) {
   lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
   if (s != LB_OK || n == 0) return s;
+  if (dtype != LB_F64) return fail(LB_ENOTSUP, "%sthe derivatives are implemented for LB_F64 only", "", 0);
   if (mode != LB_TIGHT) return fail(LB_ENOTSUP, "%sd/dx log K is implemented for LB_TIGHT only", "", 0);
   return run<KIND_K, true>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
                            (cudaStream_t)cuda_stream);
@@ -395,6 +591,13 @@ lb_status logbessel_classify(int kind, lb_dtype dtype, const void* v, int64_t v_
   if (s != LB_OK || n == 0) return s;
   const int grid = sm_count() * 4;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (dtype == LB_F32)
+    return launch(PS_CLASSIFY, st, [&] {
+      if (kind == 0)
+        lb_classify_kernel32<KIND_I><<<grid, LB_THREADS, 0, st>>>((const float*)v, v_stride, (const float*)x, region_out, n, (int)mode);
+      else
+        lb_classify_kernel32<KIND_K><<<grid, LB_THREADS, 0, st>>>((const float*)v, v_stride, (const float*)x, region_out, n, (int)mode);
+    });
   return launch(PS_CLASSIFY, st, [&] {
     if (kind == 0)
       lb_classify_kernel<KIND_I><<<grid, LB_THREADS, 0, st>>>((const double*)v, v_stride, (const double*)x, region_out, n, (int)mode);
@@ -412,6 +615,8 @@ lb_status logbessel_eval_region(int kind, lb_dtype dtype, const void* v, int64_t
   lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
   if (s != LB_OK || n == 0) return s;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (dtype == LB_F32)
+    return run32(kind, (const float*)v, v_stride, (const float*)x, (float*)out, n, (int)mode, region, st);
   if (kind == 0)
     return run<KIND_I, false>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, region, st);
   return run<KIND_K, false>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, region, st);
@@ -423,6 +628,7 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
   if (deriv != 0 && deriv != 1) return fail(LB_EINVAL, "deriv must be 0 or 1 (got %s%lld)", "", (long long)deriv);
   lb_status s = validate(dtype, kappa, 0, kappa, out, n, 0);
   if (s != LB_OK || n == 0) return s;
+  if (dtype != LB_F64) return fail(LB_ENOTSUP, "%sthe vMF log-normaliser is implemented for LB_F64 only", "", 0);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   double* nu = nullptr;
   if (cudaMallocAsync(&nu, sizeof(double), st) != cudaSuccess) {
@@ -444,6 +650,15 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
   }
   cudaFreeAsync(nu, st);
   return s;
+}
+
+lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t n, void* cuda_stream) {
+  if (which < 0 || which > 5) return fail(LB_EINVAL, "which must be 0..5 (got %s%lld)", "", (long long)which);
+  if (n < 0 || (n > 0 && (!in || !out))) return fail(LB_EINVAL, "bad buffer or size %s%lld", "", (long long)n);
+  if (n == 0) return LB_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int grid = sm_count() * 4;
+  return launch(PS_AUX, st, [&] { lb_math_kernel<<<grid, LB_THREADS, 0, st>>>(which, in, out, n); });
 }
 
 const char* logbessel_last_error(void) { return g_last_error.c_str(); }

@@ -1,25 +1,31 @@
 """Algorithmic FP64 work of the evaluation kernels, for roofline reporting.
 
-Work is counted in FP64 pipe slots: one slot per double add, multiply or fused
-multiply-add the method performs, and for each library call (exp, log,
-lgamma, division, square root) the number of DFMA issue slots that one call
-occupies on this GPU, i.e. (DFMA throughput) / (call throughput), both
-measured with all SMs busy by the microbenchmarks of fp64_peak.cu.  FLOPs are
-reported as 2 x slots (an FMA counts two).
+Work is counted in FP64 pipe slots: one slot per double add, multiply, fused
+multiply-add or compare the method performs, and for each library call
+(division, square root, reciprocal square root, lgamma) the number of DFMA
+issue slots one call occupies on this GPU, i.e. (DFMA throughput) / (call
+throughput), both measured with all SMs busy by logbessel_measure_fp64.  The
+table-driven exp and log of lb_fastmath.cuh are counted by their operations
+(12 and 13).  FLOP = 2 x slots (an FMA counts two).
 
-The counts follow the expressions as written in lb_expr.cuh and lb_kint.cuh;
-they are the method's arithmetic, not the instructions a profiler counts.
+The counts follow the code paths of lb_expr.cuh and lb_kint.cuh (tight mode,
+FP64).  Term counts are the per-pair counts of the single-precision pre-pass;
+the kernels run the maximum over each warp, so the real work is slightly
+higher than counted here.
 """
 import numpy as np
 
-# DFMA-slot cost of one call, from the measured throughput ratios on GB300
-# (DFMA 0.597 T/s; exp 31.4 G/s, log 17.1 G/s, div 58.2 G/s, sqrt 58.1 G/s,
-# lgamma 20.7 G/s on arguments 2..4).
-SLOT_EXP = 19.0
-SLOT_LOG = 34.9
+# DFMA-slot cost of one CUDA call (measured throughput ratios on GB300:
+# DFMA 0.597 T/s; div 58.2 G/s, sqrt 58.1 G/s, lgamma 20.7 G/s)
 SLOT_DIV = 10.3
 SLOT_SQRT = 10.3
+SLOT_RSQRT = 10.3
 SLOT_LGAMMA = 28.9
+# library exp/log (lb_fastmath.cuh), operation counts
+SLOT_EXP = 12.0
+SLOT_LOG = 15.0
+
+REGION_K = {0: 20, 1: 13, 4: 3, 5: 4, 6: 6, 7: 9}   # region id -> number of expansion terms
 
 
 def kint_rule(v, x):
@@ -34,54 +40,80 @@ def kint_rule(v, x):
 def kint_slots(v, x):
     """FP64 slots of one K-integral evaluation per pair (tight Gauss rule)."""
     ng, nh = kint_rule(v, x)
-    # g node: beta*log u, exp, 3 adds, log, (v-1/2)*log + 7 log u (mul + fma),
-    #         then exp(L - m): subtract, exp, accumulate
-    g_node = 1 + SLOT_EXP + 3 + SLOT_LOG + 2 + 1 + SLOT_EXP + 1
-    # h node: s + 2x, log, + y, fma, then subtract, exp, accumulate
-    h_node = 1 + SLOT_LOG + 1 + 1 + 1 + SLOT_EXP + 1
-    # per pair: beta (div), log beta, 2 small ops, final log and adds, the
-    # warp reductions (5 adds), and the prefactor (lgamma, log, 3 ops)
-    per_pair = SLOT_DIV + SLOT_LOG + 2 + SLOT_LOG + 2 + 5 + SLOT_LGAMMA + SLOT_LOG + 3
+    # g node: beta*log u, exp, 3 adds, log, fma(v-1/2, log, 7 log u) + mul,
+    #         then exp(L - m): subtract, exp, accumulate, max
+    g_node = 1 + SLOT_EXP + 3 + SLOT_LOG + 2 + 1 + SLOT_EXP + 1 + 1
+    # h node: s + 2x, log, + y, fma, then subtract, exp, accumulate, max
+    h_node = 1 + SLOT_LOG + 1 + 1 + 1 + SLOT_EXP + 1 + 1
+    # per pair: beta (div), log beta, 2 ops, final log, warp reductions (10),
+    # prefactor (lgamma, log, 3 ops)
+    per_pair = SLOT_DIV + SLOT_LOG + 2 + SLOT_LOG + 10 + SLOT_LGAMMA + SLOT_LOG + 3
     return ng * g_node + nh * h_node + per_pair
 
 
-def mu20_slots():
-    # 20 terms: subtract, two multiplies, one fma; plus 1/(8x), rsqrt/sqrt, product, log, add
-    return 20 * 4 + SLOT_DIV + SLOT_SQRT + 2 + SLOT_LOG + 1
+def mu_terms(v, x, K=20):
+    """Terms summed by the mu_K expression (single-precision pre-pass rule)."""
+    v = np.asarray(v, dtype=np.float32)
+    x = np.asarray(x, dtype=np.float32)
+    mu = 4.0 * v * v
+    inv8x = np.float32(1.0) / (np.float32(8.0) * x)
+    t = np.ones_like(x)
+    n = np.full(x.shape, K, dtype=np.int64)
+    done = np.zeros(x.shape, dtype=bool)
+    for k in range(1, K + 1):
+        t = np.where(done, t, t * (mu - np.float32((2 * k - 1) ** 2)) * inv8x / np.float32(k))
+        hit = ~done & (np.abs(t) < 1.4e-17)
+        n = np.where(hit, k, n)
+        done |= hit
+    return n
 
 
-def u13_slots():
-    # x/v, fma+sqrt, 1/r, t*t, t/v, 91 Horner fmas of P_k + 13 in q, eta (add, div, log, add),
-    # tail (multiplies, rsqrt, log, fma)
-    return (SLOT_DIV + 1 + SLOT_SQRT + SLOT_DIV + 1 + SLOT_DIV + 91 + 13
-            + 1 + SLOT_DIV + SLOT_LOG + 1 + 3 + SLOT_SQRT + SLOT_LOG + 1)
+def mu_slots(v, x, K=20):
+    # per term: subtract, 2 multiplies, fma; plus 1/(8x), 4v^2, rsqrt or sqrt, product, log, add
+    return mu_terms(v, x, K) * 4 + SLOT_DIV + 2 + SLOT_RSQRT + 2 + SLOT_LOG + 1
+
+
+def u_slots(K):
+    # x/v, fma+sqrt, 1/r, t*t, t/v, sum_k (k+1) Horner fmas of P_k, K in q,
+    # eta (add, div, log, add), tail (3 multiplies, rsqrt, multiply, log, fma)
+    horner = sum(k for k in range(1, K + 1)) + K
+    return (SLOT_DIV + 1 + SLOT_SQRT + SLOT_DIV + 1 + SLOT_DIV + horner
+            + 1 + SLOT_DIV + SLOT_LOG + 1 + 3 + SLOT_RSQRT + 1 + SLOT_LOG + 1)
 
 
 def series_terms(v, x):
-    """Number of series terms the I fallback sums for each pair (same stopping rule)."""
-    v = np.asarray(v, dtype=np.float64)
-    x = np.asarray(x, dtype=np.float64)
-    y = 0.25 * x * x
-    kpk = 0.5 * (np.sqrt(x * x + v * v) - v)
+    """Terms the I power series sums for each pair (single-precision pre-pass rule)."""
+    v = np.asarray(v, dtype=np.float32)
+    x = np.asarray(x, dtype=np.float32)
+    y = np.float32(0.25) * x * x
+    kpk = np.float32(0.5) * (np.sqrt(x * x + v * v) - v)
     term = np.ones_like(x)
     T = np.zeros_like(x)
+    n = np.ones(x.shape, dtype=np.int64)
     done = np.zeros(x.shape, dtype=bool)
-    count = np.zeros(x.shape, dtype=np.int64)
-    k = 1.0
-    for _ in range(400):
+    for k in range(1, 91):
         active = ~done
         if not active.any():
             break
-        term = np.where(active, term * y / (k * (k + v)), term)
+        term = np.where(active, term * y / (np.float32(k) * (np.float32(k) + v)), term)
         T = np.where(active, T + term, T)
-        count += active
-        done |= active & (k > kpk) & (term <= 1.3877787807814457e-17 * (1.0 + T))
-        k += 1.0
-    return count
+        n = np.where(active, k, n)
+        done |= active & (np.float32(k) > kpk) & (term <= np.float32(1.4e-17) * (1 + T))
+    return n
 
 
 def series_slots(v, x):
-    # per term: divide, 2 multiplies/adds for k(k+v), multiply, add; plus sqrt for the
-    # peak, lgamma, log1p, log, fma
+    # per term: k + v, multiply, fma, multiply, int->double; plus A/B, log, lgamma, log(x/2), fma
     n = series_terms(v, x)
-    return n * (SLOT_DIV + 4) + SLOT_SQRT + 3 + SLOT_LGAMMA + SLOT_LOG + SLOT_LOG + 2
+    return n * 5 + SLOT_DIV + SLOT_LOG + SLOT_LGAMMA + SLOT_LOG + 3
+
+
+def region_slots(region, v, x):
+    """FP64 slots of the per-thread expressions (tiles kernel) for pairs of one region."""
+    if region == 0:
+        return mu_slots(v, x)
+    if region in REGION_K and region != 4:
+        return np.full(np.shape(x), u_slots(REGION_K[region]), dtype=np.float64)
+    if region == 4:
+        return mu_slots(v, x, K=3)
+    return series_slots(v, x)

@@ -1,0 +1,69 @@
+"""Table-driven exp/log of the kernels against the double-double oracle and
+against CUDA's exp/log (ulp distances)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_08729_gb300 import _binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+def _eval(which, a, dev):
+    t = torch.tensor(a, dtype=torch.float64, device=dev)
+    out = torch.empty_like(t)
+    B.check(B.lib().logbessel_math_eval(which, t.data_ptr(), out.data_ptr(), t.numel(),
+                                        torch.cuda.current_stream(dev).cuda_stream))
+    return out.cpu().numpy()
+
+
+def _ulps(a, b):
+    ia = a.view(np.int64).astype(object)
+    ib = b.view(np.int64).astype(object)
+    return np.array([abs(int(x) - int(y)) for x, y in zip(ia, ib)])
+
+
+def _ref(fn, a):
+    out = np.empty_like(a)
+    for i, v in enumerate(a):
+        h, l = fn(float(v))
+        out[i] = h + l
+    return out
+
+
+def test_exp(cuda):
+    rng = np.random.default_rng(1)
+    a = np.concatenate([rng.uniform(-707, 707, 4000), rng.uniform(-1, 1, 2000), rng.uniform(-1e-3, 1e-3, 500),
+                        [0.0, -0.0, 1e-300, -745.0, 709.7, 800.0, -800.0, np.inf, -np.inf, np.nan]])
+    got = _eval(0, a, cuda)
+    lib = _eval(2, a, cuda)
+    fin = np.abs(a) < 700
+    ref = _ref(oracle.dd_exp, a[fin])
+    u = _ulps(got[fin], ref)
+    assert u.max() <= 1, u.max()
+    assert _ulps(got[fin], lib[fin]).max() <= 2
+    # outside |y| < 708 the libm function is used: identical results
+    fb = ~(np.abs(a) < 708)
+    np.testing.assert_array_equal(got[fb], lib[fb])
+
+
+def test_log(cuda):
+    rng = np.random.default_rng(2)
+    a = np.concatenate([np.exp(rng.uniform(-700, 700, 4000)), rng.uniform(0.5, 2.0, 3000),
+                        1.0 + rng.uniform(-1e-6, 1e-6, 500), [1.0, 2.0, 0.5, np.sqrt(2.0), 1.4142135, 1.4142136]])
+    got = _eval(1, a, cuda)
+    lib = _eval(3, a, cuda)
+    ref = _ref(oracle.dd_log, a)
+    u = _ulps(got, ref)
+    big = np.abs(ref) > 1e-300
+    assert u[big].max() <= 1, u[big].max()
+    assert _ulps(got, lib).max() <= 2
+    assert np.max(np.abs(got - ref)) <= 2.3e-16 * np.maximum(1.0, np.abs(ref)).max()
+
+
+def test_log_fallbacks(cuda):
+    a = np.array([0.0, -1.0, 5e-324, 1e-310, np.inf, np.nan])
+    got = _eval(1, a, cuda)
+    lib = _eval(3, a, cuda)
+    np.testing.assert_array_equal(got, lib)

@@ -262,3 +262,17 @@ def test_error_metric():
     e = oracle.rel_err(got, ref, np.ones(5))
     assert e[0] == pytest.approx(1e-15, rel=1e-3) and e[1] == 0 and e[2] == 0 and e[3] == 0
     assert e[4] == np.inf
+
+
+@pytest.mark.parametrize("v", [0.0, 0.3, 2.5, 1e5])
+@pytest.mark.parametrize("x", [1e-300, 1e-200, 1e-6])
+def test_extreme_small_arguments(v, x):
+    """K at arguments where x cosh t overflows inside the integration range
+    (the integrand is 0 there), and I at tiny x; mpmath at 60 digits."""
+    with mp.workdps(60):
+        rk = mp.log(mp.besselk(v, mp.mpf(x)))
+        ri = mp.log(mp.besseli(v, mp.mpf(x)))
+    lk = oracle.log_k([v], [x])[0]
+    li = oracle.log_i([v], [x])[0]
+    assert abs(lk - rk) <= 2e-16 * max(1, abs(rk))
+    assert abs(li - ri) <= 2e-16 * max(1, abs(ri))
