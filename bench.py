@@ -151,6 +151,10 @@ def main():
     ap.add_argument("--cpu-per-v", type=int, default=20000, help="oracle sample per order for cpu_baseline")
     ap.add_argument("--ref-per-v", type=int, default=4000, help="oracle sample per order per reference step")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--err-sample", type=int, default=4000, help="oracle-checked outputs per call type")
+    ap.add_argument("--serve-requests", type=int, default=4000,
+                    help="requests in the serving measurement (0 = skip)")
     args = ap.parse_args()
 
     world = _env_int("WORLD_SIZE", 1)
@@ -269,6 +273,67 @@ def main():
                "h2d_bytes_per_step": 2 * n_all * 8, "d2h_bytes_per_step": 4 * n_all * 8}
         del hx, hv, ho, dx, dv
 
+    # ---- sampled accuracy of the timed outputs (FP64) against the oracle ----
+    acc = None
+    if rank == 0 and args.err_sample > 0:
+        import oracle
+        oracle.build()
+        rs = np.random.default_rng(5)
+        idx = rs.integers(0, n_all, args.err_sample)
+        xs = x_all[idx].cpu().numpy()
+        vmix = v_mixed[idx].cpu().numpy()
+        vper = np.asarray(SWEEP_ORDERS)[idx // n1]
+        acc = {}
+        for name, row, vv, kind in (("i_per_order", 0, vper, "i"), ("i_mixed", 1, vmix, "i"),
+                                    ("k_per_order", 2, vper, "k"), ("k_mixed", 3, vmix, "k")):
+            got = outs[row][idx].cpu().numpy()
+            ref = oracle.log_i(vv, xs) if kind == "i" else oracle.log_k(vv, xs)
+            e = oracle.rel_err(got, ref, oracle.error_scale(kind, vv, xs))
+            acc[name] = float(e.max())
+        acc["samples_per_call_type"] = int(args.err_sample)
+
+    # ---- the same sweep in the FP32-mixed form ----
+    fp32 = None
+    if not args.no_fp32:
+        x32 = x_all.float()
+        v32 = v_mixed.float()
+        o32 = torch.empty((4, n_all), dtype=torch.float32, device=dev)
+        ord32 = orders.float()
+
+        def step32():
+            for kind, fn in ((0, L.logbessel_i), (1, L.logbessel_k)):
+                o_per, o_mix = o32[2 * kind], o32[2 * kind + 1]
+                for k in range(nv):
+                    B.check(fn(B.LB_F32, ord32[k:k + 1].data_ptr(), 0, x32[k * n1:(k + 1) * n1].data_ptr(),
+                               o_per[k * n1:(k + 1) * n1].data_ptr(), n1, mode, sp))
+                B.check(fn(B.LB_F32, v32.data_ptr(), 1, x32.data_ptr(), o_mix.data_ptr(), n_all, mode, sp))
+
+        for _ in range(2):
+            step32()
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            step32()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = g0.elapsed_time(g1)
+        fp32 = {"value": evals_per_step * args.steps * world / (ms32 / 1e3) / 1e9, "unit": UNIT,
+                "ms_per_step": ms32 / args.steps, "dtype": "f32 inputs/outputs, FP32-pipe evaluation"}
+        if rank == 0 and args.err_sample > 0:
+            import oracle
+            e_max = 0.0
+            for row, vv, kind in ((1, vmix, "i"), (3, vmix, "k")):
+                got = o32[row][idx].double().cpu().numpy()
+                vf = vv.astype(np.float32).astype(np.float64)
+                xf = xs.astype(np.float32).astype(np.float64)
+                ref = oracle.log_i(vf, xf) if kind == "i" else oracle.log_k(vf, xf)
+                e = oracle.rel_err(got, ref, oracle.error_scale(kind, vf, xf))
+                e_max = max(e_max, float(e.max()))
+            fp32["max_rel_err_mixed_calls"] = e_max
+        del x32, v32, o32
+
     # ---- roofline of the dominant kernel (FP64 pipe) ----
     regions_k = lb.classify("k", v_mixed, x_all).cpu().numpy()
     regions_i = lb.classify("i", v_mixed, x_all).cpu().numpy()
@@ -306,11 +371,16 @@ def main():
             sel = np.flatnonzero(regs == rid)
             tiles_slots += sampled_sum(lambda a, b, r=rid: WM.region_slots(r, a, b), sel, vv)
     work_slots = {"lb_kint_kernel": kint_slots, "lb_tiles_kernel": tiles_slots}
+    # DRAM traffic of the K-integral kernel: 37 B per queued pair (one ncu
+    # capture, profiles/lb_kint_kernel_sweep_small.md), scaled to the pairs of
+    # an average launch; it grows in proportion (per-pair gathers only).
+    kint_pairs_per_launch = (fb_mix.sum() + fb_per.sum()) * args.steps / max(prof["lb_kint_kernel"][0], 1)
+    traffic = {"lb_kint_kernel": 37.0 * kint_pairs_per_launch}
     if name in work_slots:
         work = 2.0 * work_slots[name] * args.steps
         roof = {"bound": "alu", "kernel": name, "achieved": work / (kms / 1e3) / 1e9,
                 "peak": peak_flops / 1e9, "unit": "GFLOP/s", "frac": (work / (kms / 1e3)) / peak_flops,
-                "traffic": None, "launches": nl, "avg_launch_ms": kms / max(ntimed, 1),
+                "traffic": traffic.get(name), "launches": nl, "avg_launch_ms": kms / max(ntimed, 1),
                 "peak_source": "FP64 DFMA rate measured live by logbessel_measure_fp64 (x2 flops/FMA)"}
     other = {k: {"achieved_gflops": 2.0 * w * args.steps / (prof[k][2] / 1e3) / 1e9 if prof.get(k, (0, 0, 0))[2] else None}
              for k, w in work_slots.items()}
@@ -328,6 +398,13 @@ def main():
             "kernels": {k: {"launches": v[0], "ms": v[2], **other.get(k, {})} for k, v in prof.items()},
             "region_mix_mixed_call": mix,
             "fp64_rates": {k: v / 1e9 for k, v in rates.items()}}
+    line["max_rel_err"] = acc
+    line["fp32_mixed"] = fp32
+    if rank == 0 and args.serve_requests > 0:
+        from paper_2409_08729_gb300 import servebench
+        del outs
+        torch.cuda.empty_cache()
+        line["serving"] = servebench.run(n_req=args.serve_requests, seed=0, device=str(dev))
     if rank == 0:
         r, threads, n = time_oracle(args.cpu_per_v)
         line["cpu_baseline"] = {"value": r / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",

@@ -179,6 +179,56 @@ lb_status logbessel_measure_fp64(double* rates, void* cuda_stream);
  */
 lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t n, void* cuda_stream);
 
+/*
+ * Continuous-batching server (serving loop).  Requests of any size arrive
+ * from host threads; a scheduler thread admits them as request slots and
+ * device memory (a fixed arena) free up, copies their inputs to the GPU, and
+ * publishes their tiles to a persistent kernel, which interleaves the tiles
+ * of all resident requests, so requests that arrive while others run overlap
+ * on the device.  Results are copied back into the caller's buffer.
+ *
+ *   arena_bytes  device memory for request buffers (>= 1 MiB); a request
+ *                needs about 3 n elements (v, x, out), rounded to 256 B
+ *   max_slots    requests resident on the device at once (1..4096)
+ *   ctas_per_sm  persistent thread blocks per SM (1..8)
+ *   idle_ms      a thread block with no work for this long exits; the
+ *                scheduler relaunches the kernel when work appears (every
+ *                device-side wait is bounded by it)
+ *
+ * The server runs on the device current at lb_server_create.  v, x, out of
+ * lb_server_submit are HOST pointers (pinned memory lets the copies overlap
+ * with computation); they must stay valid until lb_server_wait returns LB_OK
+ * for the ticket.  kind 0 = log I, 1 = log K; dtype LB_F64 or LB_F32
+ * (FP32-mixed; FP32 K requires LB_TIGHT).  Requests larger than the arena
+ * are rejected with LB_ENOMEM; bad arguments with LB_EINVAL (nothing queued).
+ * lb_server_wait returns LB_ETIMEOUT if the result is not ready in time (the
+ * request stays queued).  Times from lb_server_ticket_info are seconds on a
+ * monotonic clock: submission, admission (copy-in started) and completion
+ * (result in the host buffer).  lb_server_release forgets a finished ticket.
+ * lb_server_destroy stops the kernel and frees everything.  The paper has no
+ * serving component; this is the batched front end of the same kernels.
+ */
+typedef struct lb_server lb_server;
+typedef struct {
+  int64_t arena_bytes;
+  int max_slots;
+  int ctas_per_sm;
+  double idle_ms;
+} lb_server_config;
+
+lb_status lb_server_create(const lb_server_config* cfg, lb_server** server);
+lb_status lb_server_submit(lb_server* server, int kind, lb_dtype dtype, const void* v, int64_t v_stride,
+                           const void* x, void* out, int64_t n, lb_mode mode, long long* ticket);
+lb_status lb_server_wait(lb_server* server, long long ticket, double timeout_s);
+lb_status lb_server_ticket_info(lb_server* server, long long ticket, int* done, double* t_submit,
+                                double* t_admit, double* t_done);
+lb_status lb_server_release(lb_server* server, long long ticket);
+lb_status lb_server_stats(lb_server* server, long long* completed, long long* evals,
+                          long long* kernel_launches, long long* in_flight);
+lb_status lb_server_destroy(lb_server* server);
+/* Message describing the last server failure on the calling thread. */
+const char* lb_server_last_error(void);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* logbessel_last_error(void);
 

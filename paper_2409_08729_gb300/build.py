@@ -9,7 +9,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liblogbessel.so")
 
-SOURCES = ["logbessel.cu", "lb_peaks.cu"]
+SOURCES = ["logbessel.cu", "lb_peaks.cu", "lb_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -77,6 +77,8 @@ def main():
         parts.append("// g piece, Gauss-Legendre on [0,1], %d nodes: log u_j and log w_j" % N)
         parts.append(arr("lb_kq_g%d_logu" % N, [mp.log(a) for a in u]))
         parts.append(arr("lb_kq_g%d_logw" % N, [mp.log(a) for a in w]))
+        parts.append("// log w_j + (n - 1) log u_j with n = 8 (the u^(n-1) factor of g folded in)")
+        parts.append(arr("lb_kq_g%d_c" % N, [mp.log(b) + 7 * mp.log(a) for a, b in zip(u, w)]))
     Y = mp.log(SMAX)
     for N in (32, 48):
         y, w = gauss_legendre01(N)

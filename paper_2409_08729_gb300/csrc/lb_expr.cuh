@@ -35,17 +35,28 @@ enum Mode { MODE_TIGHT = 0, MODE_PAPER_GPU = 1, MODE_PAPER_CPU = 2 };
 // Domain edges (shared convention of the library): returns true and sets *r
 // when (v, x) is an edge case; K callers pass |v|.
 // ---------------------------------------------------------------------------
+// The tests use the IEEE bit patterns (integer instructions): on GB300 a
+// double-precision compare costs as much FP64-pipe time as an FMA.
+__device__ __forceinline__ bool bits_nan(long long b) { return (b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL; }
+__device__ __forceinline__ bool bits_inf(long long b) { return (b & 0x7fffffffffffffffLL) == 0x7ff0000000000000LL; }
+__device__ __forceinline__ bool bits_zero(long long b) { return (b & 0x7fffffffffffffffLL) == 0; }
+__device__ __forceinline__ bool bits_neg(long long b) { return b < 0 && !bits_zero(b); }
+
 template <int KIND>
 __device__ __forceinline__ bool special_value(double v, double x, double* r) {
+  const long long bv = __double_as_longlong(v), bx = __double_as_longlong(x);
+  if ((bv & 0x7ff0000000000000LL) != 0x7ff0000000000000LL && (bx & 0x7ff0000000000000LL) != 0x7ff0000000000000LL &&
+      !bits_neg(bx) && !bits_zero(bx) && (KIND == KIND_K || !bits_neg(bv)))
+    return false;                                   // the common case: finite, x > 0, v >= 0 for I
   if (KIND == KIND_I) {
-    if (isnan(v) || isnan(x) || v < 0.0 || x < 0.0 || (isinf(v) && isinf(x))) { *r = __longlong_as_double(0x7ff8000000000000LL); return true; }
-    if (isinf(x)) { *r = INFINITY; return true; }
-    if (isinf(v)) { *r = -INFINITY; return true; }
-    if (x == 0.0) { *r = (v == 0.0) ? 0.0 : -INFINITY; return true; }
+    if (bits_nan(bv) || bits_nan(bx) || bits_neg(bv) || bits_neg(bx) || (bits_inf(bv) && bits_inf(bx))) { *r = __longlong_as_double(0x7ff8000000000000LL); return true; }
+    if (bits_inf(bx)) { *r = INFINITY; return true; }
+    if (bits_inf(bv)) { *r = -INFINITY; return true; }
+    if (bits_zero(bx)) { *r = bits_zero(bv) ? 0.0 : -INFINITY; return true; }
   } else {
-    if (isnan(v) || isnan(x) || x < 0.0 || (isinf(v) && isinf(x))) { *r = __longlong_as_double(0x7ff8000000000000LL); return true; }
-    if (isinf(x)) { *r = -INFINITY; return true; }
-    if (x == 0.0 || isinf(v)) { *r = INFINITY; return true; }
+    if (bits_nan(bv) || bits_nan(bx) || bits_neg(bx) || (bits_inf(bv) && bits_inf(bx))) { *r = __longlong_as_double(0x7ff8000000000000LL); return true; }
+    if (bits_inf(bx)) { *r = -INFINITY; return true; }
+    if (bits_zero(bx) || bits_inf(bv)) { *r = INFINITY; return true; }
   }
   return false;
 }
@@ -87,10 +98,14 @@ __device__ __forceinline__ bool paper_u13(double v, double x) { return (x > 19.6
 // 0.5113 log x + 0.7939 > log v is replaced by v^2 < 3.24 x, which follows
 // the actual validity limit of the large-argument series (its terms grow like
 // (v^2 / 2x)^k / k!) and needs no logarithm.
+// Threshold compares of non-negative doubles on their bit patterns (same
+// order as the values; integer instructions).
+#define LB_GT(a, c) (__double_as_longlong(a) > __double_as_longlong(c))
+#define LB_LT(a, c) (__double_as_longlong(a) < __double_as_longlong(c))
 __device__ __forceinline__ bool tight_mu20(double v, double x) {
-  return (x > 30.0 && v < 13.6) || (x > 59.6925 && v * v < 3.24 * x);
+  return (LB_GT(x, 30.0) && LB_LT(v, 13.6)) || (LB_GT(x, 59.6925) && v * v < 3.24 * x);
 }
-__device__ __forceinline__ bool tight_u13(double v, double x) { return (x > 25.0 && v > 0.7) || v > 16.0; }
+__device__ __forceinline__ bool tight_u13(double v, double x) { return (LB_GT(x, 25.0) && LB_GT(v, 0.7)) || LB_GT(v, 16.0); }
 
 // With the pairs binned per expression on chip (no warp divergence), the
 // tight dispatch also uses the shorter uniform expansions of the paper's CPU
@@ -99,9 +114,9 @@ __device__ __forceinline__ bool tight_u13(double v, double x) { return (x > 25.0
 __device__ __forceinline__ int classify(double v, double x, int mode) {
   if (mode == MODE_TIGHT) {
     if (tight_mu20(v, x)) return R_MU20;
-    if (v > 230.0) return R_U4;
-    if (v > 70.0) return R_U6;
-    if (v > 28.0) return R_U9;
+    if (LB_GT(v, 230.0)) return R_U4;
+    if (LB_GT(v, 70.0)) return R_U6;
+    if (LB_GT(v, 28.0)) return R_U9;
     if (tight_u13(v, x)) return R_U13;
     return R_FALLBACK;
   }
@@ -147,22 +162,25 @@ __device__ __forceinline__ double mu_expr(double v, double x) {
   }
   n = __reduce_max_sync(0xffffffffu, n);
   const double mu = 4.0 * v * v;
-  const double inv8x = 1.0 / (8.0 * x);
+  const double inv8x = (KIND == KIND_I ? -1.0 : 1.0) / (8.0 * x);     // the sign s folded in
   double P = 1.0;
-  // Unrolled, so (2k-1)^2 and 1/k are constants; terms above n are skipped
-  // by a warp-uniform predicate.
+  // Unrolled, so 1/k and (2k-1)^2/k are constants and each term costs three
+  // FP64 operations: a = mu/k - (2k-1)^2/k, P = 1 + (a s/(8x)) P.  Terms
+  // above n are skipped by a warp-uniform predicate.
 #pragma unroll
   for (int k = K; k >= 1; --k) {
     if (k <= n) {
-      const double odd = (double)((2 * k - 1) * (2 * k - 1));
-      double r = (mu - odd) * (inv8x * (1.0 / (double)k));
-      if (KIND == KIND_I) r = -r;
-      P = fma(r, P, 1.0);
+      const double a = fma(mu, 1.0 / (double)k, -(double)((2 * k - 1) * (2 * k - 1)) / (double)k);
+      P = fma(a * inv8x, P, 1.0);
     }
   }
-  const double S = fabs(P);
-  if (KIND == KIND_I) return x + fm_log(S * rsqrt(kTwoPi * x));
-  return fm_log(S * sqrt(kPi / (2.0 * x))) - x;
+  // log(S / sqrt(2 pi x)) = log(S^2 / (2 pi x)) / 2 and
+  // log(S sqrt(pi / (2x))) = log(S^2 pi / (2x)) / 2, with 1/x = 8 |inv8x|:
+  // no square root needed.
+  const double S2 = P * P;
+  const double ax = fabs(inv8x);
+  if (KIND == KIND_I) return fma(0.5, fm_log(S2 * ax * (8.0 / kTwoPi)), x);
+  return fma(0.5, fm_log(S2 * ax * (4.0 * kPi)), -x);
 }
 
 // P_k(p) of the Debye polynomial u_k(t) = t^k P_k(t^2); k is a compile-time
@@ -217,22 +235,31 @@ __device__ __forceinline__ T debye_Q(int k, T p) {
 // ---------------------------------------------------------------------------
 template <int KIND, int K>
 __device__ __forceinline__ double u_expr(double v, double x) {
-  const double xp = x / v;
-  double r;
-  if (xp < 1e150) r = sqrt(fma(xp, xp, 1.0));
-  else r = xp;                                   // 1 + x'^2 rounds to x'^2
-  const double t = 1.0 / r;
+  const double inv_v = 1.0 / v;
+  const double xp = x * inv_v;
+  double r, t;
+  if (LB_LT(xp, 1e150)) {
+    const double r2 = fma(xp, xp, 1.0);
+    t = rsqrt(r2);                               // t = (1 + x'^2)^-1/2
+    r = r2 * t;
+  } else {
+    r = xp;                                      // 1 + x'^2 rounds to x'^2
+    t = 1.0 / r;
+  }
   const double p = t * t;
-  double q = t / v;
+  double q = t * inv_v;
   if (KIND == KIND_K) q = -q;
   // Horner in q over k = K..1:  S = 1 + q (P_1 + q (P_2 + ... + q P_K))
   double acc = debye_P(K, p);
 #pragma unroll
   for (int k = K - 1; k >= 1; --k) acc = fma(acc, q, debye_P(k, p));
-  const double S = fabs(fma(acc, q, 1.0));
+  const double S = fma(acc, q, 1.0);
   const double eta = r + fm_log(xp / (1.0 + r));
-  if (KIND == KIND_I) return fma(v, eta, fm_log(S * rsqrt(kTwoPi * v * r)));
-  return fma(-v, eta, fm_log(S * sqrt(kPi / (2.0 * v * r))));
+  // log(S / sqrt(2 pi v r)) = log(S^2 t / (2 pi v)) / 2, and for K
+  // log(S sqrt(pi / (2 v r))) = log(S^2 t pi / (2 v)) / 2 (t = 1/r): no root.
+  const double w = S * S * t * inv_v;
+  if (KIND == KIND_I) return fma(v, eta, 0.5 * fm_log(w * (1.0 / kTwoPi)));
+  return fma(-v, eta, 0.5 * fm_log(w * (0.5 * kPi)));
 }
 
 // ---------------------------------------------------------------------------

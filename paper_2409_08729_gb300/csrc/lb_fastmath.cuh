@@ -38,6 +38,44 @@ __device__ __forceinline__ double fm_exp(double y) {
   return __hiloint2double(__double2hiint(res) + (m << 20), __double2loint(res));
 }
 
+// exp(y) for y <= 708 (callers never pass more); y < -708 gives 0.  The range
+// test and the flush use integer instructions only, so no FP64 compare is
+// spent and there is no divergent fall-back path.
+__device__ __forceinline__ double fm_exp_le(double y) {
+  const bool under = (unsigned int)__double2hiint(y) > 0xC0862000u;     // y < -708 (sign bit set)
+  if (under) y = -708.0;
+  const double shifter = 6755399441055744.0;
+  const double t = fma(y, LB_FM_INV_L, shifter);
+  const int k = __double2loint(t);
+  const double kd = t - shifter;
+  double r = fma(-kd, LB_FM_L_HI, y);
+  r = fma(-kd, LB_FM_L_LO, r);
+  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r * r, r);
+  const int j = k & 127;
+  const int m = k >> 7;
+  const double th = __ldg(lb_fm_exp_hi + j);
+  const double res = fma(th, p, __ldg(lb_fm_exp_lo + j)) + th;
+  const double out = __hiloint2double(__double2hiint(res) + (m << 20), __double2loint(res));
+  return under ? 0.0 : out;
+}
+
+// Order-preserving map of a double to an int through its high word (larger
+// double, larger key); key_to_double returns a double within 2^-20
+// (relative) of the original.  Used for warp max reductions on the integer
+// pipe: the maximum only serves as a log-sum-exp shift, where any nearby
+// value is exact.
+__device__ __forceinline__ int order_key(double a) {
+  const int h = __double2hiint(a);
+  return h >= 0 ? h : (h ^ 0x7fffffff);
+}
+__device__ __forceinline__ double key_to_double(int k) {
+  const int h = k >= 0 ? k : (k ^ 0x7fffffff);
+  return __hiloint2double(h, 0);
+}
+
 __device__ __forceinline__ double fm_log(double z) {
   const int hi = __double2hiint(z);
   const int lo = __double2loint(z);

@@ -49,75 +49,91 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
   return kHalfLogPi - lgamma(v + 0.5) - fma(v, fm_log(2.0 * x), x);
 }
 
-// Warp-cooperative Gauss-rule evaluation; every lane returns the same value.
-// All 32 lanes must call it with the same (v, x).
-//   DX = false: log int_0^inf F(s) ds.
-//   DX = true:  d/dx log int_0^inf F(s) ds = (2v - 1) <1/(s + 2x)>_F, the
-//               F-weighted mean over the same nodes (dF/dx = F (2v-1)/(s+2x)).
+// Node counts of the tight rule for one pair, packed as (g count) | (h rule << 8):
+// h rule 0 = Gauss-Legendre in log s with 32 nodes, 1 = with 48, 2 = Gauss-Laguerre 32.
+__device__ __forceinline__ int kint_rule(double v, double x) {
+  const int ng = (v >= 0.9 || x >= 0.25) ? 32 : ((v >= 0.4 || x >= 1e-3) ? 64 : 128);
+  const int hr = (v <= 1.2) ? 0 : ((v <= 5.0) ? 1 : 2);
+  return ng | (hr << 8);
+}
+
+// K integrals of up to 32 pairs by one warp (Gauss rules; lane e holds pair
+// e, all lanes pass valid data).  Per pair, the lanes split the nodes; the
+// log-sum-exp shift is the warp maximum taken on the integer pipe, the sum a
+// warp-shuffle reduction (Eq. "log sum trick").  Everything that is per pair
+// rather than per node (the order-dependent constants, the prefactor, the
+// final logarithm) is computed once per lane for its own pair, not once per
+// pair by all 32 lanes.  Returns, on lane e, log K of pair e (DX = false) or
+// d/dx log K (DX = true: the prefactor derivative -v/x - 1 plus
+// (2v - 1) <1/(s + 2x)>, the F-weighted mean over the nodes, since
+// dF/dx = F (2v - 1)/(s + 2x)).
 template <bool DX>
-__device__ __forceinline__ double kint_gauss(double v, double x, int lane) {
-  const double beta = 16.0 / (2.0 * v + 1.0);
-  const double logbeta = fm_log(beta);
-  const double vm = v - 0.5, tx = 2.0 * x;
-  // g piece
-  const double* gu;
-  const double* gw;
-  int ng;
-  if (v >= 0.9 || x >= 0.25) { gu = lb_kq_g32_logu; gw = lb_kq_g32_logw; ng = 32; }
-  else if (v >= 0.4 || x >= 1e-3) { gu = lb_kq_g64_logu; gw = lb_kq_g64_logw; ng = 64; }
-  else { gu = lb_kq_g128_logu; gw = lb_kq_g128_logw; ng = 128; }
-  // h piece
-  const double *hs, *hy, *hc;
-  int nh;
-  if (v <= 1.2) { hs = lb_kq_hl32_s; hy = lb_kq_hl32_y; hc = lb_kq_hl32_c; nh = 32; }
-  else if (v <= 5.0) { hs = lb_kq_hl48_s; hy = lb_kq_hl48_y; hc = lb_kq_hl48_c; nh = 48; }
-  else { hs = lb_kq_hq32_s; hy = lb_kq_hq32_y; hc = lb_kq_hq32_c; nh = 32; }
-  // Up to 4 g terms and 2 h terms per lane; the node counts are the same on
-  // every lane, so these branches never diverge.
-  double L[6], A[6];
+__device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane) {
+  const double beta_i = 16.0 / (2.0 * vi + 1.0);
+  const double logbeta_i = fm_log(beta_i);
+  const int rule_i = kint_rule(vi, xi);
+  double m_i = 0.0, s0_i = 1.0, s1_i = 0.0;
+  for (int e = 0; e < npairs; ++e) {
+    const double v = __shfl_sync(0xffffffffu, vi, e);
+    const double x = __shfl_sync(0xffffffffu, xi, e);
+    const double beta = __shfl_sync(0xffffffffu, beta_i, e);
+    const double logbeta = __shfl_sync(0xffffffffu, logbeta_i, e);
+    const int rule = __shfl_sync(0xffffffffu, rule_i, e);
+    const int ng = rule & 0xff, hr = rule >> 8;
+    const double vm = v - 0.5, tx = 2.0 * x;
+    const double* gu = ng == 32 ? lb_kq_g32_logu : (ng == 64 ? lb_kq_g64_logu : lb_kq_g128_logu);
+    const double* gc = ng == 32 ? lb_kq_g32_c : (ng == 64 ? lb_kq_g64_c : lb_kq_g128_c);
+    const double* hs = hr == 0 ? lb_kq_hl32_s : (hr == 1 ? lb_kq_hl48_s : lb_kq_hq32_s);
+    const double* hy = hr == 0 ? lb_kq_hl32_y : (hr == 1 ? lb_kq_hl48_y : lb_kq_hq32_y);
+    const double* hc = hr == 0 ? lb_kq_hl32_c : (hr == 1 ? lb_kq_hl48_c : lb_kq_hq32_c);
+    const int nh = hr == 1 ? 48 : 32;
+    double L[6], A[6];
+    int key = (int)0x800fffff;                       // order_key(-inf)
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int j = lane + 32 * k;
-    L[k] = -INFINITY;
-    A[k] = 0.0;
-    if (32 * k < ng) {
-      const double logu = __ldg(gu + j);
-      const double ub = fm_exp(beta * logu);
-      L[k] = __ldg(gw + j) + logbeta - ub + fma(vm, fm_log(tx + ub), 7.0 * logu);
-      if (DX) A[k] = 1.0 / (tx + ub);
+    for (int k = 0; k < 4; ++k) {
+      L[k] = 0.0;
+      A[k] = 0.0;
+      if (32 * k < ng) {                            // g node: log w + 7 log u + log beta - u^beta + (v-1/2) log(2x + u^beta)
+        const int j = lane + 32 * k;
+        const double ub = fm_exp_le(beta * __ldg(gu + j));
+        L[k] = fma(vm, fm_log(tx + ub), __ldg(gc + j) + logbeta) - ub;
+        if (DX) A[k] = 1.0 / (tx + ub);
+        key = max(key, order_key(L[k]));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int j = lane + 32 * k;
+      L[4 + k] = 0.0;
+      A[4 + k] = 0.0;
+      if (j < nh) {                                 // h node: c + (v-1/2)(log s + log(s + 2x))
+        const double sj = __ldg(hs + j);
+        L[4 + k] = fma(vm, __ldg(hy + j) + fm_log(sj + tx), __ldg(hc + j));
+        if (DX) A[4 + k] = 1.0 / (sj + tx);
+        key = max(key, order_key(L[4 + k]));
+      }
+    }
+    const double mm = key_to_double(__reduce_max_sync(0xffffffffu, key));
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const bool live = (k < 4) ? (32 * k < ng) : (lane + 32 * (k - 4) < nh);
+      if (live) {
+        const double t = fm_exp_le(L[k] - mm);
+        s0 += t;
+        if (DX) s1 = fma(t, A[k], s1);
+      }
+    }
+    s0 = warp_sum(s0);
+    if (DX) s1 = warp_sum(s1);
+    if (lane == e) {
+      m_i = mm;
+      s0_i = s0;
+      s1_i = s1;
     }
   }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int j = lane + 32 * k;
-    L[4 + k] = -INFINITY;
-    A[4 + k] = 0.0;
-    if (j < nh) {
-      const double sj = __ldg(hs + j);
-      L[4 + k] = fma(vm, __ldg(hy + j) + fm_log(sj + tx), __ldg(hc + j));
-      if (DX) A[4 + k] = 1.0 / (sj + tx);
-    }
-  }
-  double m = L[0];
-#pragma unroll
-  for (int i = 1; i < 6; ++i) m = fmax(m, L[i]);
-  m = warp_max(m);
-  double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const bool live = (k < 4) ? (32 * k < ng) : (32 * (k - 4) < nh && L[k] > -INFINITY);
-    if (live) {
-      const double e = fm_exp(L[k] - m);
-      s0 += e;
-      if (DX) s1 = fma(e, A[k], s1);
-    }
-  }
-  s0 = warp_sum(s0);
-  if (DX) {
-    s1 = warp_sum(s1);
-    return (2.0 * v - 1.0) * (s1 / s0);
-  }
-  return m + fm_log(s0);
+  if (DX) return -(vi / xi + 1.0) + (2.0 * vi - 1.0) * (s1_i / s0_i);
+  return kint_prefactor(vi, xi) + m_i + fm_log(s0_i);
 }
 
 // Warp-cooperative log int_0^1 (g + h) du by the paper's Simpson rule (N = 600).

@@ -25,122 +25,48 @@
 #include <string>
 
 #include "logbessel.h"
-#include "lb_kint.cuh"
-#include "lb_expr32.cuh"
+#include "lb_tile.cuh"
 #include "lb_fastmath.cuh"
 
-#define LB_THREADS 256
-#define LB_ITEMS 4
-#define LB_TILE (LB_THREADS * LB_ITEMS)
-#define LB_VERSION "0.1.0"
+#define LB_VERSION "0.2.0"
 
 using namespace lb;
 
 namespace {
 
-// ---------------------------------------------------------------------------
-// device helpers
-// ---------------------------------------------------------------------------
-template <int KIND, bool DX>
-__device__ __forceinline__ double eval_region(int r, double v, double x, int mode) {
-  if (DX) {
-    switch (r) {
-      case R_MU20: return mu_dx<KIND, 20>(v, x);
-      case R_U13: return u_dx<KIND, 13>(v, x);
-      case R_MU3: return mu_dx<KIND, 3>(v, x);
-      case R_U4: return u_dx<KIND, 4>(v, x);
-      case R_U6: return u_dx<KIND, 6>(v, x);
-      case R_U9: return u_dx<KIND, 9>(v, x);
-      default: return (KIND == KIND_I) ? series_dx(v, x) : __longlong_as_double(0x7ff8000000000000LL);
-    }
-  }
-  switch (r) {
-    case R_MU20: return mu_expr<KIND, 20>(v, x);
-    case R_U13: return u_expr<KIND, 13>(v, x);
-    case R_MU3: return mu_expr<KIND, 3>(v, x);
-    case R_U4: return u_expr<KIND, 4>(v, x);
-    case R_U6: return u_expr<KIND, 6>(v, x);
-    case R_U9: return u_expr<KIND, 9>(v, x);
-    default: return (KIND == KIND_I) ? series_log_i(v, x) : __longlong_as_double(0x7ff8000000000000LL);
-  }
-}
-
 // Tile kernel: classify, bin per region in shared memory, evaluate the
-// per-thread expressions, queue the K fallback pairs.
-template <int KIND, bool DX>
+// per-thread expressions (lb_tile.cuh); K fallback pairs go to a global queue
+// for lb_kint_kernel.  T = double (FP64) or float (FP32-mixed).
+template <int KIND, bool DX, typename T>
 __global__ void __launch_bounds__(LB_THREADS)
-lb_tiles_kernel(const double* __restrict__ v, int64_t v_stride, const double* __restrict__ x,
-                double* __restrict__ out, int64_t n, int mode, int forced_region,
-                unsigned int* __restrict__ qcount, uint32_t* __restrict__ queue) {
-  __shared__ double sv[LB_TILE];
-  __shared__ double sx[LB_TILE];
-  __shared__ uint16_t lists[8][LB_TILE];
-  __shared__ int counts[8];
-  __shared__ unsigned int qbase;
+lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
+                int64_t n, int mode, int forced_region, unsigned int* __restrict__ qcount,
+                uint32_t* __restrict__ queue) {
+  __shared__ TileShared<T> S;
   const int tid = threadIdx.x;
   const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t t0 = tile * LB_TILE;
-    if (tid < 8) counts[tid] = 0;
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < LB_ITEMS; ++it) {
-      const int li = it * LB_THREADS + tid;
-      const int64_t i = t0 + li;
-      if (i < n) {
-        double vi = v[i * v_stride];
-        const double xi = x[i];
-        if (KIND == KIND_K) vi = fabs(vi);
-        double sp;
-        if (DX ? special_dx<KIND>(vi, xi, &sp) : special_value<KIND>(vi, xi, &sp)) {
-          out[i] = sp;
-        } else {
-          sv[li] = vi;
-          sx[li] = xi;
-          const int r = forced_region >= 0 ? forced_region : classify(vi, xi, mode);
-          const int pos = atomicAdd(&counts[r], 1);
-          lists[r][pos] = (uint16_t)li;
-        }
-      }
-    }
-    __syncthreads();
-    // Expressions evaluated one thread per pair, one region at a time.  The
-    // loop bound is uniform per warp (some expressions reduce across the
-    // warp); lanes past the end of a list recompute the warp's first entry
-    // and do not store.
-    const int lane = tid & 31;
-    for (int r = 0; r < 8; ++r) {
-      if (r == R_SPECIAL) continue;
-      if (KIND == KIND_K && r == R_FALLBACK) continue;
-      const int c = counts[r];
-      for (int j0 = tid - lane; j0 < c; j0 += LB_THREADS) {
-        const int j = j0 + lane;
-        const bool ok = j < c;
-        const int li = lists[r][ok ? j : j0];
-        const double val = eval_region<KIND, DX>(r, sv[li], sx[li], mode);
-        if (ok) out[t0 + li] = val;
-      }
-    }
+    tile_bin<KIND, DX, T>(S, v, v_stride, x, out, t0, n, mode, forced_region);
+    tile_eval<KIND, DX, T>(S, out, t0);
     if (KIND == KIND_K) {
-      const int c = counts[R_FALLBACK];
+      const int c = S.counts[R_FALLBACK];
       if (c > 0) {
-        if (tid == 0) qbase = atomicAdd(qcount, (unsigned int)c);
+        if (tid == 0) S.qbase = atomicAdd(qcount, (unsigned int)c);
         __syncthreads();
-        const unsigned int b = qbase;
-        for (int j = tid; j < c; j += LB_THREADS) queue[b + j] = (uint32_t)(t0 + lists[R_FALLBACK][j]);
+        const unsigned int b = S.qbase;
+        for (int j = tid; j < c; j += LB_THREADS) queue[b + j] = (uint32_t)(t0 + S.lists[R_FALLBACK][j]);
       }
     }
     __syncthreads();
   }
 }
 
-// K integral: one warp per queued pair; the 32 pairs of a batch share the
-// per-pair prefactor work (each lane computes one prefactor).
-template <bool GAUSS, bool DX>
+// K integral: one warp per queued pair, 32 pairs per warp batch.
+template <bool GAUSS, bool DX, typename T>
 __global__ void __launch_bounds__(LB_THREADS, 2)
-lb_kint_kernel(const double* __restrict__ v, int64_t v_stride, const double* __restrict__ x,
-               double* __restrict__ out, const unsigned int* __restrict__ qcount,
-               const uint32_t* __restrict__ queue) {
+lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
+               const unsigned int* __restrict__ qcount, const uint32_t* __restrict__ queue) {
   const unsigned int cnt = *qcount;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -148,120 +74,12 @@ lb_kint_kernel(const double* __restrict__ v, int64_t v_stride, const double* __r
   for (int64_t b = warp * 32; b < (int64_t)cnt; b += nwarps * 32) {
     const int64_t q = b + lane;
     const bool valid = q < (int64_t)cnt;
-    const int64_t idx = valid ? (int64_t)queue[q] : 0;
-    const double vi = valid ? fabs(v[idx * v_stride]) : 1.0;
-    const double xi = valid ? x[idx] : 1.0;
-    // log-prefactor log(sqrt(pi) e^{-x} / (Gamma(v+1/2) (2x)^v)), or its x-derivative -v/x - 1
-    const double pre = DX ? -(vi / xi + 1.0) : kint_prefactor(vi, xi);
+    const int64_t idx = (int64_t)queue[valid ? q : b];
+    const T vi = fabs(v[idx * v_stride]);
+    const T xi = x[idx];
     const int m = (int)min((int64_t)32, (int64_t)cnt - b);
-    double mine = 0.0;
-    for (int e = 0; e < m; ++e) {
-      const double ve = __shfl_sync(0xffffffffu, vi, e);
-      const double xe = __shfl_sync(0xffffffffu, xi, e);
-      const double li = GAUSS ? kint_gauss<DX>(ve, xe, lane) : kint_log_simpson(ve, xe, lane);
-      if (lane == e) mine = li;
-    }
-    if (valid) out[idx] = pre + mine;
-  }
-}
-
-// FP32-mixed form: same pipeline on float inputs (lb_expr32.cuh).
-template <int KIND>
-__device__ __forceinline__ float eval_region32(int r, float v, float x) {
-  switch (r) {
-    case R_MU20: return mu_expr32<KIND, 20>(v, x);
-    case R_U13: return u_expr32<KIND, 13>(v, x);
-    case R_MU3: return mu_expr32<KIND, 3>(v, x);
-    case R_U4: return u_expr32<KIND, 4>(v, x);
-    case R_U6: return u_expr32<KIND, 6>(v, x);
-    case R_U9: return u_expr32<KIND, 9>(v, x);
-    default: return (KIND == KIND_I) ? series_log_i32(v, x) : __int_as_float(0x7fc00000);
-  }
-}
-
-template <int KIND>
-__global__ void __launch_bounds__(LB_THREADS)
-lb_tiles_kernel32(const float* __restrict__ v, int64_t v_stride, const float* __restrict__ x,
-                  float* __restrict__ out, int64_t n, int mode, int forced_region,
-                  unsigned int* __restrict__ qcount, uint32_t* __restrict__ queue) {
-  __shared__ float sv[LB_TILE];
-  __shared__ float sx[LB_TILE];
-  __shared__ uint16_t lists[8][LB_TILE];
-  __shared__ int counts[8];
-  __shared__ unsigned int qbase;
-  const int tid = threadIdx.x;
-  const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t t0 = tile * LB_TILE;
-    if (tid < 8) counts[tid] = 0;
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < LB_ITEMS; ++it) {
-      const int li = it * LB_THREADS + tid;
-      const int64_t i = t0 + li;
-      if (i < n) {
-        float vi = v[i * v_stride];
-        const float xi = x[i];
-        if (KIND == KIND_K) vi = fabsf(vi);
-        float sp;
-        if (special_value32<KIND>(vi, xi, &sp)) {
-          out[i] = sp;
-        } else {
-          sv[li] = vi;
-          sx[li] = xi;
-          const int r = forced_region >= 0 ? forced_region : classify32(vi, xi, mode);
-          const int pos = atomicAdd(&counts[r], 1);
-          lists[r][pos] = (uint16_t)li;
-        }
-      }
-    }
-    __syncthreads();
-    for (int r = 0; r < 8; ++r) {
-      if (r == R_SPECIAL) continue;
-      if (KIND == KIND_K && r == R_FALLBACK) continue;
-      const int c = counts[r];
-      for (int j = tid; j < c; j += LB_THREADS) {
-        const int li = lists[r][j];
-        out[t0 + li] = eval_region32<KIND>(r, sv[li], sx[li]);
-      }
-    }
-    if (KIND == KIND_K) {
-      const int c = counts[R_FALLBACK];
-      if (c > 0) {
-        if (tid == 0) qbase = atomicAdd(qcount, (unsigned int)c);
-        __syncthreads();
-        const unsigned int b = qbase;
-        for (int j = tid; j < c; j += LB_THREADS) queue[b + j] = (uint32_t)(t0 + lists[R_FALLBACK][j]);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(LB_THREADS, 2)
-lb_kint_kernel32(const float* __restrict__ v, int64_t v_stride, const float* __restrict__ x,
-                 float* __restrict__ out, const unsigned int* __restrict__ qcount,
-                 const uint32_t* __restrict__ queue) {
-  const unsigned int cnt = *qcount;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t b = warp * 32; b < (int64_t)cnt; b += nwarps * 32) {
-    const int64_t q = b + lane;
-    const bool valid = q < (int64_t)cnt;
-    const int64_t idx = valid ? (int64_t)queue[q] : 0;
-    const float vi = valid ? fabsf(v[idx * v_stride]) : 1.0f;
-    const float xi = valid ? x[idx] : 1.0f;
-    const float pre = kint_prefactor32(vi, xi);
-    const int m = (int)min((int64_t)32, (int64_t)cnt - b);
-    float mine = 0.0f;
-    for (int e = 0; e < m; ++e) {
-      const float ve = __shfl_sync(0xffffffffu, vi, e);
-      const float xe = __shfl_sync(0xffffffffu, xi, e);
-      const float li = kint_gauss32(ve, xe, lane);
-      if (lane == e) mine = li;
-    }
-    if (valid) out[idx] = pre + mine;
+    const T val = kint_warp_batch<DX, T>(vi, xi, m, lane, GAUSS);
+    if (valid) out[idx] = val;
   }
 }
 
@@ -446,96 +264,70 @@ lb_status validate(lb_dtype dtype, const void* v, int64_t v_stride, const void* 
 // Largest chunk handled with one queue: the queue holds 32-bit offsets.
 const int64_t kChunk = (int64_t)1 << 26;
 
-template <int KIND, bool DX>
-lb_status run(const double* v, int64_t v_stride, const double* x, double* out, int64_t n, int mode,
-              int forced_region, cudaStream_t st) {
+// Enqueue the evaluation of n pairs.  The K fallback goes through a queue
+// of 32-bit pair offsets in scratch memory (qcount: one counter, queue:
+// min(n, chunk) entries), processed chunk by chunk; `scratch` supplies it,
+// or, when NULL, it comes from the stream-ordered allocator.
+template <int KIND, bool DX, typename T>
+lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, int mode, int forced_region,
+                   cudaStream_t st, void* scratch, int64_t chunk) {
   const int sms = sm_count();
+  const int64_t ntiles_all = (n + LB_TILE - 1) / LB_TILE;
   if (KIND == KIND_I || (forced_region >= 0 && forced_region != R_FALLBACK)) {
-    const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
-    const int grid = (int)(ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4);
+    const int grid = (int)(ntiles_all < (int64_t)sms * 4 ? ntiles_all : (int64_t)sms * 4);
     return launch(PS_TILES, st, [&] {
-      lb_tiles_kernel<KIND, DX><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region, nullptr, nullptr);
+      lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region,
+                                                                 nullptr, nullptr);
     });
   }
-  const int64_t cap = n < kChunk ? n : kChunk;
-  void* ws = nullptr;
-  const size_t bytes = 256 + (size_t)cap * sizeof(uint32_t);
-  cudaError_t e = cudaMallocAsync(&ws, bytes, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(LB_ENOMEM, "cudaMallocAsync of %s%lld bytes failed", "", (long long)bytes);
+  if (sizeof(T) == 4 && mode != MODE_TIGHT)
+    return fail(LB_ENOTSUP, "%sthe FP32 K integral is implemented for LB_TIGHT only", "", 0);
+  void* ws = scratch;
+  if (!ws) {
+    const int64_t cap = n < chunk ? n : chunk;
+    const size_t bytes = 256 + (size_t)cap * sizeof(uint32_t);
+    if (cudaMallocAsync(&ws, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LB_ENOMEM, "cudaMallocAsync of %s%lld bytes failed", "", (long long)bytes);
+    }
   }
   unsigned int* qcount = (unsigned int*)ws;
   uint32_t* queue = (uint32_t*)((char*)ws + 256);
   lb_status status = LB_OK;
-  for (int64_t c0 = 0; c0 < n && status == LB_OK; c0 += kChunk) {
-    const int64_t cn = (n - c0) < kChunk ? (n - c0) : kChunk;
+  for (int64_t c0 = 0; c0 < n && status == LB_OK; c0 += chunk) {
+    const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
     if (cudaMemsetAsync(qcount, 0, sizeof(unsigned int), st) != cudaSuccess) { status = check_launch("cudaMemsetAsync"); break; }
-    const double* vc = v + c0 * v_stride;
-    const double* xc = x + c0;
-    double* oc = out + c0;
+    const T* vc = v + c0 * v_stride;
+    const T* xc = x + c0;
+    T* oc = out + c0;
     const int64_t ntiles = (cn + LB_TILE - 1) / LB_TILE;
     const int grid = (int)(ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4);
     status = launch(PS_TILES, st, [&] {
-      lb_tiles_kernel<KIND, DX><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount, queue);
+      lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount, queue);
     });
     if (status != LB_OK) break;
     const int kgrid = sms * 8;
     status = launch(PS_KINT, st, [&] {
       if (mode == MODE_TIGHT)
-        lb_kint_kernel<true, DX><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
+        lb_kint_kernel<true, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
       else
-        lb_kint_kernel<false, false><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
+        lb_kint_kernel<false, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
     });
   }
-  cudaFreeAsync(ws, st);
+  if (!scratch) cudaFreeAsync(ws, st);
   return status;
+}
+
+template <int KIND, bool DX>
+lb_status run(const double* v, int64_t v_stride, const double* x, double* out, int64_t n, int mode,
+              int forced_region, cudaStream_t st) {
+  return run_impl<KIND, DX, double>(v, v_stride, x, out, n, mode, forced_region, st, nullptr, kChunk);
 }
 
 lb_status run32(int kind, const float* v, int64_t v_stride, const float* x, float* out, int64_t n, int mode,
                 int forced_region, cudaStream_t st) {
-  const int sms = sm_count();
-  if (mode != MODE_TIGHT && kind == KIND_K && (forced_region < 0 || forced_region == R_FALLBACK))
-    return fail(LB_ENOTSUP, "%sthe FP32 K integral is implemented for LB_TIGHT only", "", 0);
-  if (kind == KIND_I || (forced_region >= 0 && forced_region != R_FALLBACK)) {
-    const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
-    const int grid = (int)(ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4);
-    return launch(PS_TILES, st, [&] {
-      if (kind == KIND_I)
-        lb_tiles_kernel32<KIND_I><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region, nullptr, nullptr);
-      else
-        lb_tiles_kernel32<KIND_K><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region, nullptr, nullptr);
-    });
-  }
-  const int64_t cap = n < kChunk ? n : kChunk;
-  void* ws = nullptr;
-  const size_t bytes = 256 + (size_t)cap * sizeof(uint32_t);
-  if (cudaMallocAsync(&ws, bytes, st) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(LB_ENOMEM, "cudaMallocAsync of %s%lld bytes failed", "", (long long)bytes);
-  }
-  unsigned int* qcount = (unsigned int*)ws;
-  uint32_t* queue = (uint32_t*)((char*)ws + 256);
-  lb_status status = LB_OK;
-  for (int64_t c0 = 0; c0 < n && status == LB_OK; c0 += kChunk) {
-    const int64_t cn = (n - c0) < kChunk ? (n - c0) : kChunk;
-    if (cudaMemsetAsync(qcount, 0, sizeof(unsigned int), st) != cudaSuccess) { status = check_launch("cudaMemsetAsync"); break; }
-    const float* vc = v + c0 * v_stride;
-    const float* xc = x + c0;
-    float* oc = out + c0;
-    const int64_t ntiles = (cn + LB_TILE - 1) / LB_TILE;
-    const int grid = (int)(ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4);
-    status = launch(PS_TILES, st, [&] {
-      lb_tiles_kernel32<KIND_K><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount, queue);
-    });
-    if (status != LB_OK) break;
-    const int kgrid = sms * 8;
-    status = launch(PS_KINT, st, [&] {
-      lb_kint_kernel32<<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
-    });
-  }
-  cudaFreeAsync(ws, st);
-  return status;
+  if (kind == KIND_I) return run_impl<KIND_I, false, float>(v, v_stride, x, out, n, mode, forced_region, st, nullptr, kChunk);
+  return run_impl<KIND_K, false, float>(v, v_stride, x, out, n, mode, forced_region, st, nullptr, kChunk);
 }
 
 }  // namespace

@@ -5,8 +5,8 @@ multiply-add or compare the method performs, and for each library call
 (division, square root, reciprocal square root, lgamma) the number of DFMA
 issue slots one call occupies on this GPU, i.e. (DFMA throughput) / (call
 throughput), both measured with all SMs busy by logbessel_measure_fp64.  The
-table-driven exp and log of lb_fastmath.cuh are counted by their operations
-(12 and 13).  FLOP = 2 x slots (an FMA counts two).
+table-driven exp and log of lb_fastmath.cuh are counted the same way.
+FLOP = 2 x slots (an FMA counts two).
 
 The counts follow the code paths of lb_expr.cuh and lb_kint.cuh (tight mode,
 FP64).  Term counts are the per-pair counts of the single-precision pre-pass;
@@ -21,9 +21,11 @@ SLOT_DIV = 10.3
 SLOT_SQRT = 10.3
 SLOT_RSQRT = 10.3
 SLOT_LGAMMA = 28.9
-# library exp/log (lb_fastmath.cuh), operation counts
-SLOT_EXP = 12.0
-SLOT_LOG = 15.0
+# library exp/log (lb_fastmath.cuh): measured the same way (DFMA 627 G/s;
+# fm_exp 41.2 G/s, fm_log 33.3 G/s, less the one extra operation per call of
+# the throughput loop)
+SLOT_EXP = 14.2
+SLOT_LOG = 17.8
 
 REGION_K = {0: 20, 1: 13, 4: 3, 5: 4, 6: 6, 7: 9}   # region id -> number of expansion terms
 
@@ -40,14 +42,13 @@ def kint_rule(v, x):
 def kint_slots(v, x):
     """FP64 slots of one K-integral evaluation per pair (tight Gauss rule)."""
     ng, nh = kint_rule(v, x)
-    # g node: beta*log u, exp, 3 adds, log, fma(v-1/2, log, 7 log u) + mul,
-    #         then exp(L - m): subtract, exp, accumulate, max
-    g_node = 1 + SLOT_EXP + 3 + SLOT_LOG + 2 + 1 + SLOT_EXP + 1 + 1
-    # h node: s + 2x, log, + y, fma, then subtract, exp, accumulate, max
-    h_node = 1 + SLOT_LOG + 1 + 1 + 1 + SLOT_EXP + 1 + 1
-    # per pair: beta (div), log beta, 2 ops, final log, warp reductions (10),
-    # prefactor (lgamma, log, 3 ops)
-    per_pair = SLOT_DIV + SLOT_LOG + 2 + SLOT_LOG + 10 + SLOT_LGAMMA + SLOT_LOG + 3
+    # g node: beta*log u, exp, add, log, add, fma, subtract; then exp(L - m), accumulate
+    g_node = 1 + SLOT_EXP + 1 + SLOT_LOG + 1 + 1 + 1 + 1 + SLOT_EXP + 1
+    # h node: s + 2x, log, + y, fma; then subtract, exp, accumulate
+    h_node = 1 + SLOT_LOG + 1 + 1 + 1 + SLOT_EXP + 1
+    # per pair (once per lane of its batch): beta (div), log beta, prefactor
+    # (lgamma, log, 3 ops), final log; the warp sum (5 adds, all lanes)
+    per_pair = SLOT_DIV + SLOT_LOG + SLOT_LGAMMA + SLOT_LOG + 3 + SLOT_LOG + 2 + 5
     return ng * g_node + nh * h_node + per_pair
 
 
@@ -69,16 +70,16 @@ def mu_terms(v, x, K=20):
 
 
 def mu_slots(v, x, K=20):
-    # per term: subtract, 2 multiplies, fma; plus 1/(8x), 4v^2, rsqrt or sqrt, product, log, add
-    return mu_terms(v, x, K) * 4 + SLOT_DIV + 2 + SLOT_RSQRT + 2 + SLOT_LOG + 1
+    # per term: fma, multiply, fma; plus 4v^2, 1/(8x), S^2 and two products, log, fma
+    return mu_terms(v, x, K) * 3 + 2 + SLOT_DIV + 3 + SLOT_LOG + 1
 
 
 def u_slots(K):
-    # x/v, fma+sqrt, 1/r, t*t, t/v, sum_k (k+1) Horner fmas of P_k, K in q,
-    # eta (add, div, log, add), tail (3 multiplies, rsqrt, multiply, log, fma)
+    # 1/v, x/v, fma, rsqrt, r = r2 t, t*t, t/v, sum_k k Horner fmas of P_k, K in q,
+    # eta (add, div, log, add), tail (3 multiplies, log, 2 multiplies, fma)
     horner = sum(k for k in range(1, K + 1)) + K
-    return (SLOT_DIV + 1 + SLOT_SQRT + SLOT_DIV + 1 + SLOT_DIV + horner
-            + 1 + SLOT_DIV + SLOT_LOG + 1 + 3 + SLOT_RSQRT + 1 + SLOT_LOG + 1)
+    return (SLOT_DIV + 1 + 1 + SLOT_RSQRT + 1 + 1 + 1 + horner
+            + 1 + SLOT_DIV + SLOT_LOG + 1 + 3 + SLOT_LOG + 3)
 
 
 def series_terms(v, x):
