@@ -97,6 +97,29 @@ lb_status logbessel_k(lb_dtype dtype, const void* v, int64_t v_stride, const voi
                       int64_t n, lb_mode mode, void* cuda_stream);
 
 /*
+ * log K_v(x) like logbessel_k (FP64 only), but without allocating any device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot let a library allocate, such as code that runs under a device
+ * memory budget fixed in advance, latency-critical loops where an allocation
+ * may block or fail at the wrong moment, or frameworks whose own allocator
+ * must own all device memory.
+ *
+ * The K fallback pairs are queued in a fixed scratch array that the library
+ * defines in device global memory: 4 MiB plus 256 bytes, resident on every
+ * GPU that loads the library until the process exits.  Hence at most
+ * 1048576 pairs per call; a larger n returns LB_EINVAL with a message and
+ * launches nothing.  The first call on a device looks up the scratch
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture on the device.  Every call shares the one
+ * array and clears its counter on the stream: calls whose work overlaps on
+ * the GPU (different streams, or concurrent host threads) race and must be
+ * serialized by the caller.  Other arguments, results and errors as in
+ * logbessel_k; LB_ENOTSUP for LB_F32.
+ */
+lb_status logbessel_k_noalloc(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                              int64_t n, lb_mode mode, void* cuda_stream);
+
+/*
  * d/dx log I_v(x) = I'_v(x) / I_v(x) and d/dx log K_v(x) = K'_v(x) / K_v(x):
  * the adjoint of logbessel_i / logbessel_k, computed by differentiating each
  * region's expression term by term with the same dispatch (the paper lists

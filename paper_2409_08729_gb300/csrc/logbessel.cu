@@ -330,6 +330,38 @@ lb_status run32(int kind, const float* v, int64_t v_stride, const float* x, floa
   return run_impl<KIND_K, false, float>(v, v_stride, x, out, n, mode, forced_region, st, nullptr, kChunk);
 }
 
+// Fixed scratch for logbessel_k_noalloc: the queue counter (first 256
+// bytes) and the queue of the K fallback pairs, for at most
+// LB_NOALLOC_MAX_PAIRS pairs per call.  It lives in the module's global
+// memory for as long as the library is loaded, on every device that loads it.
+#define LB_NOALLOC_MAX_PAIRS (1 << 20)
+static __device__ __align__(256) uint32_t lb_noalloc_scratch[64 + LB_NOALLOC_MAX_PAIRS];
+
+// Device address of lb_noalloc_scratch on the current device, looked up once
+// per device (the host-side name of a __device__ array is only a stand-in).
+void* noalloc_scratch_address() {
+  static std::mutex mu;
+  static void* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    g_last_error = "logbessel_k_noalloc: no usable current device";
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, lb_noalloc_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g_last_error = std::string("logbessel_k_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+      return nullptr;
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
 }  // namespace
 
 extern "C" {
@@ -373,6 +405,19 @@ lb_status logbessel_k_dx(lb_dtype dtype, const void* v, int64_t v_stride, const 
   if (mode != LB_TIGHT) return fail(LB_ENOTSUP, "%sd/dx log K is implemented for LB_TIGHT only", "", 0);
   return run<KIND_K, true>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
                            (cudaStream_t)cuda_stream);
+}
+
+lb_status logbessel_k_noalloc(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                              int64_t n, lb_mode mode, void* cuda_stream) {
+  lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
+  if (s != LB_OK || n == 0) return s;
+  if (dtype != LB_F64) return fail(LB_ENOTSUP, "%slogbessel_k_noalloc supports LB_F64 only", "", 0);
+  if (n > LB_NOALLOC_MAX_PAIRS)
+    return fail(LB_EINVAL, "%slogbessel_k_noalloc takes at most 1048576 pairs per call (got %lld)", "", (long long)n);
+  void* scratch = noalloc_scratch_address();
+  if (!scratch) return LB_ECUDA;
+  return run_impl<KIND_K, false, double>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode,
+                                         -1, (cudaStream_t)cuda_stream, scratch, LB_NOALLOC_MAX_PAIRS);
 }
 
 lb_status logbessel_classify(int kind, lb_dtype dtype, const void* v, int64_t v_stride,
