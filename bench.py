@@ -237,7 +237,8 @@ def main():
         ms = float(t.item())
     value = evals_per_step * args.steps * world / (ms / 1e3) / 1e9
 
-    # ---- end to end: pinned host inputs -> device -> host results, each step ----
+    # ---- end to end: the same step through logbessel_host on pinned host
+    # buffers (copy-in, evaluation and copy-out of chunks overlap inside) ----
     e2e = None
     if not args.no_e2e:
         hx = torch.empty(n_all, dtype=torch.float64, pin_memory=True)
@@ -245,33 +246,36 @@ def main():
         hx.copy_(x_all)
         hv.copy_(v_mixed)
         ho = torch.empty((4, n_all), dtype=torch.float64, pin_memory=True)
-        dx = torch.empty_like(x_all)
-        dv = torch.empty_like(v_mixed)
-        # one untimed pass
-        dx.copy_(hx, non_blocking=True); dv.copy_(hv, non_blocking=True); step(dx, dv, outs)
-        ho.copy_(outs, non_blocking=True)
-        torch.cuda.synchronize()
+        hord = torch.tensor(SWEEP_ORDERS, dtype=torch.float64).pin_memory()
+
+        def step_host():
+            for fn in (0, 1):
+                o_per, o_mix = ho[2 * fn], ho[2 * fn + 1]
+                for k in range(nv):
+                    B.check(L.logbessel_host(fn, B.LB_F64, hord[k:k + 1].data_ptr(), 0,
+                                             hx[k * n1:(k + 1) * n1].data_ptr(),
+                                             o_per[k * n1:(k + 1) * n1].data_ptr(), n1, mode, 0))
+                B.check(L.logbessel_host(fn, B.LB_F64, hv.data_ptr(), 1, hx.data_ptr(), o_mix.data_ptr(), n_all,
+                                         mode, 0))
+
+        step_host()
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
+        t0h = time.perf_counter()
         for _ in range(args.steps):
-            dx.copy_(hx, non_blocking=True)
-            dv.copy_(hv, non_blocking=True)
-            step(dx, dv, outs)
-            ho.copy_(outs, non_blocking=True)
-        f1.record(stream)
+            step_host()
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1)
+        ems = (time.perf_counter() - t0h) * 1e3
         if pg:
             t = torch.tensor([ems], dtype=torch.float64, device=dev)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             ems = float(t.item())
         e2e = {"value": evals_per_step * args.steps * world / (ems / 1e3) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * n_all * 8, "d2h_bytes_per_step": 4 * n_all * 8}
-        del hx, hv, ho, dx, dv
+               "h2d_bytes_per_step": 2 * (nv * 8 + n1 * 8 * nv + 2 * n_all * 8),
+               "d2h_bytes_per_step": 4 * n_all * 8,
+               "api": "logbessel_host (C ABI, pinned host buffers, synchronous per call)"}
+        del hx, hv, ho
 
     # ---- sampled accuracy of the timed outputs (FP64) against the oracle ----
     acc = None

@@ -147,6 +147,22 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
                               int deriv, void* cuda_stream);
 
 /*
+ * The same evaluations on HOST buffers, end to end: fn = 0 log I, 1 log K,
+ * 2 d/dx log I, 3 d/dx log K.  v, x, out are host pointers (pinned memory
+ * lets the copies overlap with the computation; pageable memory works but
+ * copies synchronously).  The pairs are processed in chunks of `chunk`
+ * (0 = 8M pairs; at most 2^26) through three device buffers on three
+ * internal streams, so the copy-in of one chunk, the evaluation of the
+ * previous one and the copy-out of the one before overlap.  The call
+ * returns when every result is in `out` (it synchronizes).  Device buffers
+ * come from the stream-ordered allocator and are released before return.
+ * Errors as for the device entry points; LB_ENOTSUP for derivatives in FP32
+ * or the K derivative outside LB_TIGHT.
+ */
+lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                         int64_t n, lb_mode mode, int64_t chunk);
+
+/*
  * Region id of every pair under the dispatch of `mode` (Table "input
  * ranges"; Algorithm 1 and the GPU subset of Sec. 4.3).  kind = 0 for I,
  * 1 for K (K classifies |v|).  region_out is a device array of n uint8_t.

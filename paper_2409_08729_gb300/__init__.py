@@ -14,7 +14,7 @@ from . import _binding
 from ._binding import LogBesselError, MODES, REGIONS
 from .build import build_library
 
-__all__ = ["log_i", "log_k", "log_i_dx", "log_k_dx", "classify", "eval_region", "LogBesselError", "MODES", "REGIONS",
+__all__ = ["log_i", "log_k", "log_i_dx", "log_k_dx", "host_eval", "classify", "eval_region", "LogBesselError", "MODES", "REGIONS",
            "build_library", "version"]
 
 
@@ -127,6 +127,42 @@ def log_i_dx(v, x, mode="tight", out=None):
 def log_k_dx(v, x, mode="tight", out=None):
     """d/dx log K_v(x) = K'_v(x)/K_v(x) elementwise."""
     return _call("logbessel_k_dx", v, x, mode, out)
+
+
+_HOST_FN = {"log_i": 0, "log_k": 1, "log_i_dx": 2, "log_k_dx": 3}
+
+
+def host_eval(fn, v, x, out=None, mode="tight", chunk=0):
+    """End-to-end evaluation on host arrays (numpy, or CPU tensors; pinned
+    memory overlaps the copies with the computation).  fn is 'log_i',
+    'log_k', 'log_i_dx' or 'log_k_dx'; v is one order or an array like x."""
+    import numpy as np
+    if isinstance(x, torch.Tensor):
+        xa = x
+        dt = x.dtype
+        n = x.numel()
+        xp = x.data_ptr()
+        va = v if isinstance(v, torch.Tensor) else torch.tensor([float(v)], dtype=dt)
+        vp, vs = va.data_ptr(), (0 if va.numel() == 1 else 1)
+        if out is None:
+            out = torch.empty_like(x)
+        op = out.data_ptr()
+        code = _dtype_code(dt)
+        keep = (xa, va, out)
+    else:
+        xa = np.ascontiguousarray(x)
+        if xa.dtype not in (np.float32, np.float64):
+            xa = xa.astype(np.float64)
+        va = np.ascontiguousarray(np.atleast_1d(np.asarray(v, dtype=xa.dtype)))
+        if out is None:
+            out = np.empty_like(xa)
+        n, xp, vp, op = xa.size, xa.ctypes.data, va.ctypes.data, out.ctypes.data
+        vs = 0 if va.size == 1 else 1
+        code = _binding.LB_F64 if xa.dtype == np.float64 else _binding.LB_F32
+        keep = (xa, va, out)
+    _binding.check(_binding.lib().logbessel_host(_HOST_FN[fn], code, vp, vs, xp, op, n, MODES[mode], int(chunk)))
+    del keep
+    return out
 
 
 def classify(kind, v, x, mode="tight"):

@@ -498,6 +498,77 @@ lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t 
   return launch(PS_AUX, st, [&] { lb_math_kernel<<<grid, LB_THREADS, 0, st>>>(which, in, out, n); });
 }
 
+lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
+                         int64_t n, lb_mode mode, int64_t chunk) {
+  if (fn < 0 || fn > 3) return fail(LB_EINVAL, "fn must be 0..3 (got %s%lld)", "", (long long)fn);
+  lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
+  if (s != LB_OK || n == 0) return s;
+  if (chunk <= 0) chunk = (int64_t)1 << 23;
+  if (chunk > kChunk) chunk = kChunk;
+  if ((fn >= 2 && dtype != LB_F64) || (fn == 3 && mode != LB_TIGHT))
+    return fail(LB_ENOTSUP, "%sthe derivatives are implemented for LB_F64 (and LB_TIGHT for K) only", "", 0);
+  const size_t es = dtype == LB_F64 ? 8 : 4;
+  const int64_t nbuf = 3;                         // copy-in, compute and copy-out of three chunks overlap
+  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_in[3] = {}, ev_comp[3] = {}, ev_out[3] = {};
+  char* dbuf = nullptr;
+  const int64_t cap = n < chunk ? n : chunk;
+  const size_t vbytes = (size_t)(v_stride ? cap : 1) * es, xbytes = (size_t)cap * es;
+  const size_t slot = ((vbytes + 255) & ~(size_t)255) + 2 * ((xbytes + 255) & ~(size_t)255);
+  bool ok = true;
+  for (int i = 0; i < 3 && ok; ++i) ok = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < 3 && ok; ++i)
+    ok = cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev_out[i], cudaEventDisableTiming) == cudaSuccess;
+  if (ok) ok = cudaMallocAsync((void**)&dbuf, slot * nbuf, st[1]) == cudaSuccess &&
+               cudaStreamSynchronize(st[1]) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    s = fail(LB_ENOMEM, "%slogbessel_host: stream, event or buffer allocation failed", "", 0);
+  }
+  for (int64_t c0 = 0, i = 0; ok && s == LB_OK && c0 < n; c0 += chunk, ++i) {
+    const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
+    const int b = (int)(i % nbuf);
+    char* dv = dbuf + b * slot;
+    char* dx = dv + ((vbytes + 255) & ~(size_t)255);
+    char* dout = dx + ((xbytes + 255) & ~(size_t)255);
+    if (i >= nbuf) cudaStreamWaitEvent(st[0], ev_out[b], 0);          // slot b's results are out
+    const char* hv = (const char*)v + (v_stride ? c0 * (int64_t)es : 0);
+    cudaMemcpyAsync(dv, hv, (size_t)(v_stride ? cn : 1) * es, cudaMemcpyHostToDevice, st[0]);
+    cudaMemcpyAsync(dx, (const char*)x + c0 * (int64_t)es, (size_t)cn * es, cudaMemcpyHostToDevice, st[0]);
+    cudaEventRecord(ev_in[b], st[0]);
+    cudaStreamWaitEvent(st[1], ev_in[b], 0);
+    if (dtype == LB_F32) {
+      s = run32(fn == 0 ? KIND_I : KIND_K, (const float*)dv, v_stride, (const float*)dx, (float*)dout, cn, (int)mode, -1, st[1]);
+    } else {
+      switch (fn) {
+        case 0: s = run<KIND_I, false>((const double*)dv, v_stride, (const double*)dx, (double*)dout, cn, (int)mode, -1, st[1]); break;
+        case 1: s = run<KIND_K, false>((const double*)dv, v_stride, (const double*)dx, (double*)dout, cn, (int)mode, -1, st[1]); break;
+        case 2: s = run<KIND_I, true>((const double*)dv, v_stride, (const double*)dx, (double*)dout, cn, (int)mode, -1, st[1]); break;
+        default: s = run<KIND_K, true>((const double*)dv, v_stride, (const double*)dx, (double*)dout, cn, (int)mode, -1, st[1]); break;
+      }
+    }
+    cudaEventRecord(ev_comp[b], st[1]);
+    cudaStreamWaitEvent(st[2], ev_comp[b], 0);
+    cudaMemcpyAsync((char*)out + c0 * (int64_t)es, dout, (size_t)cn * es, cudaMemcpyDeviceToHost, st[2]);
+    cudaEventRecord(ev_out[b], st[2]);
+  }
+  for (int i = 0; i < 3; ++i)
+    if (st[i] && cudaStreamSynchronize(st[i]) != cudaSuccess && s == LB_OK) s = check_launch("logbessel_host");
+  if (dbuf) {
+    cudaFreeAsync(dbuf, st[1]);
+    cudaStreamSynchronize(st[1]);
+  }
+  for (int i = 0; i < 3; ++i) {
+    if (ev_in[i]) cudaEventDestroy(ev_in[i]);
+    if (ev_comp[i]) cudaEventDestroy(ev_comp[i]);
+    if (ev_out[i]) cudaEventDestroy(ev_out[i]);
+    if (st[i]) cudaStreamDestroy(st[i]);
+  }
+  return s;
+}
+
 const char* logbessel_last_error(void) { return g_last_error.c_str(); }
 
 void logbessel_profile_enable(int on) {
