@@ -111,53 +111,103 @@ __device__ __forceinline__ float series_log_i32(float v, float x) {
 }
 
 // K integral, Gauss rules of lb_kint.cuh evaluated in single precision
-// (float copies of the tables).  Warp-cooperative; all lanes pass the same pair.
+// (float copies of the tables), including the split g rule for v < 0.4,
+// x < 1e-3 (see kint_sums_split: the nodes anchored at s1 = 128 x carry their
+// terms less C = 2 v log s1 and are shifted by m - C).  Warp-cooperative; all
+// lanes pass the same pair.
 __device__ __forceinline__ float kint_gauss32(float v, float x, int lane) {
   const float beta = 16.0f / (2.0f * v + 1.0f);
   const float logbeta = logf(beta);
-  const float vm = v - 0.5f, tx = 2.0f * x;
-  const float* gu;
-  const float* gw;
-  int ng;
-  if (v >= 0.9f || x >= 0.25f) { gu = lb_kqf_g32_logu; gw = lb_kqf_g32_logw; ng = 32; }
-  else if (v >= 0.4f || x >= 1e-3f) { gu = lb_kqf_g64_logu; gw = lb_kqf_g64_logw; ng = 64; }
-  else { gu = lb_kqf_g128_logu; gw = lb_kqf_g128_logw; ng = 128; }
+  const float vm = v - 0.5f, vp = v + 0.5f, tx = 2.0f * x;
+  const int ng = (v >= 0.9f || x >= 0.25f) ? 32 : ((v >= 0.4f || x >= 1e-3f) ? 64 : 0);
   const float *hs, *hy, *hc;
   int nh;
   if (v <= 1.2f) { hs = lb_kqf_hl32_s; hy = lb_kqf_hl32_y; hc = lb_kqf_hl32_c; nh = 32; }
   else if (v <= 5.0f) { hs = lb_kqf_hl48_s; hy = lb_kqf_hl48_y; hc = lb_kqf_hl48_c; nh = 48; }
   else { hs = lb_kqf_hq32_s; hy = lb_kqf_hq32_y; hc = lb_kqf_hq32_c; nh = 32; }
-  float L[6];
+  float L[7];
+  bool live[7], rel[7];
+  const float sx = 128.0f * x;
+  const float y1 = (ng == 0) ? logf(sx) : 0.0f;     // log s1
+  const float C = 2.0f * v * y1;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int j = lane + 32 * k;
+  for (int k = 0; k < 5; ++k) {
     L[k] = -INFINITY;
-    if (32 * k < ng) {
-      const float logu = __ldg(gu + j);
-      const float ub = expf(beta * logu);
-      L[k] = __ldg(gw + j) + logbeta - ub + fmaf(vm, logf(tx + ub), 7.0f * logu);
+    live[k] = false;
+    rel[k] = false;
+    if (ng != 0) {
+      if (k < 2 && 32 * k < ng) {
+        const int j = lane + 32 * k;
+        const float logu = ng == 32 ? __ldg(lb_kqf_g32_logu + j) : __ldg(lb_kqf_g64_logu + j);
+        const float c = ng == 32 ? __ldg(lb_kqf_g32_c + j) : __ldg(lb_kqf_g64_c + j);
+        const float ub = expf(beta * logu);
+        L[k] = c + logbeta - ub + vm * logf(tx + ub);
+        live[k] = true;
+      }
+    } else if (k < 2) {                               // [0, s1]: s = s1 r, r = u^beta
+      const int j = lane + 32 * k;
+      const float r = expf(beta * __ldg(lb_kqf_g64_logu + j));
+      L[k] = fmaf(vm, logf(r + 0.015625f), __ldg(lb_kqf_g64_c + j) + logbeta) - sx * r;
+      live[k] = true;
+      rel[k] = true;
+    } else {                                          // [s1, 1] in y = log s, panels as in FP64
+      float a, b, t, lw;
+      bool anchored;
+      if (k == 2) {
+        const int j = lane & 15;
+        t = __ldg(lb_kqf_gl16_t + j);
+        lw = __ldg(lb_kqf_gl16_logw + j);
+        anchored = lane < 16;
+        if (anchored) { a = 0.0f; b = fminf(8.0f, -4.0f - y1); }
+        else { a = fmaxf(y1, -4.0f); b = 0.0f; }
+      } else {
+        t = __ldg(lb_kqf_gl32_t + lane);
+        lw = __ldg(lb_kqf_gl32_logw + lane);
+        anchored = k == 3;
+        if (anchored) { a = 8.0f; b = fminf(40.0f, -4.0f - y1); }
+        else { a = fmaxf(y1 + 40.0f, -40.0f); b = -4.0f; }
+      }
+      if (b > a) {
+        const float o = fmaf(b - a, t, a);
+        const float lwb = lw + logf(b - a);
+        if (anchored) {
+          const float eo = expf(o);
+          L[k] = fmaf(vm, logf(eo + 0.015625f), fmaf(vp, o, lwb)) - sx * eo;
+        } else {
+          const float sv = expf(o);
+          L[k] = fmaf(vm, logf(sv + tx), fmaf(vp, o, lwb)) - sv;
+        }
+        live[k] = true;
+        rel[k] = anchored;
+      }
     }
   }
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int j = lane + 32 * k;
-    L[4 + k] = -INFINITY;
+    L[5 + k] = -INFINITY;
+    live[5 + k] = j < nh;
+    rel[5 + k] = false;
     if (j < nh) {
       const float sj = __ldg(hs + j);
-      L[4 + k] = fmaf(vm, __ldg(hy + j) + logf(sj + tx), __ldg(hc + j));
+      L[5 + k] = fmaf(vm, __ldg(hy + j) + logf(sj + tx), __ldg(hc + j));
     }
   }
-  float m = L[0];
+  // closed-form flat middle of the split rule (int e^{2 v y} dy over
+  // [y1 + 40, -40], w = -80 - y1), less C
+  float Lflat = -INFINITY;
+  const float w = -80.0f - y1;
+  if (ng == 0 && w > 0.0f) Lflat = (v == 0.0f) ? logf(w) : fmaf(80.0f, v, logf(expm1f(2.0f * v * w) / (2.0f * v)));
+  float m = Lflat + C;
 #pragma unroll
-  for (int i = 1; i < 6; ++i) m = fmaxf(m, L[i]);
+  for (int i = 0; i < 7; ++i) m = fmaxf(m, rel[i] ? L[i] + C : L[i]);
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  float s = 0.0f;
+  const float mr = m - C;
+  float s = (lane == 0 && Lflat > -INFINITY) ? expf(Lflat - mr) : 0.0f;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const bool live = (k < 4) ? (32 * k < ng) : (32 * (k - 4) < nh && L[k] > -INFINITY);
-    if (live) s += expf(L[k] - m);
-  }
+  for (int k = 0; k < 7; ++k)
+    if (live[k]) s += expf(L[k] - (rel[k] ? mr : m));
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return m + logf(s);

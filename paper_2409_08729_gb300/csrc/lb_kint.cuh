@@ -15,9 +15,9 @@
 //
 // Rules:
 //   LB_TIGHT: Gauss rules (tables in kquad_tables.h).  g: Gauss-Legendre in u
-//     with 32 nodes (v >= 0.9 or x >= 0.25), 64 (v >= 0.4 or x >= 1e-3) or 128;
-//     small x with v away from 1/2 needs more, because (2x + u^beta)^(v-1/2)
-//     turns sharply near u = (2x)^(1/beta).  h: Gauss-Legendre in log s on
+//     with 32 nodes (v >= 0.9 or x >= 0.25), 64 (v >= 0.4 or x >= 1e-3), or
+//     for v < 0.4, x < 1e-3 a split rule (kint_sums_split), because
+//     (2x + u^beta)^(v-1/2) turns sharply near u = (2x)^(1/beta).  h: Gauss-Legendre in log s on
 //     [1, 100] (32 nodes for v <= 1.2, 48 for v <= 5) or Gauss-Laguerre in
 //     s - 1 (32 nodes, v > 5).  Node counts were chosen so the rule error
 //     stays below 1e-16 over v in [0, 16], x in [1e-6, 30] (the fallback
@@ -49,12 +49,190 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
   return kHalfLogPi - lgamma(v + 0.5) - fma(v, fm_log(2.0 * x), x);
 }
 
-// Node counts of the tight rule for one pair, packed as (g count) | (h rule << 8):
-// h rule 0 = Gauss-Legendre in log s with 32 nodes, 1 = with 48, 2 = Gauss-Laguerre 32.
+// Node counts of the tight rule for one pair, packed as (g rule) | (h rule << 8):
+// g rule 32 / 64 = Gauss-Legendre in u with that many nodes, 0 = the split
+// rule for small orders and tiny arguments (below); h rule 0 = Gauss-Legendre
+// in log s with 32 nodes, 1 = with 48, 2 = Gauss-Laguerre 32.
 __device__ __forceinline__ int kint_rule(double v, double x) {
-  const int ng = (v >= 0.9 || x >= 0.25) ? 32 : ((v >= 0.4 || x >= 1e-3) ? 64 : 128);
+  const int ng = (v >= 0.9 || x >= 0.25) ? 32 : ((v >= 0.4 || x >= 1e-3) ? 64 : 0);
   const int hr = (v <= 1.2) ? 0 : ((v <= 5.0) ? 1 : 2);
   return ng | (hr << 8);
+}
+
+// One pair, fixed Gauss rules (g: 32 or 64 nodes in u; h: rule hr), all
+// lanes of the warp: returns on every lane its part of the shifted sums
+// s0 = sum_j e^{L_j - mm} and s1 = sum_j e^{L_j - mm} / (s_j + 2x) (DX), with
+// the common shift mm (the warp maximum of L, taken on the integer pipe).
+template <bool DX>
+__device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta, double logbeta, int ng, int hr,
+                                                int lane, double& mm, double& s0, double& s1) {
+  const double vm = v - 0.5, tx = 2.0 * x;
+  const double* gu = ng == 32 ? lb_kq_g32_logu : lb_kq_g64_logu;
+  const double* gc = ng == 32 ? lb_kq_g32_c : lb_kq_g64_c;
+  const double* hs = hr == 0 ? lb_kq_hl32_s : (hr == 1 ? lb_kq_hl48_s : lb_kq_hq32_s);
+  const double* hy = hr == 0 ? lb_kq_hl32_y : (hr == 1 ? lb_kq_hl48_y : lb_kq_hq32_y);
+  const double* hc = hr == 0 ? lb_kq_hl32_c : (hr == 1 ? lb_kq_hl48_c : lb_kq_hq32_c);
+  const int nh = hr == 1 ? 48 : 32;
+  double L[4], A[4];
+  int key = (int)0x800fffff;                       // order_key(-inf)
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    L[k] = 0.0;
+    A[k] = 0.0;
+    if (32 * k < ng) {                             // g node: log w + 7 log u + log beta - u^beta + (v-1/2) log(2x + u^beta)
+      const int j = lane + 32 * k;
+      const double ub = fm_exp_le(beta * __ldg(gu + j));
+      L[k] = fma(vm, fm_log(tx + ub), __ldg(gc + j) + logbeta) - ub;
+      if (DX) A[k] = 1.0 / (tx + ub);
+      key = max(key, order_key(L[k]));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int j = lane + 32 * k;
+    L[2 + k] = 0.0;
+    A[2 + k] = 0.0;
+    if (j < nh) {                                  // h node: c + (v-1/2)(log s + log(s + 2x))
+      const double sj = __ldg(hs + j);
+      L[2 + k] = fma(vm, __ldg(hy + j) + fm_log(sj + tx), __ldg(hc + j));
+      if (DX) A[2 + k] = 1.0 / (sj + tx);
+      key = max(key, order_key(L[2 + k]));
+    }
+  }
+  mm = key_to_double(__reduce_max_sync(0xffffffffu, key));
+  s0 = 0.0;
+  s1 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool live = (k < 2) ? (32 * k < ng) : (lane + 32 * (k - 2) < nh);
+    if (live) {
+      const double t = fm_exp_le(L[k] - mm);
+      s0 += t;
+      if (DX) s1 = fma(t, A[k], s1);
+    }
+  }
+}
+
+// Split g rule (v < 0.4, x < 1e-3).  (2x + u^beta)^(v-1/2) turns within a
+// width ~1/beta of u = (2x)^(1/beta), and for v -> 0 the integrand is
+// log-uniform between s ~ 2x and 1, which no fixed rule in u resolves as
+// x -> 0.  So int_0^1 F(s) ds is split at s1 = 128 x:
+//   [0, s1]: s = s1 u^beta, the 64-node Gauss-Legendre rule in u (the turn
+//            now sits at u^beta = 1/64, where that rule is exact to 1e-16);
+//   [s1, 1]: y = log s, F(s) s = e^{-s} s^(v+1/2) (s + 2x)^(v-1/2), with
+//            Gauss-Legendre panels [y1, y1 + 8] (16 nodes) and
+//            [y1 + 8, y1 + 40] (32) for the tail of the turn (y1 = log s1),
+//            [-40, -4] (32) and [-4, 0] (16) for the e^{-s} roll-off, each
+//            cut where it meets the next; in between, F(s) s = e^{2 v y} to
+//            1e-17 and is integrated in closed form.
+// The nodes of [0, s1] and of the two panels that start at y1 are placed by
+// their offset o = y - y1 (s = s1 e^o), and their log terms are kept less the
+// common part C = 2 v y1 (log(s + 2x) = y1 + log(e^o + 1/64)): so the
+// hundreds-sized y1 never enters a node's term, whose rounding would
+// otherwise shift each node by ~|y1| ulp and cost the x-derivative (a
+// weighted mean of 1/(s + 2x) over the nodes) two digits.  These terms are
+// shifted by mm - C instead of mm.  Slots: 0, 1 the 64 nodes of [0, s1];
+// 2 = two 16-node panels ([y1, y1 + 8] on lanes 0-15, [-4, 0] on 16-31);
+// 3 = [y1 + 8, y1 + 40]; 4 = [-40, -4]; 5 = the 32 h nodes (v < 0.4, so h
+// is the 32-node rule in log s).
+template <bool DX>
+__device__ __forceinline__ void kint_sums_split(double v, double x, double beta, double logbeta, int lane,
+                                                double& mm, double& s0, double& s1) {
+  const double vm = v - 0.5, vp = v + 0.5, tx = 2.0 * x;
+  const double sx = 128.0 * x;                     // s1 (exact)
+  const double y1 = fm_log(sx);
+  const double C = 2.0 * v * y1;
+  double L[6], A[6];
+  bool live[6], rel[6];
+  int key = (int)0x800fffff;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {                    // [0, s1]: s = s1 r, r = u^beta
+    const int j = lane + 32 * k;
+    const double r = fm_exp_le(beta * __ldg(lb_kq_g64_logu + j));
+    const double sj = sx * r;
+    L[k] = fma(vm, fm_log(r + 0.015625), __ldg(lb_kq_g64_c + j) + logbeta) - sj;
+    A[k] = DX ? 1.0 / (sj + tx) : 0.0;
+    live[k] = true;
+    rel[k] = true;
+    key = max(key, order_key(L[k] + C));
+  }
+#pragma unroll
+  for (int k = 2; k < 5; ++k) {
+    double a, b, t, lw;
+    bool anchored;
+    if (k == 2) {
+      const int j = lane & 15;
+      t = __ldg(lb_kq_gl16_t + j);
+      lw = __ldg(lb_kq_gl16_logw + j);
+      anchored = lane < 16;
+      if (anchored) { a = 0.0; b = fmin(8.0, -4.0 - y1); }       // offsets
+      else { a = fmax(y1, -4.0); b = 0.0; }
+    } else {
+      t = __ldg(lb_kq_gl32_t + lane);
+      lw = __ldg(lb_kq_gl32_logw + lane);
+      anchored = k == 3;
+      if (anchored) { a = 8.0; b = fmin(40.0, -4.0 - y1); }       // offsets
+      else { a = fmax(y1 + 40.0, -40.0); b = -4.0; }
+    }
+    live[k] = b > a;
+    rel[k] = anchored;
+    L[k] = 0.0;
+    A[k] = 0.0;
+    if (live[k]) {
+      const double o = fma(b - a, t, a);
+      const double lwb = lw + fm_log(b - a);
+      double sj;
+      if (anchored) {                              // y = y1 + o
+        const double eo = fm_exp_le(o);
+        sj = sx * eo;
+        L[k] = fma(vm, fm_log(eo + 0.015625), fma(vp, o, lwb)) - sj;
+        key = max(key, order_key(L[k] + C));
+      } else {                                     // y = o
+        sj = fm_exp_le(o);
+        L[k] = fma(vm, fm_log(sj + tx), fma(vp, o, lwb)) - sj;
+        key = max(key, order_key(L[k]));
+      }
+      if (DX) A[k] = 1.0 / (sj + tx);
+    }
+  }
+  {                                                // h nodes, 32-node rule in log s
+    const double sj = __ldg(lb_kq_hl32_s + lane);
+    L[5] = fma(vm, __ldg(lb_kq_hl32_y + lane) + fm_log(sj + tx), __ldg(lb_kq_hl32_c + lane));
+    A[5] = DX ? 1.0 / (sj + tx) : 0.0;
+    live[5] = true;
+    rel[5] = false;
+    key = max(key, order_key(L[5]));
+  }
+  // flat middle [y1 + 40, -40]: int e^{2 v y} dy = e^{2 v (y1 + 40)} (e^{2 v w} - 1) / (2 v), w = -80 - y1;
+  // less C: 80 v + log(expm1(2 v w) / (2 v))
+  const double w = -80.0 - y1;
+  const bool flat = w > 0.0;
+  double Lflat = 0.0;
+  if (flat) {
+    Lflat = (v == 0.0) ? fm_log(w) : fma(80.0, v, fm_log(expm1(2.0 * v * w) / (2.0 * v)));
+    key = max(key, order_key(Lflat + C));
+  }
+  mm = key_to_double(__reduce_max_sync(0xffffffffu, key));
+  const double mr = mm - C;
+  s0 = 0.0;
+  s1 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    if (live[k]) {
+      const double t = fm_exp_le(L[k] - (rel[k] ? mr : mm));
+      s0 += t;
+      if (DX) s1 = fma(t, A[k], s1);
+    }
+  }
+  if (flat && lane == 0) {
+    s0 += fm_exp_le(Lflat - mr);
+    if (DX) {
+      // there 1/(s + 2x) = e^{-y} to 1e-17: int e^{(2v-1) y} dy over the same
+      // interval, less C: (2v - 1) 40 - y1 + log((1 - e^{(2v-1) w}) / (1 - 2v))
+      const double c = 2.0 * v - 1.0;
+      s1 += fm_exp_le(fma(40.0, c, -y1) + fm_log(-expm1(c * w) / -c) - mr);
+    }
+  }
 }
 
 // K integrals of up to 32 pairs by one warp (Gauss rules; lane e holds pair
@@ -63,10 +241,11 @@ __device__ __forceinline__ int kint_rule(double v, double x) {
 // warp-shuffle reduction (Eq. "log sum trick").  Everything that is per pair
 // rather than per node (the order-dependent constants, the prefactor, the
 // final logarithm) is computed once per lane for its own pair, not once per
-// pair by all 32 lanes.  Returns, on lane e, log K of pair e (DX = false) or
-// d/dx log K (DX = true: the prefactor derivative -v/x - 1 plus
-// (2v - 1) <1/(s + 2x)>, the F-weighted mean over the nodes, since
-// dF/dx = F (2v - 1)/(s + 2x)).
+// pair by all 32 lanes.  The rule is uniform across the warp for each pair,
+// so the split and fixed paths never diverge.  Returns, on lane e, log K of
+// pair e (DX = false) or d/dx log K (DX = true: the prefactor derivative
+// -v/x - 1 plus (2v - 1) <1/(s + 2x)>, the F-weighted mean over the nodes,
+// since dF/dx = F (2v - 1)/(s + 2x)).
 template <bool DX>
 __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane) {
   const double beta_i = 16.0 / (2.0 * vi + 1.0);
@@ -80,50 +259,9 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     const double logbeta = __shfl_sync(0xffffffffu, logbeta_i, e);
     const int rule = __shfl_sync(0xffffffffu, rule_i, e);
     const int ng = rule & 0xff, hr = rule >> 8;
-    const double vm = v - 0.5, tx = 2.0 * x;
-    const double* gu = ng == 32 ? lb_kq_g32_logu : (ng == 64 ? lb_kq_g64_logu : lb_kq_g128_logu);
-    const double* gc = ng == 32 ? lb_kq_g32_c : (ng == 64 ? lb_kq_g64_c : lb_kq_g128_c);
-    const double* hs = hr == 0 ? lb_kq_hl32_s : (hr == 1 ? lb_kq_hl48_s : lb_kq_hq32_s);
-    const double* hy = hr == 0 ? lb_kq_hl32_y : (hr == 1 ? lb_kq_hl48_y : lb_kq_hq32_y);
-    const double* hc = hr == 0 ? lb_kq_hl32_c : (hr == 1 ? lb_kq_hl48_c : lb_kq_hq32_c);
-    const int nh = hr == 1 ? 48 : 32;
-    double L[6], A[6];
-    int key = (int)0x800fffff;                       // order_key(-inf)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      L[k] = 0.0;
-      A[k] = 0.0;
-      if (32 * k < ng) {                            // g node: log w + 7 log u + log beta - u^beta + (v-1/2) log(2x + u^beta)
-        const int j = lane + 32 * k;
-        const double ub = fm_exp_le(beta * __ldg(gu + j));
-        L[k] = fma(vm, fm_log(tx + ub), __ldg(gc + j) + logbeta) - ub;
-        if (DX) A[k] = 1.0 / (tx + ub);
-        key = max(key, order_key(L[k]));
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int j = lane + 32 * k;
-      L[4 + k] = 0.0;
-      A[4 + k] = 0.0;
-      if (j < nh) {                                 // h node: c + (v-1/2)(log s + log(s + 2x))
-        const double sj = __ldg(hs + j);
-        L[4 + k] = fma(vm, __ldg(hy + j) + fm_log(sj + tx), __ldg(hc + j));
-        if (DX) A[4 + k] = 1.0 / (sj + tx);
-        key = max(key, order_key(L[4 + k]));
-      }
-    }
-    const double mm = key_to_double(__reduce_max_sync(0xffffffffu, key));
-    double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const bool live = (k < 4) ? (32 * k < ng) : (lane + 32 * (k - 4) < nh);
-      if (live) {
-        const double t = fm_exp_le(L[k] - mm);
-        s0 += t;
-        if (DX) s1 = fma(t, A[k], s1);
-      }
-    }
+    double mm, s0, s1;
+    if (ng == 0) kint_sums_split<DX>(v, x, beta, logbeta, lane, mm, s0, s1);
+    else kint_sums_fixed<DX>(v, x, beta, logbeta, ng, hr, lane, mm, s0, s1);
     s0 = warp_sum(s0);
     if (DX) s1 = warp_sum(s1);
     if (lane == e) {

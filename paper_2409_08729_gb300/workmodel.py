@@ -4,8 +4,9 @@ Work is counted in FP64 pipe slots: one slot per double add, multiply, fused
 multiply-add or compare the method performs, and for each library call
 (division, square root, reciprocal square root, lgamma) the number of DFMA
 issue slots one call occupies on this GPU, i.e. (DFMA throughput) / (call
-throughput), both measured with all SMs busy by logbessel_measure_fp64.  The
-table-driven exp and log of lb_fastmath.cuh are counted the same way.
+throughput) less the one extra operation of the measuring loop, both
+measured with all SMs busy by logbessel_measure_fp64.  The table-driven exp
+and log of lb_fastmath.cuh are counted the same way.
 FLOP = 2 x slots (an FMA counts two).
 
 The counts follow the code paths of lb_expr.cuh and lb_kint.cuh (tight mode,
@@ -15,26 +16,49 @@ higher than counted here.
 """
 import numpy as np
 
-# DFMA-slot cost of one CUDA call (measured throughput ratios on GB300:
-# DFMA 0.597 T/s; div 58.2 G/s, sqrt 58.1 G/s, lgamma 20.7 G/s)
-SLOT_DIV = 10.3
-SLOT_SQRT = 10.3
-SLOT_RSQRT = 10.3
-SLOT_LGAMMA = 28.9
-# library exp/log (lb_fastmath.cuh): measured the same way (DFMA 627 G/s;
-# fm_exp 41.2 G/s, fm_log 33.3 G/s, less the one extra operation per call of
-# the throughput loop)
-SLOT_EXP = 14.2
-SLOT_LOG = 17.8
+# DFMA-slot cost of one call: (DFMA rate) / (call rate) - 1, the rates measured
+# with all SMs busy by logbessel_measure_fp64 (the 1 is the extra operation per
+# call of its throughput loop).  These defaults are one GB300 measurement
+# (DFMA 627 G/s; division 61.2, sqrt 61.1, lgamma 21.9 G/s); bench.py replaces
+# them with the rates it measures on the GPU it runs on (set_costs).
+SLOT_DIV = 9.2
+SLOT_SQRT = 9.3
+SLOT_RSQRT = 9.3
+SLOT_LGAMMA = 27.6
+# table-driven exp/log of lb_fastmath.cuh: 10, 9 and 14 FP64 operations as
+# written; the measured costs replace these
+SLOT_EXP = 10.0
+SLOT_EXP_TERM = 9.0
+SLOT_LOG = 14.0
+
+
+def set_costs(rates):
+    """Set the slot costs from measured rates (dict of operations per second,
+    as returned by _binding.measure_fp64)."""
+    global SLOT_DIV, SLOT_SQRT, SLOT_RSQRT, SLOT_LGAMMA, SLOT_EXP, SLOT_EXP_TERM, SLOT_LOG
+    d = rates["dfma"]
+    SLOT_DIV = d / rates["div"] - 1.0
+    SLOT_SQRT = SLOT_RSQRT = d / rates["sqrt"] - 1.0
+    SLOT_LGAMMA = d / rates["lgamma"] - 1.0
+    SLOT_EXP = d / rates["fm_exp"] - 1.0
+    SLOT_LOG = d / rates["fm_log"] - 1.0
+    if "fm_exp_term" in rates:
+        SLOT_EXP_TERM = d / rates["fm_exp_term"] - 1.0
+    return {"div": SLOT_DIV, "sqrt": SLOT_SQRT, "lgamma": SLOT_LGAMMA, "fm_exp": SLOT_EXP,
+            "fm_exp_term": SLOT_EXP_TERM, "fm_log": SLOT_LOG}
+
 
 REGION_K = {0: 20, 1: 13, 4: 3, 5: 4, 6: 6, 7: 9}   # region id -> number of expansion terms
 
 
 def kint_rule(v, x):
-    """Node counts (g, h) of the tight K-integral rule for each pair (|v| given)."""
+    """Node counts (g, h) of the tight K-integral rule for each pair (|v| given).
+    The split g rule (v < 0.4, x < 1e-3) has 64 + 32 + 32 nodes, plus 32 more
+    below x ~ 4e-21."""
     v = np.asarray(v, dtype=np.float64)
     x = np.asarray(x, dtype=np.float64)
-    ng = np.where((v >= 0.9) | (x >= 0.25), 32, np.where((v >= 0.4) | (x >= 1e-3), 64, 128))
+    split = np.where(np.log(128 * np.maximum(x, 1e-320)) + 40 < -4, 160, 128)
+    ng = np.where((v >= 0.9) | (x >= 0.25), 32, np.where((v >= 0.4) | (x >= 1e-3), 64, split))
     nh = np.where(v <= 1.2, 32, np.where(v <= 5.0, 48, 32))
     return ng, nh
 
@@ -42,13 +66,17 @@ def kint_rule(v, x):
 def kint_slots(v, x):
     """FP64 slots of one K-integral evaluation per pair (tight Gauss rule)."""
     ng, nh = kint_rule(v, x)
+    split = ng > 64
     # g node: beta*log u, exp, add, log, add, fma, subtract; then exp(L - m), accumulate
-    g_node = 1 + SLOT_EXP + 1 + SLOT_LOG + 1 + 1 + 1 + 1 + SLOT_EXP + 1
+    # (split rule: 3 more for the offset form: s1 * r, the shift by C, the key add)
+    g_node = 7 + 2 * SLOT_EXP_TERM + SLOT_LOG + np.where(split, 3, 0)
     # h node: s + 2x, log, + y, fma; then subtract, exp, accumulate
-    h_node = 1 + SLOT_LOG + 1 + 1 + 1 + SLOT_EXP + 1
+    h_node = 1 + SLOT_LOG + 1 + 1 + 1 + SLOT_EXP_TERM + 1
     # per pair (once per lane of its batch): beta (div), log beta, prefactor
     # (lgamma, log, 3 ops), final log; the warp sum (5 adds, all lanes)
     per_pair = SLOT_DIV + SLOT_LOG + SLOT_LGAMMA + SLOT_LOG + 3 + SLOT_LOG + 2 + 5
+    # split rule: log s1, C, three panel widths (log + add each), the flat term (log, expm1, division)
+    per_pair = per_pair + np.where(split, 2 + 4 * SLOT_LOG + 3 + SLOT_EXP + SLOT_DIV + 4, 0)
     return ng * g_node + nh * h_node + per_pair
 
 

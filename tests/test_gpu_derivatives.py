@@ -93,3 +93,10 @@ def test_domain_edges(cuda):
     dk = _dx("k", v, x, cuda)
     assert di[0] == 0.0 and di[1] == np.inf and di[2] == 1.0 and np.isnan(di[3]) and np.isnan(di[4])
     assert dk[0] == -np.inf and dk[1] == -np.inf and dk[2] == -1.0 and np.isnan(dk[3]) and np.isnan(dk[4])
+
+
+def test_k_derivative_tiny_arguments(cuda):
+    rng = np.random.default_rng(18)
+    v = rng.uniform(0, 0.4, 1500)
+    x = np.exp(rng.uniform(np.log(1e-300), np.log(1e-3), 1500))
+    _check("k", v, x, _dx("k", v, x, cuda))

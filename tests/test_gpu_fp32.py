@@ -65,3 +65,11 @@ def test_ragged(cuda, kind):
     for n in (1, 33, 1025, 5000):
         v, x = W.robust_pairs(n, seed=n + 1, vmax=1e3, xmin=1e-4, xmax=1e3)
         _check(kind, v, x, cuda)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_tiny_arguments(cuda, kind):
+    rng = np.random.default_rng(19)
+    v = rng.uniform(0, 0.6, 6000)
+    x = np.exp(rng.uniform(np.log(1e-37), np.log(1e-2), 6000))
+    _check(kind, v, x, cuda)
