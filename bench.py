@@ -155,6 +155,10 @@ def main():
     ap.add_argument("--err-sample", type=int, default=4000, help="oracle-checked outputs per call type")
     ap.add_argument("--serve-requests", type=int, default=4000,
                     help="requests in the serving measurement (0 = skip)")
+    ap.add_argument("--robust-n", type=int, default=64 << 20,
+                    help="pairs of the robustness sweep measurement (0 = skip)")
+    ap.add_argument("--no-paper-tables", action="store_true",
+                    help="skip the paper's Small/Large and order-0/1 workloads")
     args = ap.parse_args()
 
     world = _env_int("WORLD_SIZE", 1)
@@ -203,6 +207,7 @@ def main():
 
     # FP64 roofline of this GPU, measured live
     rates = B.measure_fp64(sp)
+    slot_costs = WM.set_costs(rates)
 
     for _ in range(args.warmup):
         step(x_all, v_mixed, outs)
@@ -401,13 +406,23 @@ def main():
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clocks,
             "kernels": {k: {"launches": v[0], "ms": v[2], **other.get(k, {})} for k, v in prof.items()},
             "region_mix_mixed_call": mix,
-            "fp64_rates": {k: v / 1e9 for k, v in rates.items()}}
+            "fp64_rates": {k: v / 1e9 for k, v in rates.items()}, "slot_costs": slot_costs}
     line["max_rel_err"] = acc
     line["fp32_mixed"] = fp32
+    del outs
+    torch.cuda.empty_cache()
+    if rank == 0 and args.robust_n > 0:
+        from paper_2409_08729_gb300 import robustbench
+        line["robustness_sweep"] = robustbench.run(n=args.robust_n, device=str(dev),
+                                                   per_region=1000 if args.err_sample > 0 else 0,
+                                                   check=args.err_sample > 0)
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_paper_tables:
+        from paper_2409_08729_gb300 import paperbench
+        line["paper_workloads"] = paperbench.run(device=str(dev))
+        torch.cuda.empty_cache()
     if rank == 0 and args.serve_requests > 0:
         from paper_2409_08729_gb300 import servebench
-        del outs
-        torch.cuda.empty_cache()
         line["serving"] = servebench.run(n_req=args.serve_requests, seed=0, device=str(dev))
     if rank == 0:
         r, threads, n = time_oracle(args.cpu_per_v)

@@ -38,6 +38,17 @@ def _pool(n, seed):
 
 
 def run(n_req=20000, seed=0, max_n=1_000_000, load=0.8, device="cuda", pool_n=1 << 23, out_slots=512):
+    """One offered load (a float) or several (a sequence): the capacity is
+    measured once, then both systems run the arrival stream of each load."""
+    loads = [load] if isinstance(load, (int, float)) else list(load)
+    res = _run(n_req, seed, max_n, loads, device, pool_n, out_slots)
+    if isinstance(load, (int, float)):
+        res["batched"] = res.pop("batched_by_load")[0]
+        res["per_request_calls"] = res.pop("per_request_calls_by_load")[0]
+    return res
+
+
+def _run(n_req, seed, max_n, loads, device, pool_n, out_slots):
     dev = torch.device(device)
     sizes, kinds, f32 = _mix(n_req, seed, max_n)
     pv64, px64, pv32, px32 = _pool(pool_n, seed + 1)
@@ -71,31 +82,36 @@ def run(n_req=20000, seed=0, max_n=1_000_000, load=0.8, device="cuda", pool_n=1 
         for t in tickets:
             srv.release(t)
         res["capacity_gevals"] = cap / 1e9
-        # open loop, Poisson arrivals at load x capacity (in pairs per second)
-        rate = load * cap / (total / n_req)                # requests per second
-        arr = np.cumsum(rng.exponential(1.0 / rate, n_req))
-        tickets = [None] * n_req
-        start = time.perf_counter()
-        for i in range(n_req):
-            dt = arr[i] - (time.perf_counter() - start)
-            if dt > 0:
-                time.sleep(dt)
-            if i >= out_slots:
-                srv.wait(tickets[i - out_slots], timeout=300)
-            tickets[i] = srv.submit("ik"[kinds[i]], *args_of(i))
-        for t in tickets[-out_slots:]:
-            srv.wait(t, timeout=300)
-        lat = np.empty(n_req)
-        t_first, t_last = np.inf, 0.0
-        for i, t in enumerate(tickets):
-            done, ts, ta, td = srv.info(t)
-            lat[i] = td - ts
-            t_first, t_last = min(t_first, ts), max(t_last, td)
-            srv.release(t)
-        st = srv.stats()
-    res["batched"] = {"offered_load": load, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                      "p99_ms": 1e3 * float(np.percentile(lat, 99)), "gevals": total / (t_last - t_first) / 1e9,
-                      "kernel_launches": st["kernel_launches"]}
+        res["batched_by_load"] = []
+        arrivals = []
+        for load in loads:
+            # open loop, Poisson arrivals at load x capacity (in pairs per second)
+            rate = load * cap / (total / n_req)                # requests per second
+            arr = np.cumsum(rng.exponential(1.0 / rate, n_req))
+            arrivals.append(arr)
+            tickets = [None] * n_req
+            st0 = srv.stats()["kernel_launches"]
+            start = time.perf_counter()
+            for i in range(n_req):
+                dt = arr[i] - (time.perf_counter() - start)
+                if dt > 0:
+                    time.sleep(dt)
+                if i >= out_slots:
+                    srv.wait(tickets[i - out_slots], timeout=300)
+                tickets[i] = srv.submit("ik"[kinds[i]], *args_of(i))
+            for t in tickets[-out_slots:]:
+                srv.wait(t, timeout=300)
+            lat = np.empty(n_req)
+            t_first, t_last = np.inf, 0.0
+            for i, t in enumerate(tickets):
+                done, ts, ta, td = srv.info(t)
+                lat[i] = td - ts
+                t_first, t_last = min(t_first, ts), max(t_last, td)
+                srv.release(t)
+            res["batched_by_load"].append({
+                "offered_load": load, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "gevals": total / (t_last - t_first) / 1e9,
+                "kernel_launches": srv.stats()["kernel_launches"] - st0})
 
     # one library call per request, same arrivals, one stream, FIFO
     L = B.lib()
@@ -106,27 +122,43 @@ def run(n_req=20000, seed=0, max_n=1_000_000, load=0.8, device="cuda", pool_n=1 
     dv32 = torch.empty(max_n, dtype=torch.float32, device=dev)
     dx32 = torch.empty(max_n, dtype=torch.float32, device=dev)
     do32 = torch.empty(max_n, dtype=torch.float32, device=dev)
-    lat2 = np.empty(n_req)
-    start = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for i in range(n_req):
-            dt = arr[i] - (time.perf_counter() - start)
-            if dt > 0:
-                time.sleep(dt)
-            hv, hx, ho = args_of(i)
-            n = int(sizes[i])
-            if f32[i]:
-                dv, dx, do, code = dv32, dx32, do32, B.LB_F32
-            else:
-                dv, dx, do, code = dv64, dx64, do64, B.LB_F64
-            dv[:n].copy_(hv, non_blocking=True)
-            dx[:n].copy_(hx, non_blocking=True)
-            fn = L.logbessel_i if kinds[i] == 0 else L.logbessel_k
-            B.check(fn(code, dv.data_ptr(), 1, dx.data_ptr(), do.data_ptr(), n, 0, stream.cuda_stream))
-            ho.copy_(do[:n], non_blocking=True)
-            stream.synchronize()
-            lat2[i] = (time.perf_counter() - start) - arr[i]
-    span = (time.perf_counter() - start) - arr[0]
-    res["per_request_calls"] = {"p50_ms": 1e3 * float(np.percentile(lat2, 50)),
-                                "p99_ms": 1e3 * float(np.percentile(lat2, 99)), "gevals": total / span / 1e9}
+    res["per_request_calls_by_load"] = []
+    for load, arr in zip(loads, arrivals):
+        lat2 = np.empty(n_req)
+        start = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(n_req):
+                dt = arr[i] - (time.perf_counter() - start)
+                if dt > 0:
+                    time.sleep(dt)
+                hv, hx, ho = args_of(i)
+                n = int(sizes[i])
+                if f32[i]:
+                    dv, dx, do, code = dv32, dx32, do32, B.LB_F32
+                else:
+                    dv, dx, do, code = dv64, dx64, do64, B.LB_F64
+                dv[:n].copy_(hv, non_blocking=True)
+                dx[:n].copy_(hx, non_blocking=True)
+                fn = L.logbessel_i if kinds[i] == 0 else L.logbessel_k
+                B.check(fn(code, dv.data_ptr(), 1, dx.data_ptr(), do.data_ptr(), n, 0, stream.cuda_stream))
+                ho.copy_(do[:n], non_blocking=True)
+                stream.synchronize()
+                lat2[i] = (time.perf_counter() - start) - arr[i]
+        span = (time.perf_counter() - start) - arr[0]
+        res["per_request_calls_by_load"].append({
+            "offered_load": load, "p50_ms": 1e3 * float(np.percentile(lat2, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat2, 99)), "gevals": total / span / 1e9})
     return res
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="Serving benchmark (continuous batching vs one call per request)")
+    ap.add_argument("--requests", type=int, default=100_000)
+    ap.add_argument("--loads", default="0.5,0.8,0.95")
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args()
+    from . import build_library
+    build_library()
+    print(json.dumps(run(n_req=a.requests, seed=a.seed, load=[float(t) for t in a.loads.split(",")])), flush=True)

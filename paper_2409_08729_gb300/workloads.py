@@ -49,6 +49,24 @@ def robust_pairs(n, seed=0, vmax=1e5, xmin=1e-6, xmax=1e5):
     return v, x
 
 
+def robust_device(n, seed, device, vmax=1e5, xmin=1e-6, xmax=1e5):
+    """robust_pairs generated on the GPU (torch Philox): v log-uniform on
+    [1e-6, vmax] with 1% exactly 0 and 1% exactly 1/2, x log-uniform on
+    [xmin, xmax].  Returns float64 device tensors (v, x)."""
+    import math
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    v = torch.empty(n, dtype=torch.float64, device=device)
+    x = torch.empty(n, dtype=torch.float64, device=device)
+    v.uniform_(math.log(1e-6), math.log(vmax), generator=g).exp_()
+    x.uniform_(math.log(xmin), math.log(xmax), generator=g).exp_()
+    u = torch.rand(n, dtype=torch.float64, device=device, generator=g)
+    v[u < 0.01] = 0.0
+    v[(u >= 0.01) & (u < 0.02)] = 0.5
+    return v, x
+
+
 def paper_regions(n, seed=0, which="small", kind="i"):
     """Paper Sec. 5.1 test regions: Small [0,150]^2; Large [150,1e4]^2 for I and
     [150,4000]^2 for K; uniform samples."""
