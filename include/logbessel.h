@@ -202,9 +202,11 @@ long long logbessel_launch_count(void);
 /*
  * Measure the FP64-pipe roofline of the current GPU (microbenchmarks with
  * every SM busy; runs about 0.2 s and synchronizes the stream).  rates is a
- * host array of 8 doubles that receives operations per second for: DFMA,
+ * host array of 11 doubles that receives operations per second for: DFMA,
  * exp, log, division, sqrt, lgamma (CUDA, double precision), and the
- * library's table-driven exp and log.  Returns LB_EINVAL for
+ * library's table-driven exp and log, its exp for quadrature terms (no low
+ * table part), and its integer-pipe exp and log (11 doubles in all).
+ * Returns LB_EINVAL for
  * a NULL rates, LB_ENOMEM or LB_ECUDA on failure.
  */
 lb_status logbessel_measure_fp64(double* rates, void* cuda_stream);
@@ -213,7 +215,9 @@ lb_status logbessel_measure_fp64(double* rates, void* cuda_stream);
  * Elementwise double-precision exp/log used inside the kernels, exposed for
  * checking: which = 0 table-driven exp, 1 table-driven log (Tang's method),
  * 2 CUDA exp, 3 CUDA log, 4 log(cyl_bessel_i0), 5 log(cyl_bessel_i1) (CUDA's
- * order-0/1 functions, the comparison system of paper Sec. 6.1).  in/out are
+ * order-0/1 functions, the comparison system of paper Sec. 6.1), 6 the
+ * table-driven exp without the low table part (quadrature terms; y <= 708),
+ * 7 exp and 8 log in fixed-point integer arithmetic (exp: y <= 708).  in/out are
  * device arrays of n doubles.  LB_EINVAL for a bad which, size or pointer.
  */
 lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t n, void* cuda_stream);

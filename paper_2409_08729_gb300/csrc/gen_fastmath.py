@@ -5,7 +5,7 @@ implementation of the exponential function in IEEE floating-point arithmetic"
 (ACM TOMS 15(2), 1989) and "Table-driven implementation of the logarithm
 function in IEEE floating-point arithmetic" (ACM TOMS 16(4), 1990):
 
-  exp: 2^(j/128), j = 0..127, as a double-double (hi + lo).
+  exp: 2^(j/512), j = 0..511, as a double-double (hi + lo).
   log: for m = 1 + (j + 1/2)/128 (the midpoints of the 128 mantissa intervals
        of [1, 2)), c_j = 1/m rounded to 24 bits, and -log(c_j) as a
        double-double; for m >= sqrt(2) the entry is -log(c_j) - log(2) so that
@@ -37,8 +37,8 @@ def main():
     out = sys.argv[1] if len(sys.argv) > 1 else os.path.join(os.path.dirname(os.path.abspath(__file__)), "fastmath_tables.h")
     lines = ["// Generated by gen_fastmath.py -- do not edit.", "#pragma once", ""]
     ehi, elo = [], []
-    for j in range(128):
-        h, l = dd(mp.mpf(2) ** (mp.mpf(j) / 128))
+    for j in range(512):
+        h, l = dd(mp.mpf(2) ** (mp.mpf(j) / 512))
         ehi.append(h)
         elo.append(l)
     ch, lh, ll = [], [], []
@@ -66,7 +66,7 @@ def main():
 
     def arr(name, vals):
         body = ",\n  ".join(", ".join(repr(v) for v in vals[i:i + 4]) for i in range(0, len(vals), 4))
-        return "static __device__ const double %s[128] = {\n  %s};\n" % (name, body)
+        return "static __device__ const double %s[%d] = {\n  %s};\n" % (name, len(vals), body)
 
     lines.append("#define LB_FM_LOG_JSPLIT %d" % jsplit)
     lines.append(arr("lb_fm_exp_hi", ehi))
@@ -74,9 +74,9 @@ def main():
     lines.append(arr("lb_fm_log_c", ch))
     lines.append(arr("lb_fm_log_hi", lh))
     lines.append(arr("lb_fm_log_lo", ll))
-    # reduction constants for exp: 128/ln2, ln2/128 split so that k * hi is exact for |k| < 2^18
-    inv = float(128 / mp.log(2))
-    l = mp.log(2) / 128
+    # reduction constants for exp: 512/ln2, ln2/512 split so that k * hi is exact for |k| < 2^20
+    inv = float(512 / mp.log(2))
+    l = mp.log(2) / 512
     hi_bits = struct.unpack("<Q", struct.pack("<d", float(l)))[0] & ~((1 << 20) - 1)   # keep 33 bits
     lhi = struct.unpack("<d", struct.pack("<Q", hi_bits))[0]
     llo = float(l - mp.mpf(lhi))

@@ -5,10 +5,11 @@
 // log.  These are table-driven implementations after P. T. P. Tang
 // ("Table-driven implementation of the exponential function in IEEE
 // floating-point arithmetic", ACM TOMS 15(2), 1989; "... of the logarithm
-// function ...", ACM TOMS 16(4), 1990): argument reduction with 128-entry
-// tables (gen_fastmath.py), a short polynomial, and exponent handling with
-// integer instructions, which run on other pipes.  About 12 (exp) and 15
-// (log) FP64 operations per call.  Both fall back to the libm function
+// function ...", ACM TOMS 16(4), 1990): argument reduction with tables
+// (gen_fastmath.py: 512 entries for exp, 128 for log), a short polynomial,
+// and exponent handling with integer instructions, which run on other pipes.
+// 10 (exp; 9 without the low table part) and 14 (log) FP64 operations per
+// call.  Both fall back to the libm function
 // outside their fast range (|y| >= 708 for exp; zero, negative, subnormal,
 // infinite or NaN arguments for log).  Accuracy is checked against the
 // double-double oracle and against CUDA's exp/log in the test suite.
@@ -18,23 +19,32 @@
 
 namespace lb {
 
-__device__ __forceinline__ double fm_exp(double y) {
-  if (!(fabs(y) < 708.0)) return exp(y);
+// Shared core of the exps: y = (k / 512) ln 2 + r, |r| <= ln2 / 1024, k split
+// as 512 m + j; e^y = 2^m 2^(j/512) e^r.  Returns 2^(j/512) (1 + p) with
+// p = e^r - 1 (|r|^5/120 < 1.2e-18 is the truncation of the degree-4
+// polynomial); `lo` adds the low part of the table entry.  The caller
+// applies 2^m to the exponent field (integer add).
+template <bool LO>
+__device__ __forceinline__ double fm_exp_core(double y, int* m) {
   const double shifter = 6755399441055744.0;                 // 1.5 * 2^52
-  const double t = fma(y, LB_FM_INV_L, shifter);             // rint(y * 128 / ln 2) in the low bits
+  const double t = fma(y, LB_FM_INV_L, shifter);             // rint(y * 512 / ln 2) in the low bits
   const int k = __double2loint(t);
   const double kd = t - shifter;
-  double r = fma(-kd, LB_FM_L_HI, y);                        // exact: kd * L_HI has <= 51 bits
-  r = fma(-kd, LB_FM_L_LO, r);                               // |r| <= ln2/256
-  // e^r - 1 = r + r^2 (1/2 + r (1/6 + r (1/24 + r/120)))   (|r|^6/720 < 6e-19)
-  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  p = fma(p, r, 1.0 / 6.0);
+  double r = fma(-kd, LB_FM_L_HI, y);                        // exact: kd * L_HI has <= 53 bits
+  r = fma(-kd, LB_FM_L_LO, r);
+  double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   p = fma(p, r, 0.5);
   p = fma(p, r * r, r);
-  const int j = k & 127;
-  const int m = k >> 7;
+  const int j = k & 511;
+  *m = k >> 9;
   const double th = __ldg(lb_fm_exp_hi + j);
-  const double res = fma(th, p, __ldg(lb_fm_exp_lo + j)) + th;   // 2^(j/128) e^r
+  return LO ? fma(th, p, __ldg(lb_fm_exp_lo + j)) + th : fma(th, p, th);
+}
+
+__device__ __forceinline__ double fm_exp(double y) {
+  if (!(fabs(y) < 708.0)) return exp(y);
+  int m;
+  const double res = fm_exp_core<true>(y, &m);
   return __hiloint2double(__double2hiint(res) + (m << 20), __double2loint(res));
 }
 
@@ -44,20 +54,21 @@ __device__ __forceinline__ double fm_exp(double y) {
 __device__ __forceinline__ double fm_exp_le(double y) {
   const bool under = (unsigned int)__double2hiint(y) > 0xC0862000u;     // y < -708 (sign bit set)
   if (under) y = -708.0;
-  const double shifter = 6755399441055744.0;
-  const double t = fma(y, LB_FM_INV_L, shifter);
-  const int k = __double2loint(t);
-  const double kd = t - shifter;
-  double r = fma(-kd, LB_FM_L_HI, y);
-  r = fma(-kd, LB_FM_L_LO, r);
-  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  p = fma(p, r, 1.0 / 6.0);
-  p = fma(p, r, 0.5);
-  p = fma(p, r * r, r);
-  const int j = k & 127;
-  const int m = k >> 7;
-  const double th = __ldg(lb_fm_exp_hi + j);
-  const double res = fma(th, p, __ldg(lb_fm_exp_lo + j)) + th;
+  int m;
+  const double res = fm_exp_core<true>(y, &m);
+  const double out = __hiloint2double(__double2hiint(res) + (m << 20), __double2loint(res));
+  return under ? 0.0 : out;
+}
+
+// fm_exp_le without the low table part: within about 1 ulp instead of 0.5,
+// one FP64 operation less.  For the terms of a quadrature sum and for node
+// positions, where a 1-ulp error per term is far below the sum's own
+// rounding.
+__device__ __forceinline__ double fm_exp_term(double y) {
+  const bool under = (unsigned int)__double2hiint(y) > 0xC0862000u;
+  if (under) y = -708.0;
+  int m;
+  const double res = fm_exp_core<false>(y, &m);
   const double out = __hiloint2double(__double2hiint(res) + (m << 20), __double2loint(res));
   return under ? 0.0 : out;
 }
@@ -84,9 +95,9 @@ __device__ __forceinline__ double fm_log(double z) {
   const int e = ((hi >> 20) - 1023) + (j >= LB_FM_LOG_JSPLIT ? 1 : 0);
   const double mant = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);   // in [1, 2)
   const double r = fma(mant, __ldg(lb_fm_log_c + j), -1.0);                   // |r| < 2^-7
-  // log1p(r) = r - r^2 (1/2 - r (1/3 - r (1/4 - ... - r (1/8 - r/9))))   (|r|^9/9 < 2e-20)
-  double q = fma(r, -1.0 / 9.0, 1.0 / 8.0);
-  q = fma(q, -r, 1.0 / 7.0);
+  // log1p(r) = r - r^2 (1/2 - r (1/3 - r (1/4 - ... - r (1/7 - r/8))))
+  // (truncation |r|^9/9 < 1.6e-18 |r|)
+  double q = fma(r, -1.0 / 8.0, 1.0 / 7.0);
   q = fma(q, -r, 1.0 / 6.0);
   q = fma(q, -r, 1.0 / 5.0);
   q = fma(q, -r, 0.25);

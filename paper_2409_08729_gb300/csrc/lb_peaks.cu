@@ -7,12 +7,15 @@
 //     division, sqrt), 4 independent chains per thread.
 // The ratio DFMA rate / call rate is the number of DFMA issue slots one call
 // occupies, which the roofline accounting uses as the cost of a call.  The
-// table-driven exp and log of lb_fastmath.cuh are measured the same way.
+// table-driven exp (also without its low table part) and log of
+// lb_fastmath.cuh, and the integer-pipe exp and log of lb_intmath.cuh, are
+// measured the same way.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "logbessel.h"
 #include "lb_fastmath.cuh"
+#include "lb_intmath.cuh"
 
 namespace {
 
@@ -37,12 +40,15 @@ __device__ __forceinline__ double call_op(double a) {
   if (OP == 3) return sqrt(a) + 1.0;
   if (OP == 5) return lb::fm_exp(a) * 0.1;
   if (OP == 6) return lb::fm_log(a) + 2.0;
+  if (OP == 7) return lb::fm_exp_term(a) * 0.1;
+  if (OP == 8) return lb::ix_exp(a) * 0.1;
+  if (OP == 9) return lb::ix_log(a) + 2.0;
   return lgamma(a) + 2.0;
 }
 
 template <int OP>
 __global__ void peak_call(double* out, int iters) {
-  double a = (OP == 0 || OP == 5 ? 0.1 : 2.1) + threadIdx.x * 1e-6, b = a + 0.2, c = a + 0.3, d = a + 0.4;
+  double a = (OP == 0 || OP == 5 || OP == 7 || OP == 8 ? 0.1 : 2.1) + threadIdx.x * 1e-6, b = a + 0.2, c = a + 0.3, d = a + 0.4;
   for (int i = 0; i < iters; ++i) {
     a = call_op<OP>(a); b = call_op<OP>(b); c = call_op<OP>(c); d = call_op<OP>(d);
   }
@@ -64,7 +70,7 @@ extern "C" lb_status logbessel_measure_fp64(double* rates, void* cuda_stream) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   lb_status status = LB_OK;
-  for (int which = 0; which < 8 && status == LB_OK; ++which) {
+  for (int which = 0; which < 11 && status == LB_OK; ++which) {
     const int iters = which == 0 ? 1000 : (which == 5 ? 40 : 160);
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
@@ -77,7 +83,10 @@ extern "C" lb_status logbessel_measure_fp64(double* rates, void* cuda_stream) {
         case 4: peak_call<3><<<blocks, threads, 0, st>>>(buf, iters); break;
         case 5: peak_call<4><<<blocks, threads, 0, st>>>(buf, iters); break;
         case 6: peak_call<5><<<blocks, threads, 0, st>>>(buf, iters); break;
-        default: peak_call<6><<<blocks, threads, 0, st>>>(buf, iters); break;
+        case 7: peak_call<6><<<blocks, threads, 0, st>>>(buf, iters); break;
+        case 8: peak_call<7><<<blocks, threads, 0, st>>>(buf, iters); break;
+        case 9: peak_call<8><<<blocks, threads, 0, st>>>(buf, iters); break;
+        default: peak_call<9><<<blocks, threads, 0, st>>>(buf, iters); break;
       }
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) { status = LB_ECUDA; break; }

@@ -149,7 +149,10 @@ __global__ void lb_math_kernel(int which, const double* __restrict__ in, double*
       case 2: r = exp(a); break;
       case 3: r = log(a); break;
       case 4: r = log(cyl_bessel_i0(a)); break;
-      default: r = log(cyl_bessel_i1(a)); break;
+      case 5: r = log(cyl_bessel_i1(a)); break;
+      case 6: r = fm_exp_term(a); break;
+      case 7: r = ix_exp(a); break;
+      default: r = ix_log(a); break;
     }
     out[i] = r;
   }
@@ -490,7 +493,7 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
 }
 
 lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t n, void* cuda_stream) {
-  if (which < 0 || which > 5) return fail(LB_EINVAL, "which must be 0..5 (got %s%lld)", "", (long long)which);
+  if (which < 0 || which > 8) return fail(LB_EINVAL, "which must be 0..8 (got %s%lld)", "", (long long)which);
   if (n < 0 || (n > 0 && (!in || !out))) return fail(LB_EINVAL, "bad buffer or size %s%lld", "", (long long)n);
   if (n == 0) return LB_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;

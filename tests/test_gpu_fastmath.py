@@ -48,6 +48,17 @@ def test_exp(cuda):
     np.testing.assert_array_equal(got[fb], lib[fb])
 
 
+def test_exp_term(cuda):
+    """The exp of the quadrature terms (no low table part): within 2 ulp; y < -708 flushes to 0."""
+    rng = np.random.default_rng(3)
+    a = np.concatenate([rng.uniform(-707, 707, 4000), rng.uniform(-40, 0, 2000), rng.uniform(-1e-3, 1e-3, 500),
+                        [0.0, -0.0, 1e-300]])
+    got = _eval(6, a, cuda)
+    ref = _ref(oracle.dd_exp, a)
+    assert _ulps(got, ref).max() <= 2
+    np.testing.assert_array_equal(_eval(6, np.array([-708.5, -745.0, -1e300]), cuda), 0.0)
+
+
 def test_log(cuda):
     rng = np.random.default_rng(2)
     a = np.concatenate([np.exp(rng.uniform(-700, 700, 4000)), rng.uniform(0.5, 2.0, 3000),
@@ -67,3 +78,16 @@ def test_log_fallbacks(cuda):
     got = _eval(1, a, cuda)
     lib = _eval(3, a, cuda)
     np.testing.assert_array_equal(got, lib)
+
+
+def test_integer_pipe_exp_log_bit_exact(cuda):
+    """The integer-pipe exp and log on the GPU give the same bits as their host
+    build (which the CPU suite holds to 0.51 ulp of the oracle)."""
+    from intmath_host import ix_exp, ix_log
+    rng = np.random.default_rng(21)
+    y = np.concatenate([rng.uniform(-708, 708, 50000), rng.uniform(-1, 1, 20000), -np.exp(rng.uniform(-60, 6, 20000)),
+                        [0.0, -0.0, 1e-300, -708.5, 708.5, 700.0]])
+    np.testing.assert_array_equal(_eval(7, y, cuda), ix_exp(y))
+    z = np.concatenate([np.exp(rng.uniform(-708, 709, 50000)), rng.uniform(0.5, 2.0, 20000),
+                        1.0 + rng.uniform(-1e-9, 1e-9, 5000), [1.0, 2.0, 0.5, np.e, 1e-300, 1e300]])
+    np.testing.assert_array_equal(_eval(8, z, cuda), ix_log(z))
