@@ -1,0 +1,215 @@
+// lb_intmath.cuh -- double-precision exp and log computed on the integer pipes.
+//
+// On GB300 the FP64 pipe retires 2 operations per SM per clock, while the
+// integer pipes retire 64 each; a kernel whose FP64 work is mostly exp and
+// log (the K integral: two exps and a log per quadrature node) is bound by
+// the FP64 pipe with the integer pipes idle.  These versions follow the
+// table-driven methods of P. T. P. Tang ("Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2),
+// 1989; "... of the logarithm function ...", ACM TOMS 16(4), 1990) -- table
+// reduction, a short polynomial, reconstruction -- but carry every step in
+// 64- and 128-bit fixed-point integers (tables from gen_intmath.py), and
+// build the double result from its bit fields.  No FP64 instruction is
+// executed; ix_exp spends two FP32 instructions to estimate its reduction
+// index.
+//
+//   ix_exp(y), y <= 708:  y = (k/512) ln2 + r, |r| <= 0.61 ln2/512, with k
+//     estimated in single precision and r = y - k ln2/512 exact in Q116;
+//     e^r - 1 by a degree-5 polynomial in Q62/Q73; 2^(j/512)(1 + p) in Q62,
+//     j = k mod 512; 2^(k div 512) into the exponent field.  Error below
+//     0.51 ulp.  |y| < 2^-64 gives 1; y < -708 gives 0; y > 708 gives +inf.
+//   ix_log(z), z positive and normal:  z = 2^e m, m in [1, 2); j = the top
+//     9 fraction bits, r = m C_j / 2^13 - 1 exact (|r| < 2^-9.8; C_0 = 2^13
+//     and C_511 = 2^12 keep arguments next to 1 exact), log(1 + r) by a
+//     degree-6 polynomial, and e ln2 - log(C_j / 2^13) + log(1 + r) summed
+//     in Q116 (128 bits): error below 0.51 ulp.  Other arguments (zero,
+//     negative, subnormal, infinite, NaN) go to the libm log.
+//
+// The functions are plain integer code: compiled for the host (without
+// __CUDACC__) they give bit-identical results, which the CPU test suite
+// checks against the oracle's double-double exp and log.
+#pragma once
+
+#include <stdint.h>
+#include <math.h>
+
+#if defined(__CUDACC__)
+#define LB_IX_FN __device__ __forceinline__
+#define LB_IX_TABLE static __device__ const
+#define LB_IX_LOAD(p) __ldg(p)
+#else
+#include <string.h>
+#define LB_IX_FN static inline
+#define LB_IX_TABLE static const
+#define LB_IX_LOAD(p) (*(p))
+#endif
+
+#include "intmath_tables.h"
+
+namespace lb {
+
+LB_IX_FN int64_t ix_mulhi(int64_t a, int64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __mul64hi(a, b);
+#else
+  return (int64_t)(((__int128)a * (__int128)b) >> 64);
+#endif
+}
+
+LB_IX_FN uint64_t ix_umulhi(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+#endif
+}
+
+LB_IX_FN int ix_clz(uint64_t a) {
+#if defined(__CUDA_ARCH__)
+  return __clzll((long long)a);
+#else
+  return a ? __builtin_clzll(a) : 64;
+#endif
+}
+
+LB_IX_FN uint64_t ix_bits(double d) {
+#if defined(__CUDA_ARCH__)
+  return (uint64_t)__double_as_longlong(d);
+#else
+  uint64_t b;
+  memcpy(&b, &d, 8);
+  return b;
+#endif
+}
+
+LB_IX_FN double ix_double(uint64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  memcpy(&d, &b, 8);
+  return d;
+#endif
+}
+
+LB_IX_FN float ix_float(uint32_t b) {
+#if defined(__CUDA_ARCH__)
+  return __int_as_float((int)b);
+#else
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+
+LB_IX_FN uint32_t ix_fbits(float f) {
+#if defined(__CUDA_ARCH__)
+  return (uint32_t)__float_as_int(f);
+#else
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  return b;
+#endif
+}
+
+LB_IX_FN double ix_exp(double y) {
+  const uint64_t b = ix_bits(y);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const bool neg = (b >> 63) != 0;
+  if (E < 959) return 1.0;                                  // |y| < 2^-64 (and zeros, subnormals)
+  if (((uint32_t)(b >> 32) & 0x7fffffffu) > 0x40862000u) return neg ? 0.0 : INFINITY;   // |y| > 708 (or NaN)
+  // |y| in Q116 (exact: the 53-bit significand shifted left by E - 959 <= 73)
+  const uint64_t M = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
+  const int s = E - 959;
+  uint64_t yhi, ylo;
+  if (s >= 64) { yhi = M << (s - 64); ylo = 0; }
+  else { yhi = s ? M >> (64 - s) : 0; ylo = M << s; }
+  // k ~ rint(|y| 512 / ln2) from a single-precision copy of |y| (24 bits, truncated)
+  const float yf = ix_float((uint32_t)((E - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+  const uint32_t ak = ix_fbits(fmaf(yf, 738.65986f, 12582912.0f)) - 0x4B400000u;   // 1.5 2^23 shift
+  // r = |y| - k ln2/512 in Q116, then Q73
+  const uint64_t klo = (uint64_t)ak * LB_IX_L512_LO;
+  const uint64_t khi = (uint64_t)ak * LB_IX_L512_HI + ix_umulhi((uint64_t)ak, LB_IX_L512_LO);
+  const uint64_t rlo = ylo - klo;
+  const uint64_t rhi = yhi - khi - (ylo < klo ? 1u : 0u);
+  int64_t r = (int64_t)((rhi << 21) | (rlo >> 43));
+  int k = (int)ak;
+  if (neg) { r = -r; k = -k; }
+  // e^r - 1 = r (1 + r (1/2 + r (1/6 + r (1/24 + r/120)))), coefficients in Q62, r in Q73
+  int64_t a = LB_IX_E5;
+  a = LB_IX_E4 + (ix_mulhi(a, r) >> 9);
+  a = LB_IX_E3 + (ix_mulhi(a, r) >> 9);
+  a = LB_IX_E2 + (ix_mulhi(a, r) >> 9);
+  a = LB_IX_E1 + (ix_mulhi(a, r) >> 9);
+  const int64_t p = ix_mulhi(a, r);                         // Q71
+  const int64_t t = (int64_t)LB_IX_LOAD(lb_ix_exp_t + (k & 511));   // 2^(j/512), Q62
+  const int64_t res = t + (ix_mulhi(t, p) >> 7);            // Q62, in [0.999, 2.002)
+  const int lz = ix_clz((uint64_t)res);                     // 1 or 2
+  const uint64_t m53 = (((uint64_t)res << (lz - 1)) + (1ull << 9)) >> 10;   // [2^52, 2^53]
+  const int biased = (k >> 9) + 1024 - lz;
+  if (biased <= 0) return 0.0;
+  return ix_double(((uint64_t)(biased - 1) << 52) + m53);
+}
+
+LB_IX_FN double ix_log(double z) {
+  const uint64_t b = ix_bits(z);
+  const uint32_t hi = (uint32_t)(b >> 32);
+  if (hi < 0x00100000u || hi >= 0x7ff00000u) return log(z);   // <= 0, subnormal, inf, NaN
+  const int e = (int)(hi >> 20) - 1023;
+  const uint64_t F = b & 0x000fffffffffffffull;
+  const int j = (int)(F >> 43);
+  const uint64_t M = F | 0x0010000000000000ull;
+  // r = m C_j / 2^13 - 1 in Q65: the low 64 bits of M C_j (the product is 2^65 (1 + r))
+  const int64_t r = (int64_t)(M * (uint64_t)LB_IX_LOAD(lb_ix_log_c + j));
+  // log(1 + r) = r (1 - r (1/2 - r (1/3 - r (1/4 - r (1/5 - r/6))))), Q62
+  int64_t a = LB_IX_L6;
+  a = LB_IX_L5 - (ix_mulhi(a, r) >> 1);
+  a = LB_IX_L4 - (ix_mulhi(a, r) >> 1);
+  a = LB_IX_L3 - (ix_mulhi(a, r) >> 1);
+  a = LB_IX_L2 - (ix_mulhi(a, r) >> 1);
+  a = LB_IX_L1 - (ix_mulhi(a, r) >> 1);
+  // p = a r as a full product (Q127), moved to Q116
+  const int64_t phi = ix_mulhi(a, r);
+  const uint64_t plo = (uint64_t)a * (uint64_t)r;
+  uint64_t slo = (plo >> 11) | ((uint64_t)phi << 53);
+  int64_t shi = phi >> 11;
+  // + table entry -log(C_j / 2^13), Q116
+  {
+    const uint64_t tlo = LB_IX_LOAD(lb_ix_log_tlo + j);
+    const int64_t thi = LB_IX_LOAD(lb_ix_log_thi + j);
+    const uint64_t lo = slo + tlo;
+    shi = shi + thi + (lo < slo ? 1 : 0);
+    slo = lo;
+  }
+  // + e ln2, Q116
+  if (e != 0) {
+    const uint64_t ae = (uint64_t)(e < 0 ? -e : e);
+    uint64_t llo = ae * LB_IX_LN2_LO;
+    uint64_t lhi = ae * LB_IX_LN2_HI + ix_umulhi(ae, LB_IX_LN2_LO);
+    if (e < 0) {
+      llo = ~llo + 1;
+      lhi = ~lhi + (llo == 0 ? 1 : 0);
+    }
+    const uint64_t lo = slo + llo;
+    shi = (int64_t)((uint64_t)shi + lhi + (lo < slo ? 1 : 0));
+    slo = lo;
+  }
+  // to double: sign, magnitude, normalise, round to 53 bits
+  uint64_t sign = 0, mhi = (uint64_t)shi, mlo = slo;
+  if (shi < 0) {
+    sign = 0x8000000000000000ull;
+    mlo = ~mlo + 1;
+    mhi = ~mhi + (mlo == 0 ? 1 : 0);
+  }
+  if ((mhi | mlo) == 0) return 0.0;
+  const int lz = mhi ? ix_clz(mhi) : 64 + ix_clz(mlo);
+  uint64_t top;                                             // bits 127 - lz .. 64 - lz
+  if (lz == 0) top = mhi;
+  else if (lz < 64) top = (mhi << lz) | (mlo >> (64 - lz));
+  else top = mlo << (lz - 64);
+  const uint64_t m53 = (top >> 11) + ((top >> 10) & 1u);    // [2^52, 2^53] (no overflow at top ~ 2^64)
+  const int biased = 11 - lz + 1023;                        // value = top 2^(11 - lz - 63)
+  return ix_double(sign | (((uint64_t)(biased - 1) << 52) + m53));
+}
+
+}  // namespace lb

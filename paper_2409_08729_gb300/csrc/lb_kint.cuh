@@ -29,6 +29,7 @@
 #pragma once
 
 #include "lb_expr.cuh"
+#include "lb_intmath.cuh"
 #include "kquad_tables.h"
 
 namespace lb {
@@ -63,8 +64,11 @@ __device__ __forceinline__ int kint_rule(double v, double x) {
 // lanes of the warp: returns on every lane its part of the shifted sums
 // s0 = sum_j e^{L_j - mm} and s1 = sum_j e^{L_j - mm} / (s_j + 2x) (DX), with
 // the common shift mm (the warp maximum of L, taken on the integer pipe).
+// The node exps and logs run on the integer pipes (lb_intmath.cuh); log beta,
+// common to the g nodes, multiplies their partial sums instead of entering
+// every node (any shift is exact, and beta <= 16 cannot overflow them).
 template <bool DX>
-__device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta, double logbeta, int ng, int hr,
+__device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta, int ng, int hr,
                                                 int lane, double& mm, double& s0, double& s1) {
   const double vm = v - 0.5, tx = 2.0 * x;
   const double* gu = ng == 32 ? lb_kq_g32_logu : lb_kq_g64_logu;
@@ -79,10 +83,10 @@ __device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta,
   for (int k = 0; k < 2; ++k) {
     L[k] = 0.0;
     A[k] = 0.0;
-    if (32 * k < ng) {                             // g node: log w + 7 log u + log beta - u^beta + (v-1/2) log(2x + u^beta)
+    if (32 * k < ng) {                             // g node: log w + 7 log u - u^beta + (v-1/2) log(2x + u^beta)
       const int j = lane + 32 * k;
-      const double ub = fm_exp_le(beta * __ldg(gu + j));
-      L[k] = fma(vm, fm_log(tx + ub), __ldg(gc + j) + logbeta) - ub;
+      const double ub = ix_exp(beta * __ldg(gu + j));
+      L[k] = fma(vm, ix_log(tx + ub), __ldg(gc + j)) - ub;
       if (DX) A[k] = 1.0 / (tx + ub);
       key = max(key, order_key(L[k]));
     }
@@ -94,23 +98,29 @@ __device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta,
     A[2 + k] = 0.0;
     if (j < nh) {                                  // h node: c + (v-1/2)(log s + log(s + 2x))
       const double sj = __ldg(hs + j);
-      L[2 + k] = fma(vm, __ldg(hy + j) + fm_log(sj + tx), __ldg(hc + j));
+      L[2 + k] = fma(vm, __ldg(hy + j) + ix_log(sj + tx), __ldg(hc + j));
       if (DX) A[2 + k] = 1.0 / (sj + tx);
       key = max(key, order_key(L[2 + k]));
     }
   }
   mm = key_to_double(__reduce_max_sync(0xffffffffu, key));
-  s0 = 0.0;
-  s1 = 0.0;
+  double g0 = 0.0, g1 = 0.0, h0 = 0.0, h1 = 0.0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const bool live = (k < 2) ? (32 * k < ng) : (lane + 32 * (k - 2) < nh);
     if (live) {
-      const double t = fm_exp_le(L[k] - mm);
-      s0 += t;
-      if (DX) s1 = fma(t, A[k], s1);
+      const double t = ix_exp(L[k] - mm);
+      if (k < 2) {
+        g0 += t;
+        if (DX) g1 = fma(t, A[k], g1);
+      } else {
+        h0 += t;
+        if (DX) h1 = fma(t, A[k], h1);
+      }
     }
   }
+  s0 = fma(beta, g0, h0);
+  s1 = DX ? fma(beta, g1, h1) : 0.0;
 }
 
 // Split g rule (v < 0.4, x < 1e-3).  (2x + u^beta)^(v-1/2) turns within a
@@ -136,11 +146,11 @@ __device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta,
 // 3 = [y1 + 8, y1 + 40]; 4 = [-40, -4]; 5 = the 32 h nodes (v < 0.4, so h
 // is the 32-node rule in log s).
 template <bool DX>
-__device__ __forceinline__ void kint_sums_split(double v, double x, double beta, double logbeta, int lane,
+__device__ __forceinline__ void kint_sums_split(double v, double x, double beta, int lane,
                                                 double& mm, double& s0, double& s1) {
   const double vm = v - 0.5, vp = v + 0.5, tx = 2.0 * x;
   const double sx = 128.0 * x;                     // s1 (exact)
-  const double y1 = fm_log(sx);
+  const double y1 = ix_log(sx);
   const double C = 2.0 * v * y1;
   double L[6], A[6];
   bool live[6], rel[6];
@@ -148,9 +158,9 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
 #pragma unroll
   for (int k = 0; k < 2; ++k) {                    // [0, s1]: s = s1 r, r = u^beta
     const int j = lane + 32 * k;
-    const double r = fm_exp_le(beta * __ldg(lb_kq_g64_logu + j));
+    const double r = ix_exp(beta * __ldg(lb_kq_g64_logu + j));
     const double sj = sx * r;
-    L[k] = fma(vm, fm_log(r + 0.015625), __ldg(lb_kq_g64_c + j) + logbeta) - sj;
+    L[k] = fma(vm, ix_log(r + 0.015625), __ldg(lb_kq_g64_c + j)) - sj;     // less log beta, as above
     A[k] = DX ? 1.0 / (sj + tx) : 0.0;
     live[k] = true;
     rel[k] = true;
@@ -180,16 +190,16 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
     A[k] = 0.0;
     if (live[k]) {
       const double o = fma(b - a, t, a);
-      const double lwb = lw + fm_log(b - a);
+      const double lwb = lw + ix_log(b - a);
       double sj;
       if (anchored) {                              // y = y1 + o
-        const double eo = fm_exp_le(o);
+        const double eo = ix_exp(o);
         sj = sx * eo;
-        L[k] = fma(vm, fm_log(eo + 0.015625), fma(vp, o, lwb)) - sj;
+        L[k] = fma(vm, ix_log(eo + 0.015625), fma(vp, o, lwb)) - sj;
         key = max(key, order_key(L[k] + C));
       } else {                                     // y = o
-        sj = fm_exp_le(o);
-        L[k] = fma(vm, fm_log(sj + tx), fma(vp, o, lwb)) - sj;
+        sj = ix_exp(o);
+        L[k] = fma(vm, ix_log(sj + tx), fma(vp, o, lwb)) - sj;
         key = max(key, order_key(L[k]));
       }
       if (DX) A[k] = 1.0 / (sj + tx);
@@ -197,7 +207,7 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
   }
   {                                                // h nodes, 32-node rule in log s
     const double sj = __ldg(lb_kq_hl32_s + lane);
-    L[5] = fma(vm, __ldg(lb_kq_hl32_y + lane) + fm_log(sj + tx), __ldg(lb_kq_hl32_c + lane));
+    L[5] = fma(vm, __ldg(lb_kq_hl32_y + lane) + ix_log(sj + tx), __ldg(lb_kq_hl32_c + lane));
     A[5] = DX ? 1.0 / (sj + tx) : 0.0;
     live[5] = true;
     rel[5] = false;
@@ -214,23 +224,31 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
   }
   mm = key_to_double(__reduce_max_sync(0xffffffffu, key));
   const double mr = mm - C;
+  double g0 = 0.0, g1 = 0.0;
   s0 = 0.0;
   s1 = 0.0;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     if (live[k]) {
-      const double t = fm_exp_le(L[k] - (rel[k] ? mr : mm));
-      s0 += t;
-      if (DX) s1 = fma(t, A[k], s1);
+      const double t = ix_exp(L[k] - (rel[k] ? mr : mm));
+      if (k < 2) {
+        g0 += t;
+        if (DX) g1 = fma(t, A[k], g1);
+      } else {
+        s0 += t;
+        if (DX) s1 = fma(t, A[k], s1);
+      }
     }
   }
+  s0 = fma(beta, g0, s0);
+  if (DX) s1 = fma(beta, g1, s1);
   if (flat && lane == 0) {
-    s0 += fm_exp_le(Lflat - mr);
+    s0 += ix_exp(Lflat - mr);
     if (DX) {
       // there 1/(s + 2x) = e^{-y} to 1e-17: int e^{(2v-1) y} dy over the same
       // interval, less C: (2v - 1) 40 - y1 + log((1 - e^{(2v-1) w}) / (1 - 2v))
       const double c = 2.0 * v - 1.0;
-      s1 += fm_exp_le(fma(40.0, c, -y1) + fm_log(-expm1(c * w) / -c) - mr);
+      s1 += ix_exp(fma(40.0, c, -y1) + fm_log(-expm1(c * w) / -c) - mr);
     }
   }
 }
@@ -249,19 +267,17 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
 template <bool DX>
 __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane) {
   const double beta_i = 16.0 / (2.0 * vi + 1.0);
-  const double logbeta_i = fm_log(beta_i);
   const int rule_i = kint_rule(vi, xi);
   double m_i = 0.0, s0_i = 1.0, s1_i = 0.0;
   for (int e = 0; e < npairs; ++e) {
     const double v = __shfl_sync(0xffffffffu, vi, e);
     const double x = __shfl_sync(0xffffffffu, xi, e);
     const double beta = __shfl_sync(0xffffffffu, beta_i, e);
-    const double logbeta = __shfl_sync(0xffffffffu, logbeta_i, e);
     const int rule = __shfl_sync(0xffffffffu, rule_i, e);
     const int ng = rule & 0xff, hr = rule >> 8;
     double mm, s0, s1;
-    if (ng == 0) kint_sums_split<DX>(v, x, beta, logbeta, lane, mm, s0, s1);
-    else kint_sums_fixed<DX>(v, x, beta, logbeta, ng, hr, lane, mm, s0, s1);
+    if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1);
+    else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1);
     s0 = warp_sum(s0);
     if (DX) s1 = warp_sum(s1);
     if (lane == e) {

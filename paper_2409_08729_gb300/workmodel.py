@@ -10,7 +10,10 @@ and log of lb_fastmath.cuh are counted the same way.
 FLOP = 2 x slots (an FMA counts two).
 
 The counts follow the code paths of lb_expr.cuh and lb_kint.cuh (tight mode,
-FP64).  Term counts are the per-pair counts of the single-precision pre-pass;
+FP64).  The exps and logs of the K-integral nodes run on the integer pipes
+(lb_intmath.cuh); they are priced by the same measured rule, so the sum of
+slots is the time the kernel's operations would take one after another at
+full throughput, and frac = that time / the measured time.  Term counts are the per-pair counts of the single-precision pre-pass;
 the kernels run the maximum over each warp, so the real work is slightly
 higher than counted here.
 """
@@ -30,12 +33,16 @@ SLOT_LGAMMA = 27.6
 SLOT_EXP = 10.0
 SLOT_EXP_TERM = 9.0
 SLOT_LOG = 14.0
+# exp and log on the integer pipes (lb_intmath.cuh), priced the same way: the
+# DFMA slots that the time of one call at full throughput would hold
+SLOT_IX_EXP = 3.0
+SLOT_IX_LOG = 3.5
 
 
 def set_costs(rates):
     """Set the slot costs from measured rates (dict of operations per second,
     as returned by _binding.measure_fp64)."""
-    global SLOT_DIV, SLOT_SQRT, SLOT_RSQRT, SLOT_LGAMMA, SLOT_EXP, SLOT_EXP_TERM, SLOT_LOG
+    global SLOT_DIV, SLOT_SQRT, SLOT_RSQRT, SLOT_LGAMMA, SLOT_EXP, SLOT_EXP_TERM, SLOT_LOG, SLOT_IX_EXP, SLOT_IX_LOG
     d = rates["dfma"]
     SLOT_DIV = d / rates["div"] - 1.0
     SLOT_SQRT = SLOT_RSQRT = d / rates["sqrt"] - 1.0
@@ -44,8 +51,11 @@ def set_costs(rates):
     SLOT_LOG = d / rates["fm_log"] - 1.0
     if "fm_exp_term" in rates:
         SLOT_EXP_TERM = d / rates["fm_exp_term"] - 1.0
+    if "ix_exp" in rates:
+        SLOT_IX_EXP = d / rates["ix_exp"] - 1.0
+        SLOT_IX_LOG = d / rates["ix_log"] - 1.0
     return {"div": SLOT_DIV, "sqrt": SLOT_SQRT, "lgamma": SLOT_LGAMMA, "fm_exp": SLOT_EXP,
-            "fm_exp_term": SLOT_EXP_TERM, "fm_log": SLOT_LOG}
+            "fm_exp_term": SLOT_EXP_TERM, "fm_log": SLOT_LOG, "ix_exp": SLOT_IX_EXP, "ix_log": SLOT_IX_LOG}
 
 
 REGION_K = {0: 20, 1: 13, 4: 3, 5: 4, 6: 6, 7: 9}   # region id -> number of expansion terms
@@ -64,17 +74,18 @@ def kint_rule(v, x):
 
 
 def kint_slots(v, x):
-    """FP64 slots of one K-integral evaluation per pair (tight Gauss rule)."""
+    """Work of one K-integral evaluation per pair (tight Gauss rule), in DFMA
+    slots; the node exps and logs are the integer-pipe ones."""
     ng, nh = kint_rule(v, x)
     split = ng > 64
-    # g node: beta*log u, exp, add, log, add, fma, subtract; then exp(L - m), accumulate
+    # g node: beta*log u, exp, 2x + u^beta, log, fma, - u^beta; then L - m, exp, accumulate
     # (split rule: 3 more for the offset form: s1 * r, the shift by C, the key add)
-    g_node = 7 + 2 * SLOT_EXP_TERM + SLOT_LOG + np.where(split, 3, 0)
-    # h node: s + 2x, log, + y, fma; then subtract, exp, accumulate
-    h_node = 1 + SLOT_LOG + 1 + 1 + 1 + SLOT_EXP_TERM + 1
-    # per pair (once per lane of its batch): beta (div), log beta, prefactor
-    # (lgamma, log, 3 ops), final log; the warp sum (5 adds, all lanes)
-    per_pair = SLOT_DIV + SLOT_LOG + SLOT_LGAMMA + SLOT_LOG + 3 + SLOT_LOG + 2 + 5
+    g_node = 6 + 2 * SLOT_IX_EXP + SLOT_IX_LOG + np.where(split, 3, 0)
+    # h node: s + 2x, log, + y, fma; then L - m, exp, accumulate
+    h_node = 5 + SLOT_IX_EXP + SLOT_IX_LOG
+    # per pair (once per lane of its batch): beta (div), prefactor (lgamma,
+    # log, 3 ops), final log and beta g + h; the warp sum (5 adds, all lanes)
+    per_pair = SLOT_DIV + SLOT_LGAMMA + SLOT_LOG + 3 + SLOT_LOG + 2 + 1 + 5
     # split rule: log s1, C, three panel widths (log + add each), the flat term (log, expm1, division)
     per_pair = per_pair + np.where(split, 2 + 4 * SLOT_LOG + 3 + SLOT_EXP + SLOT_DIV + 4, 0)
     return ng * g_node + nh * h_node + per_pair

@@ -1,0 +1,80 @@
+"""Integer-pipe exp and log (csrc/lb_intmath.cuh), host build, against the
+oracle's double-double exp and log: within 0.51 ulp of the exact value."""
+import numpy as np
+import pytest
+
+import oracle
+from intmath_host import ix_exp, ix_log
+
+
+def _ref(fn, a):
+    out = np.empty((a.size, 2))
+    for i, v in enumerate(a):
+        out[i] = fn(float(v))
+    return out
+
+
+def _ulp_err(got, ref):
+    return np.abs((got - ref[:, 0]) - ref[:, 1]) / np.spacing(np.abs(ref[:, 0]))
+
+
+def test_exp_accuracy():
+    rng = np.random.default_rng(11)
+    y = np.concatenate([rng.uniform(-708, 708, 20000), rng.uniform(-1, 1, 5000), rng.uniform(-1e-3, 1e-3, 2000),
+                        np.exp(rng.uniform(-40, 3, 3000)) * rng.choice([-1.0, 1.0], 3000),
+                        np.log(2.0) / 512 * (np.arange(-600, 600) + 0.5),        # reduction boundaries
+                        [0.5, -0.5, np.log(2.0), -np.log(2.0), 700.0, -700.0, 708.0, -708.0]])
+    e = _ulp_err(ix_exp(y), _ref(oracle.dd_exp, y))
+    assert e.max() < 0.51, (e.max(), y[e.argmax()])
+
+
+def test_exp_special():
+    got = ix_exp(np.array([0.0, -0.0, 1e-300, -1e-300, 2.0 ** -70, -708.5, -745.0, -1e300, 708.5]))
+    assert list(got[:5]) == [1.0] * 5
+    assert list(got[5:8]) == [0.0] * 3
+    assert got[8] == np.inf
+
+
+def test_log_accuracy():
+    rng = np.random.default_rng(12)
+    z = np.concatenate([np.exp(rng.uniform(-708, 709, 20000)), rng.uniform(0.5, 2.0, 5000),
+                        1.0 + rng.uniform(-1e-3, 1e-3, 2000), 1.0 + rng.uniform(-1e-9, 1e-9, 1000),
+                        1.0 + np.arange(1, 200) * 2.0 ** -52, 1.0 - np.arange(1, 200) * 2.0 ** -53,
+                        1.0 + np.arange(512) / 512.0, 2.0 ** np.arange(-1022, 1024, 37),
+                        [2.0 ** -1022, 1.7976931348623157e308, 3.0, 10.0, np.e]])
+    ref = _ref(oracle.dd_log, z)
+    e = _ulp_err(ix_log(z), ref)
+    assert e.max() < 0.51, (e.max(), z[e.argmax()])
+
+
+def test_results_next_to_powers_of_two():
+    """Results just below and above a power of two (the rounding carry of the
+    53-bit significand into the exponent)."""
+    k = np.arange(-12, 10)
+    nudge = np.array([-3, -2, -1, 0, 1, 2, 3])
+    z = np.exp(2.0 ** k)[:, None] * (1.0 + nudge[None, :] * 2.0 ** -52)
+    z = np.concatenate([z.ravel(), [np.nextafter(np.e, 0), np.nextafter(np.e, 4)]])
+    e = _ulp_err(ix_log(z), _ref(oracle.dd_log, z))
+    assert e.max() < 0.51, (e.max(), z[e.argmax()])
+    y = (np.arange(-1000, 1000) * np.log(2.0))[:, None] * (1.0 + nudge[None, :] * 2.0 ** -52)
+    y = y.ravel()
+    y = y[np.abs(y) <= 708]
+    e = _ulp_err(ix_exp(y), _ref(oracle.dd_exp, y))
+    assert e.max() < 0.51, (e.max(), y[e.argmax()])
+
+
+def test_log_special():
+    got = ix_log(np.array([1.0, 2.0, 0.5, 0.0, -1.0, np.inf, 5e-324]))
+    assert got[0] == 0.0
+    assert got[1] == np.log(2.0) and got[2] == -np.log(2.0)
+    assert got[3] == -np.inf and np.isnan(got[4]) and got[5] == np.inf
+    assert got[6] == np.log(5e-324)          # subnormal: the libm log
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_exp_log_roundtrip(seed):
+    """log(exp(y)) returns y to within the rounding of exp (|y| <= 700)."""
+    rng = np.random.default_rng(seed)
+    y = rng.uniform(-700, 700, 20000)
+    back = ix_log(ix_exp(y))
+    assert np.max(np.abs(back - y) / np.maximum(np.abs(y), 1.0)) < 4e-16
