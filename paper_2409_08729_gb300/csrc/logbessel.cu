@@ -34,11 +34,20 @@ using namespace lb;
 
 namespace {
 
+// Resident CTAs per SM the two kernels are built and launched for (launch
+// bounds and persistent grid sizes: a multiple of the SM count).
+#ifndef LB_TILES_CTAS_PER_SM
+#define LB_TILES_CTAS_PER_SM 6
+#endif
+#ifndef LB_KINT_CTAS_PER_SM
+#define LB_KINT_CTAS_PER_SM 3
+#endif
+
 // Tile kernel: classify, bin per region in shared memory, evaluate the
 // per-thread expressions (lb_tile.cuh); K fallback pairs go to a global queue
 // for lb_kint_kernel.  T = double (FP64) or float (FP32-mixed).
 template <int KIND, bool DX, typename T>
-__global__ void __launch_bounds__(LB_THREADS)
+__global__ void __launch_bounds__(LB_THREADS, LB_TILES_CTAS_PER_SM)
 lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
                 int64_t n, int mode, int forced_region, unsigned int* __restrict__ qcount,
                 uint32_t* __restrict__ queue) {
@@ -64,7 +73,7 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
 
 // K integral: one warp per queued pair, 32 pairs per warp batch.
 template <bool GAUSS, bool DX, typename T>
-__global__ void __launch_bounds__(LB_THREADS, 2)
+__global__ void __launch_bounds__(LB_THREADS, LB_KINT_CTAS_PER_SM)
 lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
                const unsigned int* __restrict__ qcount, const uint32_t* __restrict__ queue) {
   const unsigned int cnt = *qcount;
@@ -277,7 +286,7 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
   const int sms = sm_count();
   const int64_t ntiles_all = (n + LB_TILE - 1) / LB_TILE;
   if (KIND == KIND_I || (forced_region >= 0 && forced_region != R_FALLBACK)) {
-    const int grid = (int)(ntiles_all < (int64_t)sms * 4 ? ntiles_all : (int64_t)sms * 4);
+    const int grid = (int)(ntiles_all < (int64_t)sms * LB_TILES_CTAS_PER_SM ? ntiles_all : (int64_t)sms * LB_TILES_CTAS_PER_SM);
     return launch(PS_TILES, st, [&] {
       lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region,
                                                                  nullptr, nullptr);
@@ -304,7 +313,7 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
     const T* xc = x + c0;
     T* oc = out + c0;
     const int64_t ntiles = (cn + LB_TILE - 1) / LB_TILE;
-    const int grid = (int)(ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4);
+    const int grid = (int)(ntiles < (int64_t)sms * LB_TILES_CTAS_PER_SM ? ntiles : (int64_t)sms * LB_TILES_CTAS_PER_SM);
     status = launch(PS_TILES, st, [&] {
       lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount, queue);
     });
