@@ -10,7 +10,8 @@ in 64- and 128-bit integers instead of doubles:
        C_511 = 2^12 exactly, so that arguments next to 1 keep their relative
        accuracy), and -log(C_j / 2^13) in Q116 (128 bits, signed); ln 2 in
        Q116 (the entry for j = 511 is this same constant).
-  Horner coefficients of e^r - 1 and log(1 + r) in Q62.
+  Horner coefficients of e^r - 1 and log(1 + r) in Q31 (inner steps, done
+  with 32-bit multiplies) and Q62.
 """
 import os
 import sys
@@ -69,9 +70,17 @@ def main():
     hi, lo = split128(ln2)
     L.append("#define LB_IX_LN2_HI %dull" % hi)
     L.append("#define LB_IX_LN2_LO 0x%016xull" % lo)
-    for k in range(1, 6):               # e^r - 1 = r (1 + r (1/2 + r (1/6 + r (1/24 + r/120))))
+    # e^r - 1 = r (1 + r (1/2 + r (1/6 + r (1/24 + r/120)))): the inner three
+    # coefficients in Q31 (32-bit steps), the outer two in Q62
+    for k in (3, 4, 5):
+        L.append("#define LB_IX_E%d %d" % (k, q(1 / mp.factorial(k), 31)))
+    for k in (1, 2):
         L.append("#define LB_IX_E%d %dll" % (k, q(1 / mp.factorial(k), 62)))
-    for k in range(1, 7):               # log(1 + r) = r (1 - r (1/2 - r (1/3 - ... - r/6)))
+    # log(1 + r) = r (1 - r (1/2 - r (1/3 - r (1/4 - r (1/5 - r/6))))): 1/4..1/6
+    # in Q31, 1/1..1/3 in Q62
+    for k in (4, 5, 6):
+        L.append("#define LB_IX_L%d %d" % (k, q(mp.mpf(1) / k, 31)))
+    for k in (1, 2, 3):
         L.append("#define LB_IX_L%d %dll" % (k, q(mp.mpf(1) / k, 62)))
     with open(out, "w") as f:
         f.write("\n".join(L) + "\n")

@@ -15,7 +15,8 @@
 //
 //   ix_exp(y), y <= 708:  y = (k/512) ln2 + r, |r| <= 0.61 ln2/512, with k
 //     estimated in single precision and r = y - k ln2/512 exact in Q116;
-//     e^r - 1 by a degree-5 polynomial in Q62/Q73; 2^(j/512)(1 + p) in Q62,
+//     e^r - 1 by a degree-5 polynomial (inner steps in 32 bits, outer in
+//     Q62, r in Q73); 2^(j/512)(1 + p) in Q62,
 //     j = k mod 512; 2^(k div 512) into the exponent field.  Error below
 //     0.51 ulp.  |y| < 2^-64 gives 1; y < -708 gives 0; y > 708 gives +inf.
 //   ix_log(z), z positive and normal:  z = 2^e m, m in [1, 2); j = the top
@@ -62,6 +63,23 @@ LB_IX_FN uint64_t ix_umulhi(uint64_t a, uint64_t b) {
 #else
   return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
 #endif
+}
+
+// high 32 bits of a 32 x 32-bit signed product
+LB_IX_FN int32_t ix_mulhi32(int32_t a, int32_t b) {
+#if defined(__CUDA_ARCH__)
+  return __mulhi(a, b);
+#else
+  return (int32_t)(((int64_t)a * (int64_t)b) >> 32);
+#endif
+}
+
+// floor(a b / 2^32) for a signed 64-bit a and a signed 32-bit b (|a b| < 2^95):
+// two 32 x 32 -> 64-bit products instead of a 64 x 64 one.
+LB_IX_FN int64_t ix_mul64x32hi(int64_t a, int32_t b) {
+  const int64_t hi = (int64_t)(int32_t)(a >> 32) * (int64_t)b;
+  const int64_t lo = (int64_t)((uint64_t)(uint32_t)a * (uint64_t)(int64_t)b);   // (a mod 2^32) b, exact in 64 bits
+  return hi + (lo >> 32);
 }
 
 LB_IX_FN int ix_clz(uint64_t a) {
@@ -127,19 +145,23 @@ LB_IX_FN double ix_exp(double y) {
   // k ~ rint(|y| 512 / ln2) from a single-precision copy of |y| (24 bits, truncated)
   const float yf = ix_float((uint32_t)((E - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
   const uint32_t ak = ix_fbits(fmaf(yf, 738.65986f, 12582912.0f)) - 0x4B400000u;   // 1.5 2^23 shift
-  // r = |y| - k ln2/512 in Q116, then Q73
-  const uint64_t klo = (uint64_t)ak * LB_IX_L512_LO;
-  const uint64_t khi = (uint64_t)ak * LB_IX_L512_HI + ix_umulhi((uint64_t)ak, LB_IX_L512_LO);
+  // r = |y| - k ln2/512 in Q116, then Q73 (k < 2^20: 64 x 32-bit products)
+  const uint64_t k0 = (uint64_t)ak * (LB_IX_L512_LO & 0xffffffffull);
+  const uint64_t k1 = (uint64_t)ak * (LB_IX_L512_LO >> 32);
+  const uint64_t klo = k0 + (k1 << 32);
+  const uint64_t khi = (uint64_t)ak * LB_IX_L512_HI + (k1 >> 32) + (klo < k0 ? 1u : 0u);
   const uint64_t rlo = ylo - klo;
   const uint64_t rhi = yhi - khi - (ylo < klo ? 1u : 0u);
   int64_t r = (int64_t)((rhi << 21) | (rlo >> 43));
   int k = (int)ak;
   if (neg) { r = -r; k = -k; }
-  // e^r - 1 = r (1 + r (1/2 + r (1/6 + r (1/24 + r/120)))), coefficients in Q62, r in Q73
-  int64_t a = LB_IX_E5;
-  a = LB_IX_E4 + (ix_mulhi(a, r) >> 9);
-  a = LB_IX_E3 + (ix_mulhi(a, r) >> 9);
-  a = LB_IX_E2 + (ix_mulhi(a, r) >> 9);
+  // e^r - 1 = r (1 + r (1/2 + r (1/6 + r (1/24 + r/120)))).  The steps for
+  // 1/24 and 1/6 enter the result times r^3 (|r| < 2^-10.4), so 32-bit
+  // precision (Q31, r in Q41) suffices there; 1/2 and 1 are carried in Q62.
+  const int32_t r32 = (int32_t)(r >> 32);                   // Q41
+  int32_t a3 = LB_IX_E4 + (ix_mulhi32(LB_IX_E5, r32) >> 9);
+  a3 = LB_IX_E3 + (ix_mulhi32(a3, r32) >> 9);
+  int64_t a = LB_IX_E2 + (ix_mul64x32hi(r, a3) >> 10);      // r a3 in Q72
   a = LB_IX_E1 + (ix_mulhi(a, r) >> 9);
   const int64_t p = ix_mulhi(a, r);                         // Q71
   const int64_t t = (int64_t)LB_IX_LOAD(lb_ix_exp_t + (k & 511));   // 2^(j/512), Q62
@@ -161,11 +183,13 @@ LB_IX_FN double ix_log(double z) {
   const uint64_t M = F | 0x0010000000000000ull;
   // r = m C_j / 2^13 - 1 in Q65: the low 64 bits of M C_j (the product is 2^65 (1 + r))
   const int64_t r = (int64_t)(M * (uint64_t)LB_IX_LOAD(lb_ix_log_c + j));
-  // log(1 + r) = r (1 - r (1/2 - r (1/3 - r (1/4 - r (1/5 - r/6))))), Q62
-  int64_t a = LB_IX_L6;
-  a = LB_IX_L5 - (ix_mulhi(a, r) >> 1);
-  a = LB_IX_L4 - (ix_mulhi(a, r) >> 1);
-  a = LB_IX_L3 - (ix_mulhi(a, r) >> 1);
+  // log(1 + r) = r (1 - r (1/2 - r (1/3 - r (1/4 - r (1/5 - r/6))))).  The
+  // steps for 1/5 and 1/4 enter the result times r^4 (|r| < 2^-9.8): 32-bit
+  // precision (Q31, r in Q33) suffices there; 1/3, 1/2 and 1 in Q62.
+  const int32_t r32 = (int32_t)(r >> 32);                   // Q33
+  int32_t a4 = LB_IX_L5 - (ix_mulhi32(LB_IX_L6, r32) >> 1);
+  a4 = LB_IX_L4 - (ix_mulhi32(a4, r32) >> 1);
+  int64_t a = LB_IX_L3 - (ix_mul64x32hi(r, a4) >> 2);       // r a4 in Q64
   a = LB_IX_L2 - (ix_mulhi(a, r) >> 1);
   a = LB_IX_L1 - (ix_mulhi(a, r) >> 1);
   // p = a r as a full product (Q127), moved to Q116
@@ -183,9 +207,11 @@ LB_IX_FN double ix_log(double z) {
   }
   // + e ln2, Q116
   if (e != 0) {
-    const uint64_t ae = (uint64_t)(e < 0 ? -e : e);
-    uint64_t llo = ae * LB_IX_LN2_LO;
-    uint64_t lhi = ae * LB_IX_LN2_HI + ix_umulhi(ae, LB_IX_LN2_LO);
+    const uint64_t ae = (uint64_t)(e < 0 ? -e : e);       // < 2^11: 64 x 32-bit products
+    const uint64_t l0 = ae * (LB_IX_LN2_LO & 0xffffffffull);
+    const uint64_t l1 = ae * (LB_IX_LN2_LO >> 32);
+    uint64_t llo = l0 + (l1 << 32);
+    uint64_t lhi = ae * LB_IX_LN2_HI + (l1 >> 32) + (llo < l0 ? 1u : 0u);
     if (e < 0) {
       llo = ~llo + 1;
       lhi = ~lhi + (llo == 0 ? 1 : 0);

@@ -47,7 +47,7 @@ __device__ __forceinline__ double warp_sum(double a) {
 
 // log of the prefactor sqrt(pi) e^{-x} / (Gamma(v+1/2) (2x)^v)
 __device__ __forceinline__ double kint_prefactor(double v, double x) {
-  return kHalfLogPi - lgamma(v + 0.5) - fma(v, fm_log(2.0 * x), x);
+  return kHalfLogPi - lgamma(v + 0.5) - fma(v, ix_log(2.0 * x), x);
 }
 
 // Node counts of the tight rule for one pair, packed as (g rule) | (h rule << 8):
@@ -287,7 +287,7 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     }
   }
   if (DX) return -(vi / xi + 1.0) + (2.0 * vi - 1.0) * (s1_i / s0_i);
-  return kint_prefactor(vi, xi) + m_i + fm_log(s0_i);
+  return kint_prefactor(vi, xi) + m_i + ix_log(s0_i);
 }
 
 // Warp-cooperative log int_0^1 (g + h) du by the paper's Simpson rule (N = 600).

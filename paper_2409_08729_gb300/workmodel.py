@@ -85,7 +85,7 @@ def kint_slots(v, x):
     h_node = 5 + SLOT_IX_EXP + SLOT_IX_LOG
     # per pair (once per lane of its batch): beta (div), prefactor (lgamma,
     # log, 3 ops), final log and beta g + h; the warp sum (5 adds, all lanes)
-    per_pair = SLOT_DIV + SLOT_LGAMMA + SLOT_LOG + 3 + SLOT_LOG + 2 + 1 + 5
+    per_pair = SLOT_DIV + SLOT_LGAMMA + SLOT_IX_LOG + 3 + SLOT_IX_LOG + 2 + 1 + 5
     # split rule: log s1, C, three panel widths (log + add each), the flat term (log, expm1, division)
     per_pair = per_pair + np.where(split, 2 + 4 * SLOT_LOG + 3 + SLOT_EXP + SLOT_DIV + 4, 0)
     return ng * g_node + nh * h_node + per_pair
@@ -110,15 +110,15 @@ def mu_terms(v, x, K=20):
 
 def mu_slots(v, x, K=20):
     # per term: fma, multiply, fma; plus 4v^2, 1/(8x), S^2 and two products, log, fma
-    return mu_terms(v, x, K) * 3 + 2 + SLOT_DIV + 3 + SLOT_LOG + 1
+    return mu_terms(v, x, K) * 3 + 2 + SLOT_DIV + 3 + SLOT_IX_LOG + 1
 
 
 def u_slots(K):
     # 1/v, x/v, fma, rsqrt, r = r2 t, t*t, t/v, sum_k k Horner fmas of P_k, K in q,
-    # eta (add, div, log, add), tail (3 multiplies, log, 2 multiplies, fma)
+    # eta (add, two logs, subtract, add), tail (3 multiplies, log, 2 multiplies, fma)
     horner = sum(k for k in range(1, K + 1)) + K
     return (SLOT_DIV + 1 + 1 + SLOT_RSQRT + 1 + 1 + 1 + horner
-            + 1 + SLOT_DIV + SLOT_LOG + 1 + 3 + SLOT_LOG + 3)
+            + 1 + 2 * SLOT_IX_LOG + 1 + 1 + 3 + SLOT_IX_LOG + 3)
 
 
 def series_terms(v, x):
@@ -145,7 +145,7 @@ def series_terms(v, x):
 def series_slots(v, x):
     # per term: k + v, multiply, fma, multiply, int->double; plus A/B, log, lgamma, log(x/2), fma
     n = series_terms(v, x)
-    return n * 5 + SLOT_DIV + SLOT_LOG + SLOT_LGAMMA + SLOT_LOG + 3
+    return n * 5 + SLOT_DIV + SLOT_IX_LOG + SLOT_LGAMMA + SLOT_IX_LOG + 3
 
 
 def region_slots(region, v, x):
