@@ -32,6 +32,7 @@ struct TileShared {
   int counts[8];
   unsigned int qbase;
   uint16_t wcount[LB_ITEMS][LB_THREADS / 32][8];   // pairs per (item round, warp, region), then offsets
+  int next_chunk[8];                               // per region: next chunk of 32 pairs to hand out (tile_eval)
 };
 
 template <int KIND, bool DX, typename T>
@@ -142,29 +143,46 @@ __device__ __forceinline__ void tile_bin(TileShared<T>& S, const T* __restrict__
 #pragma unroll
   for (int it = 0; it < LB_ITEMS; ++it)
     if (reg[it] >= 0) S.lists[reg[it]][S.wcount[it][warp][reg[it]] + rank[it]] = (uint16_t)(it * LB_THREADS + tid);
+  if (tid < 8) S.next_chunk[tid] = 0;
   __syncthreads();
 }
 
-// Per-thread expressions, one region at a time.  The loop bound is uniform
-// per warp (some expressions reduce across the warp); lanes past the end of
-// a list recompute the warp's first entry and do not store.  The K fallback
-// list is left for tile_kint or a queue.
+// The chunks (32 pairs, one warp each) of region R's list, handed out from a
+// shared counter: a warp that runs out moves on to the next region while the
+// others finish this one.  Lanes past the end of the list recompute the
+// chunk's first entry and do not store.
+template <int KIND, bool DX, typename T, int R>
+__device__ __forceinline__ void tile_eval_region(TileShared<T>& S, T* __restrict__ out, int64_t t0, int lane) {
+  const int c = S.counts[R];
+  const int nch = (c + 31) >> 5;
+  for (;;) {
+    int id = 0;
+    if (lane == 0) id = atomicAdd(&S.next_chunk[R], 1);
+    id = __shfl_sync(0xffffffffu, id, 0);
+    if (id >= nch) break;
+    const int j0 = id << 5, j = j0 + lane;
+    const bool ok = j < c;
+    const int li = S.lists[R][ok ? j : j0];
+    const T val = tile_expr<KIND, DX, T>(R, S.sv[li], S.sx[li]);
+    if (ok) out[t0 + li] = val;
+  }
+}
+
+// Per-thread expressions, region by region, costliest first (so that the
+// last chunks of a tile are cheap and the warps reach the closing barrier
+// close together); every warp runs a single expression at a time, and the
+// result of a pair does not depend on which warp takes its chunk.  The K
+// fallback list is left for tile_kint or a queue.
 template <int KIND, bool DX, typename T>
 __device__ __forceinline__ void tile_eval(TileShared<T>& S, T* __restrict__ out, int64_t t0) {
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  for (int r = 0; r < 8; ++r) {
-    if (r == R_SPECIAL) continue;
-    if (KIND == KIND_K && r == R_FALLBACK) continue;
-    const int c = S.counts[r];
-    for (int j0 = tid - lane; j0 < c; j0 += LB_THREADS) {
-      const int j = j0 + lane;
-      const bool ok = j < c;
-      const int li = S.lists[r][ok ? j : j0];
-      const T val = tile_expr<KIND, DX, T>(r, S.sv[li], S.sx[li]);
-      if (ok) out[t0 + li] = val;
-    }
-  }
+  const int lane = threadIdx.x & 31;
+  if (KIND == KIND_I) tile_eval_region<KIND, DX, T, R_FALLBACK>(S, out, t0, lane);
+  tile_eval_region<KIND, DX, T, R_U13>(S, out, t0, lane);
+  tile_eval_region<KIND, DX, T, R_U9>(S, out, t0, lane);
+  tile_eval_region<KIND, DX, T, R_MU20>(S, out, t0, lane);
+  tile_eval_region<KIND, DX, T, R_U6>(S, out, t0, lane);
+  tile_eval_region<KIND, DX, T, R_MU3>(S, out, t0, lane);
+  tile_eval_region<KIND, DX, T, R_U4>(S, out, t0, lane);
 }
 
 // K integral of a batch of up to 32 pairs by one warp: lane e holds pair e;
