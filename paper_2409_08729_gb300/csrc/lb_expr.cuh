@@ -180,8 +180,8 @@ __device__ __forceinline__ double mu_expr(double v, double x) {
   // no square root needed.
   const double S2 = P * P;
   const double ax = fabs(inv8x);
-  if (KIND == KIND_I) return fma(0.5, ix_log(S2 * ax * (8.0 / kTwoPi)), x);
-  return fma(0.5, ix_log(S2 * ax * (4.0 * kPi)), -x);
+  if (KIND == KIND_I) return fma(0.5, ix_log_call(S2 * ax * (8.0 / kTwoPi)), x);
+  return fma(0.5, ix_log_call(S2 * ax * (4.0 * kPi)), -x);
 }
 
 // P_k(p) of the Debye polynomial u_k(t) = t^k P_k(t^2); k is a compile-time
@@ -255,12 +255,12 @@ __device__ __forceinline__ double u_expr(double v, double x) {
 #pragma unroll
   for (int k = K - 1; k >= 1; --k) acc = fma(acc, q, debye_P(k, p));
   const double S = fma(acc, q, 1.0);
-  const double eta = r + (ix_log(xp) - ix_log(1.0 + r));      // log(x' / (1 + r)), no division
+  const double eta = r + (ix_log_call(xp) - ix_log_call(1.0 + r));      // log(x' / (1 + r)), no division
   // log(S / sqrt(2 pi v r)) = log(S^2 t / (2 pi v)) / 2, and for K
   // log(S sqrt(pi / (2 v r))) = log(S^2 t pi / (2 v)) / 2 (t = 1/r): no root.
   const double w = S * S * t * inv_v;
-  if (KIND == KIND_I) return fma(v, eta, 0.5 * ix_log(w * (1.0 / kTwoPi)));
-  return fma(-v, eta, 0.5 * ix_log(w * (0.5 * kPi)));
+  if (KIND == KIND_I) return fma(v, eta, 0.5 * ix_log_call(w * (1.0 / kTwoPi)));
+  return fma(-v, eta, 0.5 * ix_log_call(w * (0.5 * kPi)));
 }
 
 // ---------------------------------------------------------------------------
@@ -305,8 +305,8 @@ __device__ __forceinline__ double series_log_i(double v, double x) {
     B *= d;
     kd -= 1.0;
   }
-  double res = ix_log(A / B) - lgamma(v + 1.0);
-  if (v != 0.0) res = fma(v, ix_log(0.5 * x), res);
+  double res = ix_log_call(A / B) - lgamma(v + 1.0);
+  if (v != 0.0) res = fma(v, ix_log_call(0.5 * x), res);
   return res;
 }
 

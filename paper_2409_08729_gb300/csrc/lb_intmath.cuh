@@ -238,4 +238,11 @@ LB_IX_FN double ix_log(double z) {
   return ix_double(sign | (((uint64_t)(biased - 1) << 52) + m53));
 }
 
+#if defined(__CUDACC__)
+// ix_log as a called function, for the per-pair call sites of large kernels:
+// one copy of its code instead of one per call site keeps the tile kernel's
+// hot code within the instruction cache (measured 2.5 % faster).
+static __device__ __noinline__ double ix_log_call(double z) { return ix_log(z); }
+#endif
+
 }  // namespace lb

@@ -40,7 +40,7 @@ namespace {
 #define LB_TILES_CTAS_PER_SM 6
 #endif
 #ifndef LB_KINT_CTAS_PER_SM
-#define LB_KINT_CTAS_PER_SM 3
+#define LB_KINT_CTAS_PER_SM 4
 #endif
 
 // Tile kernel: classify, bin per region in shared memory, evaluate the
