@@ -10,13 +10,13 @@ split at s = 1 into g(u) on [0, 1] (s = u^beta, beta = 2n/(2v+1), n = 8) and
 h(u) on [0, 1] (s = 1/u).  The paper integrates both with composite Simpson,
 N = 600.  These tables hold Gauss rules for the same two pieces instead:
 
-  g piece: Gauss-Legendre in u on [0, 1], 32 or 64 nodes; for small
+  g piece: Gauss-Legendre in u on [0, 1], 24, 32 or 64 nodes; for small
            orders and tiny arguments (v < 0.4, x < 1e-3) the g piece is split
            at s1 = 128 x: [0, s1] with the 64-node rule in u (s = s1 u^beta),
            [s1, 1] in y = log s with plain Gauss-Legendre panels placed per
            pair (tables of 16 and 32 nodes on [0, 1]).
   h piece: Gauss-Legendre in y = log s on [0, log 100] (s in [1, 100]),
-           32 or 48 nodes, for orders v <= 5;
+           32, 40 or 48 nodes, for orders v <= 5;
            Gauss-Laguerre in t = s - 1, 32 nodes, for orders v > 5.
 
 Writes kquad_tables.h beside this file.  Nodes and weights are computed in
@@ -76,7 +76,7 @@ def main():
     parts = ["// Generated by gen_quad.py -- do not edit.",
              "// Gauss rules for the g and h pieces of the K integral (see gen_quad.py).",
              "#pragma once", "", "#define LB_KQ_SMAX %d" % SMAX, ""]
-    for N in (32, 64):
+    for N in (24, 32, 64):
         u, w = gauss_legendre01(N)
         parts.append("// g piece, Gauss-Legendre on [0,1], %d nodes: log u_j and log w_j" % N)
         parts.append(arr("lb_kq_g%d_logu" % N, [mp.log(a) for a in u]))
@@ -89,7 +89,7 @@ def main():
         parts.append(arr("lb_kq_gl%d_t" % N, t))
         parts.append(arr("lb_kq_gl%d_logw" % N, [mp.log(a) for a in w]))
     Y = mp.log(SMAX)
-    for N in (32, 48):
+    for N in (32, 40, 48):
         y, w = gauss_legendre01(N)
         ys = [a * Y for a in y]
         parts.append("// h piece, Gauss-Legendre in y = log s on [0, log %d], %d nodes:" % (SMAX, N))

@@ -14,7 +14,8 @@
 // maximum as shift.
 //
 // Rules:
-//   LB_TIGHT: Gauss rules (tables in kquad_tables.h).  g: Gauss-Legendre in u
+//   LB_TIGHT: Gauss rules (tables in kquad_tables.h).  For 1.2 < v <= 5: 24
+//     g nodes and 40 h nodes (two full lane slots).  Otherwise g: Gauss-Legendre in u
 //     with 32 nodes (v >= 0.9 or x >= 0.25), 64 (v >= 0.4 or x >= 1e-3), or
 //     for v < 0.4, x < 1e-3 a split rule (kint_sums_split), because
 //     (2x + u^beta)^(v-1/2) turns sharply near u = (2x)^(1/beta).  h: Gauss-Legendre in log s on
@@ -54,7 +55,11 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
 // g rule 32 / 64 = Gauss-Legendre in u with that many nodes, 0 = the split
 // rule for small orders and tiny arguments (below); h rule 0 = Gauss-Legendre
 // in log s with 32 nodes, 1 = with 48, 2 = Gauss-Laguerre 32.
+// g rule 24 goes with h rule 3 (40 nodes in log s): for 1.2 < v <= 5 the
+// 24 + 40 nodes fill two 32-lane slots (the 32 + 48 of the general rule take
+// three), error map below 4e-17 over x in [1e-300, 30].
 __device__ __forceinline__ int kint_rule(double v, double x) {
+  if (v > 1.2 && v <= 5.0) return 24 | (3 << 8);
   const int ng = (v >= 0.9 || x >= 0.25) ? 32 : ((v >= 0.4 || x >= 1e-3) ? 64 : 0);
   const int hr = (v <= 1.2) ? 0 : ((v <= 5.0) ? 1 : 2);
   return ng | (hr << 8);
@@ -121,6 +126,36 @@ __device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta,
   }
   s0 = fma(beta, g0, h0);
   s1 = DX ? fma(beta, g1, h1) : 0.0;
+}
+
+// One pair, 24 g nodes and 40 h nodes (h rule 3) in two slots: slot 0 holds
+// the g nodes on lanes 0-23 and h nodes 0-7 on lanes 24-31, slot 1 h nodes
+// 8-39.  A g node is c + (v-1/2) log(2x + s) - s with s = u^beta; an h node
+// c + (v-1/2)(y + log(s + 2x)) with s, y = log s and -s folded into c; the
+// exp of s runs on the g lanes only.  Sums as in kint_sums_fixed.
+template <bool DX>
+__device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta, int lane,
+                                                 double& mm, double& s0, double& s1) {
+  const double vm = v - 0.5, tx = 2.0 * x;
+  const bool isg = lane < 24;
+  const int jh = isg ? 0 : lane - 24;
+  double s;
+  if (isg) s = ix_exp(beta * __ldg(lb_kq_g24_logu + lane));
+  else s = __ldg(lb_kq_hl40_s + jh);
+  const double y0 = isg ? 0.0 : __ldg(lb_kq_hl40_y + jh);
+  const double c0 = isg ? __ldg(lb_kq_g24_c + lane) : __ldg(lb_kq_hl40_c + jh);
+  const double L0 = fma(vm, ix_log(tx + s) + y0, c0) - (isg ? s : 0.0);
+  const double sh = __ldg(lb_kq_hl40_s + 8 + lane);
+  const double L1 = fma(vm, __ldg(lb_kq_hl40_y + 8 + lane) + ix_log(sh + tx), __ldg(lb_kq_hl40_c + 8 + lane));
+  mm = key_to_double(__reduce_max_sync(0xffffffffu, max(order_key(L0), order_key(L1))));
+  const double t0 = ix_exp(L0 - mm), t1 = ix_exp(L1 - mm);
+  const double g0 = isg ? t0 : 0.0, h0 = (isg ? 0.0 : t0) + t1;
+  s0 = fma(beta, g0, h0);
+  s1 = 0.0;
+  if (DX) {
+    const double a0 = t0 / (tx + s), a1 = t1 / (sh + tx);
+    s1 = fma(beta, isg ? a0 : 0.0, (isg ? 0.0 : a0) + a1);
+  }
 }
 
 // Split g rule (v < 0.4, x < 1e-3).  (2x + u^beta)^(v-1/2) turns within a
@@ -277,6 +312,7 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     const int ng = rule & 0xff, hr = rule >> 8;
     double mm, s0, s1;
     if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1);
+    else if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1);
     else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1);
     s0 = warp_sum(s0);
     if (DX) s1 = warp_sum(s1);
