@@ -119,6 +119,24 @@ __device__ __forceinline__ float kint_gauss32(float v, float x, int lane) {
   const float beta = 16.0f / (2.0f * v + 1.0f);
   const float logbeta = logf(beta);
   const float vm = v - 0.5f, vp = v + 0.5f, tx = 2.0f * x;
+  if (v > 1.2f && v <= 5.0f) {
+    // 24 g + 40 h nodes in two lane slots (as kint_sums_g24h40)
+    const bool isg = lane < 24;
+    const int jh = isg ? 0 : lane - 24;
+    const float s = isg ? expf(beta * __ldg(lb_kqf_g24_logu + lane)) : __ldg(lb_kqf_hl40_s + jh);
+    const float y0 = isg ? 0.0f : __ldg(lb_kqf_hl40_y + jh);
+    const float c0 = isg ? __ldg(lb_kqf_g24_c + lane) + logbeta : __ldg(lb_kqf_hl40_c + jh);
+    const float L0 = fmaf(vm, logf(tx + s) + y0, c0) - (isg ? s : 0.0f);
+    const float sh = __ldg(lb_kqf_hl40_s + 8 + lane);
+    const float L1 = fmaf(vm, __ldg(lb_kqf_hl40_y + 8 + lane) + logf(sh + tx), __ldg(lb_kqf_hl40_c + 8 + lane));
+    float m = fmaxf(L0, L1);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    float sum = expf(L0 - m) + expf(L1 - m);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    return m + logf(sum);
+  }
   const int ng = (v >= 0.9f || x >= 0.25f) ? 32 : ((v >= 0.4f || x >= 1e-3f) ? 64 : 0);
   const float *hs, *hy, *hc;
   int nh;
