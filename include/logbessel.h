@@ -97,6 +97,30 @@ lb_status logbessel_k(lb_dtype dtype, const void* v, int64_t v_stride, const voi
                       int64_t n, lb_mode mode, void* cuda_stream);
 
 /*
+ * Caller-supplied workspace.  The K entry points queue the pairs that take
+ * the integral (the fallback region) in device scratch: 256 bytes for a
+ * counter plus 4 bytes per pair of a pass.  logbessel_k and logbessel_k_dx
+ * take it from the stream-ordered allocator; these variants take it from the
+ * caller and allocate nothing.
+ *
+ * logbessel_workspace_bytes(n): the bytes that evaluate n pairs in one pass,
+ * 256 + 4 min(n, 2^26) (0 for n < 0).
+ * logbessel_k_ws / logbessel_k_dx_ws: as logbessel_k / logbessel_k_dx, with
+ * `workspace` a device pointer (256-byte aligned) to `ws_bytes` bytes, at
+ * least 4352 (1024 pairs per pass); n pairs are processed in passes of
+ * (ws_bytes - 256) / 4 pairs rounded down to a multiple of 1024 (at most
+ * 2^26), with results identical to one pass.  The workspace is used in
+ * stream order on cuda_stream: other work must not use it until the call's
+ * work has finished.  LB_EINVAL (nothing enqueued) for a NULL, misaligned
+ * or too small workspace; other errors as the plain entry points.
+ */
+int64_t logbessel_workspace_bytes(int64_t n);
+lb_status logbessel_k_ws(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out, int64_t n,
+                         lb_mode mode, void* workspace, int64_t ws_bytes, void* cuda_stream);
+lb_status logbessel_k_dx_ws(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out, int64_t n,
+                            lb_mode mode, void* workspace, int64_t ws_bytes, void* cuda_stream);
+
+/*
  * log K_v(x) like logbessel_k (FP64 only), but without allocating any device
  * memory.  The paper has no counterpart: this entry point exists for callers
  * that cannot let a library allocate, such as code that runs under a device

@@ -33,6 +33,12 @@ def lib():
             f = getattr(L, name)
             f.argtypes = [i32, vp, i64, vp, vp, i64, i32, vp]
             f.restype = i32
+        L.logbessel_workspace_bytes.argtypes = [i64]
+        L.logbessel_workspace_bytes.restype = i64
+        for name in ("logbessel_k_ws", "logbessel_k_dx_ws"):
+            f = getattr(L, name)
+            f.argtypes = [i32, vp, i64, vp, vp, i64, i32, vp, i64, vp]
+            f.restype = i32
         L.logbessel_host.argtypes = [i32, i32, vp, i64, vp, vp, i64, i32, i64]
         L.logbessel_host.restype = i32
         L.logbessel_vmf_log_c.argtypes = [i32, ctypes.c_double, vp, vp, i64, i32, vp]

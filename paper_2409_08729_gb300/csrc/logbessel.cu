@@ -432,6 +432,47 @@ lb_status logbessel_k_noalloc(lb_dtype dtype, const void* v, int64_t v_stride, c
                                          -1, (cudaStream_t)cuda_stream, scratch, LB_NOALLOC_MAX_PAIRS);
 }
 
+int64_t logbessel_workspace_bytes(int64_t n) {
+  if (n < 0) return 0;
+  return 256 + 4 * (n < kChunk ? n : kChunk);
+}
+
+lb_status logbessel_k_ws(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out, int64_t n,
+                         lb_mode mode, void* workspace, int64_t ws_bytes, void* cuda_stream) {
+  lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
+  if (s != LB_OK) return s;
+  if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < 256 + 4 * 1024)
+    return fail(LB_EINVAL, "%sworkspace must be non-NULL, 256-byte aligned and at least 4352 bytes (got %lld)", "",
+                (long long)ws_bytes);
+  if (n == 0) return LB_OK;
+  // passes start on tile boundaries, so the results equal those of one pass
+  const int64_t cap0 = (ws_bytes - 256) / 4;
+  const int64_t cap = ((cap0 < kChunk ? cap0 : kChunk) / LB_TILE) * LB_TILE;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (dtype == LB_F32)
+    return run_impl<KIND_K, false, float>((const float*)v, v_stride, (const float*)x, (float*)out, n, (int)mode, -1,
+                                          st, workspace, cap);
+  return run_impl<KIND_K, false, double>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode,
+                                         -1, st, workspace, cap);
+}
+
+lb_status logbessel_k_dx_ws(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out, int64_t n,
+                            lb_mode mode, void* workspace, int64_t ws_bytes, void* cuda_stream) {
+  lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
+  if (s != LB_OK) return s;
+  if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < 256 + 4 * 1024)
+    return fail(LB_EINVAL, "%sworkspace must be non-NULL, 256-byte aligned and at least 4352 bytes (got %lld)", "",
+                (long long)ws_bytes);
+  if (n == 0) return LB_OK;
+  if (dtype != LB_F64) return fail(LB_ENOTSUP, "%sthe derivatives are implemented for LB_F64 only", "", 0);
+  if (mode != LB_TIGHT) return fail(LB_ENOTSUP, "%sd/dx log K is implemented for LB_TIGHT only", "", 0);
+  // passes start on tile boundaries, so the results equal those of one pass
+  const int64_t cap0 = (ws_bytes - 256) / 4;
+  const int64_t cap = ((cap0 < kChunk ? cap0 : kChunk) / LB_TILE) * LB_TILE;
+  return run_impl<KIND_K, true, double>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
+                                        (cudaStream_t)cuda_stream, workspace, cap);
+}
+
 lb_status logbessel_classify(int kind, lb_dtype dtype, const void* v, int64_t v_stride,
                              const void* x, uint8_t* region_out, int64_t n, lb_mode mode,
                              void* cuda_stream) {

@@ -85,3 +85,21 @@ def test_python_api_requires_cuda_tensors():
     import paper_2409_08729_gb300 as lb
     with pytest.raises((ValueError, TypeError)):
         lb.log_i(1.0, torch.ones(3, dtype=torch.float64))
+
+
+def test_workspace_entry_points_validate(L):
+    """Workspace size rule and argument checks of the caller-workspace K entry points (no launch)."""
+    from paper_2409_08729_gb300 import _binding as B
+    assert L.logbessel_workspace_bytes(0) == 256
+    assert L.logbessel_workspace_bytes(1000) == 256 + 4000
+    assert L.logbessel_workspace_bytes(1 << 30) == 256 + 4 * (1 << 26)
+    assert L.logbessel_workspace_bytes(-1) == 0
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.cast(buf, ctypes.c_void_p).value
+    for fn in (L.logbessel_k_ws, L.logbessel_k_dx_ws):
+        assert fn(B.LB_F64, p, 1, p, p, 5, 0, None, 1 << 20, None) == B.LB_EINVAL     # NULL workspace
+        assert b"workspace" in L.logbessel_last_error()
+        assert fn(B.LB_F64, p, 1, p, p, 5, 0, 256 * 3 + 8, 1 << 20, None) == B.LB_EINVAL   # misaligned
+        assert fn(B.LB_F64, p, 1, p, p, 5, 0, 256 * 3, 1000, None) == B.LB_EINVAL         # too small
+        assert fn(B.LB_F64, p, 1, p, p, -1, 0, 256 * 3, 1 << 20, None) == B.LB_EINVAL     # n < 0
+        assert fn(B.LB_F64, p, 1, p, p, 0, 0, 256 * 3, 1 << 20, None) == B.LB_OK          # nothing to do
