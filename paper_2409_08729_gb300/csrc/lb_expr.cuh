@@ -153,12 +153,16 @@ __device__ __forceinline__ double mu_expr(double v, double x) {
   // single-precision estimate of the number of terms
   int n = K;
   {
-    const float muf = 4.0f * (float)v * (float)v, inv8xf = 1.0f / (8.0f * (float)x);
+    // unrolled, so (2k-1)^2 and 1/k are constants: no division, no branch
+    const float muf = 4.0f * (float)v * (float)v, inv8xf = __fdividef(1.0f, 8.0f * (float)x);
     float t = 1.0f;
-#pragma unroll 1
+    bool found = false;
+#pragma unroll
     for (int k = 1; k <= K; ++k) {
-      t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * inv8xf / (float)k;
-      if (fabsf(t) < 1.4e-17f) { n = k; break; }
+      t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * (inv8xf * (1.0f / (float)k));
+      const bool hit = !found && fabsf(t) < 1.4e-17f;
+      n = hit ? k : n;
+      found = found || hit;
     }
   }
   n = __reduce_max_sync(0xffffffffu, n);
@@ -285,13 +289,14 @@ __device__ __forceinline__ double series_log_i(double v, double x) {
   {
     const float yf = 0.25f * (float)x * (float)x, vf = (float)v;
     const float kpk = 0.5f * (sqrtf(fmaf((float)x, (float)x, vf * vf)) - vf);
-    float term = 1.0f, T = 0.0f;
+    float term = 1.0f, T = 0.0f, kf = 0.0f;
 #pragma unroll 1
     for (int k = 1; k <= 90; ++k) {
-      term *= yf / ((float)k * ((float)k + vf));
+      kf += 1.0f;
+      term *= __fdividef(yf, kf * (kf + vf));      // an estimate: the fast division suffices
       T += term;
       n = k;
-      if ((float)k > kpk && term <= 1.4e-17f * (1.0f + T)) break;
+      if (kf > kpk && term <= 1.4e-17f * (1.0f + T)) break;
     }
   }
   n = __reduce_max_sync(0xffffffffu, n);
