@@ -371,14 +371,15 @@ def main():
         return float(np.mean(fn(vv[sub], x_h[sub]))) * sel_idx.size
 
     tiles_slots = 0.0
-    for kind_regs in ((regions_i, vm_h, True), (ri_per, per_order_k, True),
-                      (regions_k, vm_h, False), (rk_per, per_order_k, False)):
-        regs, vv, is_i = kind_regs
+    # per-order calls pass one order for all pairs (the scalar-order path)
+    for kind_regs in ((regions_i, vm_h, True, False), (ri_per, per_order_k, True, True),
+                      (regions_k, vm_h, False, False), (rk_per, per_order_k, False, True)):
+        regs, vv, is_i, scalar = kind_regs
         for rid in (0, 1, 2, 4, 5, 6, 7):
             if rid == 2 and not is_i:
                 continue
             sel = np.flatnonzero(regs == rid)
-            tiles_slots += sampled_sum(lambda a, b, r=rid: WM.region_slots(r, a, b), sel, vv)
+            tiles_slots += sampled_sum(lambda a, b, r=rid, sc=scalar: WM.region_slots(r, a, b, sc), sel, vv)
     work_slots = {"lb_kint_kernel": kint_slots, "lb_tiles_kernel": tiles_slots}
     # DRAM traffic of the K-integral kernel: 37 B per queued pair (one ncu
     # capture, profiles/lb_kint_kernel_sweep_small.md), scaled to the pairs of

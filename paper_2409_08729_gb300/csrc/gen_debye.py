@@ -82,6 +82,14 @@ def render_header(polys):
         cs = p_coeffs(k, polys)
         lines.append("// P_%d(p), coefficients ascending: %s" % (k, ", ".join(str(c) for c in cs)))
         lines += _horner(cs, "lb_debye_P%d" % k)
+    lines.append("// The same coefficients as a table: lb_debye_c[k][i] = coefficient of t^(k+2i)")
+    lines.append("// in u_k(t) (k = 0..13, i = 0..k; zero beyond), for sums formed per block.")
+    rows = []
+    for k in range(KMAX + 1):
+        cs = p_coeffs(k, polys) if k > 0 else [Fraction(1)]
+        rows.append("  {" + ", ".join(repr(float(c)) for c in cs + [Fraction(0)] * (KMAX + 1 - len(cs))) + "}")
+    lines.append("static __device__ const double lb_debye_c[%d][%d] = {\n%s};" % (KMAX + 1, KMAX + 1, ",\n".join(rows)))
+    lines.append("")
     lines.append("// Q_k(p) = k P_k(p) + 2 p P_k'(p): d/dt u_k(t) = t^(k-1) Q_k(t^2)")
     lines.append("")
     for k in range(1, KMAX + 1):

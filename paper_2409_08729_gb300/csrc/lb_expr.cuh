@@ -316,6 +316,139 @@ __device__ __forceinline__ double series_log_i(double v, double x) {
 }
 
 // ---------------------------------------------------------------------------
+// One order for every argument (v_stride 0).  The order-dependent parts of
+// the expressions are then the same for every pair, and a block computes
+// them once (scalar_order_setup):
+//   mu_K:   S = sum_k a_k w^k, w = 1/(8x), a_k = s^k prod_{j<=k} (mu - (2j-1)^2) / k!
+//           -- one FMA per term instead of three;
+//   series: P <- 1 + (y / (k (k + v))) P with the reciprocals 1/(k (k + v))
+//           tabulated -- two operations per term instead of six, and
+//           lgamma(v + 1) once;
+//   U_K:    S(t) = 1 + sum_k (s/v)^k u_k(t) = sum_m C_m t^m as one polynomial
+//           of degree 3K in t -- 3K FMAs instead of K(K+3)/2, and 1/v once.
+// The sums are the same sums in another order of operations.
+// ---------------------------------------------------------------------------
+struct ScalarOrder {
+  double v, inv_v, lg1;                 // v, 1/v, lgamma(v + 1)
+  double mu[21];                        // a_0..a_20 (sign s of the kind folded in)
+  double ser[91];                       // 1 / (k (k + v)), k = 1..90
+  double u4[13], u6[19], u9[28], u13[40];   // C_0..C_3K
+};
+
+// All threads of the block call it; ends with a barrier.
+template <int KIND>
+__device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    so.v = v;
+    so.inv_v = 1.0 / v;
+    so.lg1 = lgamma(v + 1.0);
+    const double mu = 4.0 * v * v, s = KIND == KIND_I ? -1.0 : 1.0;
+    double a = 1.0;
+    so.mu[0] = 1.0;
+    for (int k = 1; k <= 20; ++k) {
+      a = a * (s * (mu - (double)((2 * k - 1) * (2 * k - 1)))) / (double)k;
+      so.mu[k] = a;
+    }
+  } else if (tid <= 90) {
+    so.ser[tid] = 1.0 / ((double)tid * ((double)tid + v));
+  } else if (tid >= 128 && tid < 228) {
+    // C_m of U_K: the coefficients of t^m, sum over k + 2i = m of c_{k,i} (s/v)^k
+    int j = tid - 128, K, m;
+    double* dst;
+    if (j < 13) { K = 4; m = j; dst = so.u4; }
+    else if (j < 32) { K = 6; m = j - 13; dst = so.u6; }
+    else if (j < 60) { K = 9; m = j - 32; dst = so.u9; }
+    else { K = 13; m = j - 60; dst = so.u13; }
+    const double sv = (KIND == KIND_I ? 1.0 : -1.0) / v;
+    double c = 0.0, pk = 1.0;
+    for (int k = 0; k <= K; ++k) {
+      if (k > 0) pk *= sv;
+      const int twoi = m - k;
+      if (twoi >= 0 && (twoi & 1) == 0 && (twoi >> 1) <= k) c = fma(lb_debye_c[k][twoi >> 1], pk, c);
+    }
+    dst[m] = c;
+  }
+  __syncthreads();
+}
+
+template <int KIND>
+__device__ __forceinline__ double mu_expr_so(const ScalarOrder& so, double x) {
+  constexpr int K = 20;
+  int n = K;
+  {
+    const float muf = 4.0f * (float)so.v * (float)so.v, inv8xf = __fdividef(1.0f, 8.0f * (float)x);
+    float t = 1.0f;
+    bool found = false;
+#pragma unroll
+    for (int k = 1; k <= K; ++k) {
+      t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * (inv8xf * (1.0f / (float)k));
+      const bool hit = !found && fabsf(t) < 1.4e-17f;
+      n = hit ? k : n;
+      found = found || hit;
+    }
+  }
+  n = __reduce_max_sync(0xffffffffu, n);
+  const double w = 1.0 / (8.0 * x);
+  double P = 0.0;
+#pragma unroll
+  for (int k = K; k >= 0; --k)
+    if (k <= n) P = fma(P, w, so.mu[k]);
+  const double S2 = P * P;
+  if (KIND == KIND_I) return fma(0.5, ix_log_call(S2 * w * (8.0 / kTwoPi)), x);
+  return fma(0.5, ix_log_call(S2 * w * (4.0 * kPi)), -x);
+}
+
+template <int KIND, int K>
+__device__ __forceinline__ double u_expr_so(const ScalarOrder& so, double x) {
+  const double v = so.v, inv_v = so.inv_v;
+  const double xp = x * inv_v;
+  double r, t;
+  if (LB_LT(xp, 1e150)) {
+    const double r2 = fma(xp, xp, 1.0);
+    t = rsqrt(r2);
+    r = r2 * t;
+  } else {
+    r = xp;
+    t = 1.0 / r;
+  }
+  const double* C = K == 4 ? so.u4 : (K == 6 ? so.u6 : (K == 9 ? so.u9 : so.u13));
+  double S = C[3 * K];
+#pragma unroll
+  for (int m = 3 * K - 1; m >= 0; --m) S = fma(S, t, C[m]);
+  const double eta = r + (ix_log_call(xp) - ix_log_call(1.0 + r));
+  const double w = S * S * t * inv_v;
+  if (KIND == KIND_I) return fma(v, eta, 0.5 * ix_log_call(w * (1.0 / kTwoPi)));
+  return fma(-v, eta, 0.5 * ix_log_call(w * (0.5 * kPi)));
+}
+
+__device__ __forceinline__ double series_so(const ScalarOrder& so, double x) {
+  const double v = so.v;
+  int n = 1;
+  {
+    const float yf = 0.25f * (float)x * (float)x, vf = (float)v;
+    const float kpk = 0.5f * (sqrtf(fmaf((float)x, (float)x, vf * vf)) - vf);
+    float term = 1.0f, T = 0.0f, kf = 0.0f;
+#pragma unroll 1
+    for (int k = 1; k <= 90; ++k) {
+      kf += 1.0f;
+      term *= __fdividef(yf, kf * (kf + vf));
+      T += term;
+      n = k;
+      if (kf > kpk && term <= 1.4e-17f * (1.0f + T)) break;
+    }
+  }
+  n = __reduce_max_sync(0xffffffffu, n);
+  const double y = 0.25 * x * x;
+  double P = 1.0;
+#pragma unroll 1
+  for (int k = n; k >= 1; --k) P = fma(y * so.ser[k], P, 1.0);
+  double res = ix_log_call(P) - so.lg1;
+  if (v != 0.0) res = fma(v, ix_log_call(0.5 * x), res);
+  return res;
+}
+
+// ---------------------------------------------------------------------------
 // x-derivatives of the same expressions (the adjoint of the forward path).
 // Each differentiates its expression term by term, so it is valid exactly
 // where the expression is; the paper lists derivatives as future work

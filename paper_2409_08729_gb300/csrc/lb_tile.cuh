@@ -147,12 +147,28 @@ __device__ __forceinline__ void tile_bin(TileShared<T>& S, const T* __restrict__
   __syncthreads();
 }
 
+// The FP64 expressions with the order's constants of a ScalarOrder block.
+template <int KIND>
+__device__ __forceinline__ double tile_expr_so(int r, const ScalarOrder& so, double x) {
+  switch (r) {
+    case R_MU20: return mu_expr_so<KIND>(so, x);
+    case R_U13: return u_expr_so<KIND, 13>(so, x);
+    case R_MU3: return mu_expr<KIND, 3>(so.v, x);
+    case R_U4: return u_expr_so<KIND, 4>(so, x);
+    case R_U6: return u_expr_so<KIND, 6>(so, x);
+    case R_U9: return u_expr_so<KIND, 9>(so, x);
+    default: return (KIND == KIND_I) ? series_so(so, x) : __longlong_as_double(0x7ff8000000000000LL);
+  }
+}
+
 // The chunks (32 pairs, one warp each) of region R's list, handed out from a
 // shared counter: a warp that runs out moves on to the next region while the
 // others finish this one.  Lanes past the end of the list recompute the
-// chunk's first entry and do not store.
+// chunk's first entry and do not store.  `so` (FP64 values only) holds the
+// constants of a call whose pairs all have one order, or is NULL.
 template <int KIND, bool DX, typename T, int R>
-__device__ __forceinline__ void tile_eval_region(TileShared<T>& S, T* __restrict__ out, int64_t t0, int lane) {
+__device__ __forceinline__ void tile_eval_region(TileShared<T>& S, T* __restrict__ out, int64_t t0, int lane,
+                                                 const ScalarOrder* so) {
   const int c = S.counts[R];
   const int nch = (c + 31) >> 5;
   for (;;) {
@@ -163,7 +179,13 @@ __device__ __forceinline__ void tile_eval_region(TileShared<T>& S, T* __restrict
     const int j0 = id << 5, j = j0 + lane;
     const bool ok = j < c;
     const int li = S.lists[R][ok ? j : j0];
-    const T val = tile_expr<KIND, DX, T>(R, S.sv[li], S.sx[li]);
+    T val;
+    if constexpr (sizeof(T) == 8 && !DX) {
+      if (so) val = tile_expr_so<KIND>(R, *so, S.sx[li]);
+      else val = tile_expr<KIND, DX, T>(R, S.sv[li], S.sx[li]);
+    } else {
+      val = tile_expr<KIND, DX, T>(R, S.sv[li], S.sx[li]);
+    }
     if (ok) out[t0 + li] = val;
   }
 }
@@ -174,15 +196,16 @@ __device__ __forceinline__ void tile_eval_region(TileShared<T>& S, T* __restrict
 // result of a pair does not depend on which warp takes its chunk.  The K
 // fallback list is left for tile_kint or a queue.
 template <int KIND, bool DX, typename T>
-__device__ __forceinline__ void tile_eval(TileShared<T>& S, T* __restrict__ out, int64_t t0) {
+__device__ __forceinline__ void tile_eval(TileShared<T>& S, T* __restrict__ out, int64_t t0,
+                                          const ScalarOrder* so = nullptr) {
   const int lane = threadIdx.x & 31;
-  if (KIND == KIND_I) tile_eval_region<KIND, DX, T, R_FALLBACK>(S, out, t0, lane);
-  tile_eval_region<KIND, DX, T, R_U13>(S, out, t0, lane);
-  tile_eval_region<KIND, DX, T, R_U9>(S, out, t0, lane);
-  tile_eval_region<KIND, DX, T, R_MU20>(S, out, t0, lane);
-  tile_eval_region<KIND, DX, T, R_U6>(S, out, t0, lane);
-  tile_eval_region<KIND, DX, T, R_MU3>(S, out, t0, lane);
-  tile_eval_region<KIND, DX, T, R_U4>(S, out, t0, lane);
+  if (KIND == KIND_I) tile_eval_region<KIND, DX, T, R_FALLBACK>(S, out, t0, lane, so);
+  tile_eval_region<KIND, DX, T, R_U13>(S, out, t0, lane, so);
+  tile_eval_region<KIND, DX, T, R_U9>(S, out, t0, lane, so);
+  tile_eval_region<KIND, DX, T, R_MU20>(S, out, t0, lane, so);
+  tile_eval_region<KIND, DX, T, R_U6>(S, out, t0, lane, so);
+  tile_eval_region<KIND, DX, T, R_MU3>(S, out, t0, lane, so);
+  tile_eval_region<KIND, DX, T, R_U4>(S, out, t0, lane, so);
 }
 
 // K integral of a batch of up to 32 pairs by one warp: lane e holds pair e;

@@ -54,10 +54,19 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
   __shared__ TileShared<T> S;
   const int tid = threadIdx.x;
   const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
+  const ScalarOrder* so = nullptr;
+  if constexpr (sizeof(T) == 8 && !DX) {
+    // one order for every argument: its constants once per block
+    __shared__ ScalarOrder SO;
+    if (v_stride == 0 && forced_region < 0 && n > 0) {
+      scalar_order_setup<KIND>(SO, KIND == KIND_K ? fabs((double)v[0]) : (double)v[0]);
+      so = &SO;
+    }
+  }
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t t0 = tile * LB_TILE;
     tile_bin<KIND, DX, T>(S, v, v_stride, x, out, t0, n, mode, forced_region);
-    tile_eval<KIND, DX, T>(S, out, t0);
+    tile_eval<KIND, DX, T>(S, out, t0, so);
     if (KIND == KIND_K) {
       const int c = S.counts[R_FALLBACK];
       if (c > 0) {

@@ -149,12 +149,32 @@ def series_slots(v, x):
     return n * 6 + SLOT_DIV + SLOT_IX_LOG + SLOT_LGAMMA + SLOT_IX_LOG + 3
 
 
-def region_slots(region, v, x):
-    """FP64 slots of the per-thread expressions (tiles kernel) for pairs of one region."""
+def mu_slots_scalar(v, x, K=20):
+    # one order for all pairs: per term one fma; plus 1/(8x), S^2 and two products, log, fma
+    return mu_terms(v, x, K) * 1 + SLOT_DIV + 3 + SLOT_IX_LOG + 1
+
+
+def u_slots_scalar(K):
+    # x/v, fma, rsqrt, r2 t, Horner of degree 3K in t, eta (add, two logs, subtract, add),
+    # tail (3 multiplies, log, 2 multiplies, fma)
+    return 1 + 1 + SLOT_RSQRT + 1 + 3 * K + 1 + 2 * SLOT_IX_LOG + 1 + 1 + 3 + SLOT_IX_LOG + 3
+
+
+def series_slots_scalar(v, x):
+    # per term: y r_k, fma; plus y, log P, log(x/2), fma
+    n = series_terms(v, x)
+    return n * 2 + 2 + SLOT_IX_LOG + SLOT_IX_LOG + 3
+
+
+def region_slots(region, v, x, scalar=False):
+    """FP64 slots of the per-thread expressions (tiles kernel) for pairs of one
+    region; scalar=True for a call with one order for all pairs (the order's
+    constants are computed once per block, see ScalarOrder)."""
     if region == 0:
-        return mu_slots(v, x)
+        return mu_slots_scalar(v, x) if scalar else mu_slots(v, x)
     if region in REGION_K and region != 4:
-        return np.full(np.shape(x), u_slots(REGION_K[region]), dtype=np.float64)
+        k = REGION_K[region]
+        return np.full(np.shape(x), u_slots_scalar(k) if scalar else u_slots(k), dtype=np.float64)
     if region == 4:
         return mu_slots(v, x, K=3)
-    return series_slots(v, x)
+    return series_slots_scalar(v, x) if scalar else series_slots(v, x)
