@@ -361,7 +361,7 @@ def main():
     rk_per = lb.classify("k", per_order_t, x_all).cpu().numpy()
     del per_order_t
     kint_slots = (WM.kint_slots(vm_h[fb_mix], x_h[fb_mix]).sum()
-                  + WM.kint_slots(per_order_k[fb_per], x_h[fb_per]).sum())
+                  + WM.kint_slots(per_order_k[fb_per], x_h[fb_per], scalar=True).sum())
     rng_w = np.random.default_rng(0)
 
     def sampled_sum(fn, sel_idx, vv):

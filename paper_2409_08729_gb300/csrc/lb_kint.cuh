@@ -65,6 +65,26 @@ __device__ __forceinline__ int kint_rule(double v, double x) {
   return ng | (hr << 8);
 }
 
+// One order for every pair of a call (v_stride 0): the g-node positions
+// u_j^beta of the three u rules and the order's part of the prefactor are
+// the same for every pair, so a block computes them once (with the same
+// operations as the per-pair path: the results do not change).
+struct KintScalar {
+  double ub24[24], ub32[32], ub64[64];
+  double pre;                                      // log(sqrt(pi)) - lgamma(v + 1/2)
+};
+
+// All threads of the block call it; ends with a barrier.
+__device__ __forceinline__ void kint_scalar_setup(KintScalar& ks, double v) {
+  const int tid = threadIdx.x;
+  const double beta = 16.0 / (2.0 * v + 1.0);
+  if (tid < 24) ks.ub24[tid] = ix_exp(beta * __ldg(lb_kq_g24_logu + tid));
+  else if (tid < 56) ks.ub32[tid - 24] = ix_exp(beta * __ldg(lb_kq_g32_logu + tid - 24));
+  else if (tid < 120) ks.ub64[tid - 56] = ix_exp(beta * __ldg(lb_kq_g64_logu + tid - 56));
+  else if (tid == 120) ks.pre = kHalfLogPi - lgamma(v + 0.5);
+  __syncthreads();
+}
+
 // One pair, fixed Gauss rules (g: 32 or 64 nodes in u; h: rule hr), all
 // lanes of the warp: returns on every lane its part of the shifted sums
 // s0 = sum_j e^{L_j - mm} and s1 = sum_j e^{L_j - mm} / (s_j + 2x) (DX), with
@@ -74,7 +94,8 @@ __device__ __forceinline__ int kint_rule(double v, double x) {
 // every node (any shift is exact, and beta <= 16 cannot overflow them).
 template <bool DX>
 __device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta, int ng, int hr,
-                                                int lane, double& mm, double& s0, double& s1) {
+                                                int lane, double& mm, double& s0, double& s1,
+                                                const KintScalar* ks) {
   const double vm = v - 0.5, tx = 2.0 * x;
   const double* gu = ng == 32 ? lb_kq_g32_logu : lb_kq_g64_logu;
   const double* gc = ng == 32 ? lb_kq_g32_c : lb_kq_g64_c;
@@ -90,7 +111,7 @@ __device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta,
     A[k] = 0.0;
     if (32 * k < ng) {                             // g node: log w + 7 log u - u^beta + (v-1/2) log(2x + u^beta)
       const int j = lane + 32 * k;
-      const double ub = ix_exp(beta * __ldg(gu + j));
+      const double ub = ks ? (ng == 32 ? ks->ub32[j] : ks->ub64[j]) : ix_exp(beta * __ldg(gu + j));
       L[k] = fma(vm, ix_log(tx + ub), __ldg(gc + j)) - ub;
       if (DX) A[k] = 1.0 / (tx + ub);
       key = max(key, order_key(L[k]));
@@ -135,12 +156,12 @@ __device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta,
 // exp of s runs on the g lanes only.  Sums as in kint_sums_fixed.
 template <bool DX>
 __device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta, int lane,
-                                                 double& mm, double& s0, double& s1) {
+                                                 double& mm, double& s0, double& s1, const KintScalar* ks) {
   const double vm = v - 0.5, tx = 2.0 * x;
   const bool isg = lane < 24;
   const int jh = isg ? 0 : lane - 24;
   double s;
-  if (isg) s = ix_exp(beta * __ldg(lb_kq_g24_logu + lane));
+  if (isg) s = ks ? ks->ub24[lane] : ix_exp(beta * __ldg(lb_kq_g24_logu + lane));
   else s = __ldg(lb_kq_hl40_s + jh);
   const double y0 = isg ? 0.0 : __ldg(lb_kq_hl40_y + jh);
   const double c0 = isg ? __ldg(lb_kq_g24_c + lane) : __ldg(lb_kq_hl40_c + jh);
@@ -182,7 +203,7 @@ __device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta
 // is the 32-node rule in log s).
 template <bool DX>
 __device__ __forceinline__ void kint_sums_split(double v, double x, double beta, int lane,
-                                                double& mm, double& s0, double& s1) {
+                                                double& mm, double& s0, double& s1, const KintScalar* ks) {
   const double vm = v - 0.5, vp = v + 0.5, tx = 2.0 * x;
   const double sx = 128.0 * x;                     // s1 (exact)
   const double y1 = ix_log(sx);
@@ -193,7 +214,7 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
 #pragma unroll
   for (int k = 0; k < 2; ++k) {                    // [0, s1]: s = s1 r, r = u^beta
     const int j = lane + 32 * k;
-    const double r = ix_exp(beta * __ldg(lb_kq_g64_logu + j));
+    const double r = ks ? ks->ub64[j] : ix_exp(beta * __ldg(lb_kq_g64_logu + j));
     const double sj = sx * r;
     L[k] = fma(vm, ix_log(r + 0.015625), __ldg(lb_kq_g64_c + j)) - sj;     // less log beta, as above
     A[k] = DX ? 1.0 / (sj + tx) : 0.0;
@@ -300,7 +321,8 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
 // -v/x - 1 plus (2v - 1) <1/(s + 2x)>, the F-weighted mean over the nodes,
 // since dF/dx = F (2v - 1)/(s + 2x)).
 template <bool DX>
-__device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane) {
+__device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane,
+                                                   const KintScalar* ks = nullptr) {
   const double beta_i = 16.0 / (2.0 * vi + 1.0);
   const int rule_i = kint_rule(vi, xi);
   double m_i = 0.0, s0_i = 1.0, s1_i = 0.0;
@@ -311,9 +333,9 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     const int rule = __shfl_sync(0xffffffffu, rule_i, e);
     const int ng = rule & 0xff, hr = rule >> 8;
     double mm, s0, s1;
-    if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1);
-    else if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1);
-    else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1);
+    if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
+    else if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1, ks);
+    else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1, ks);
     s0 = warp_sum(s0);
     if (DX) s1 = warp_sum(s1);
     if (lane == e) {
@@ -323,7 +345,8 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     }
   }
   if (DX) return -(vi / xi + 1.0) + (2.0 * vi - 1.0) * (s1_i / s0_i);
-  return kint_prefactor(vi, xi) + m_i + ix_log(s0_i);
+  const double pre = ks ? ks->pre - fma(vi, ix_log(2.0 * xi), xi) : kint_prefactor(vi, xi);
+  return pre + m_i + ix_log(s0_i);
 }
 
 // Warp-cooperative log int_0^1 (g + h) du by the paper's Simpson rule (N = 600).

@@ -212,9 +212,10 @@ __device__ __forceinline__ void tile_eval(TileShared<T>& S, T* __restrict__ out,
 // each lane computes its pair's prefactor, then the warp evaluates the
 // integrals one pair at a time with the nodes spread over the lanes.
 template <bool DX, typename T>
-__device__ __forceinline__ T kint_warp_batch(T vi, T xi, int m, int lane, bool gauss) {
+__device__ __forceinline__ T kint_warp_batch(T vi, T xi, int m, int lane, bool gauss,
+                                            const KintScalar* ks = nullptr) {
   if constexpr (sizeof(T) == 8) {
-    if (gauss) return kint_batch_gauss<DX>(vi, xi, m, lane);
+    if (gauss) return kint_batch_gauss<DX>(vi, xi, m, lane, ks);
   }
   T pre;
   if constexpr (sizeof(T) == 8) pre = DX ? -(vi / xi + 1.0) : kint_prefactor(vi, xi);

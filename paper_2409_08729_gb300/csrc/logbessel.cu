@@ -87,6 +87,15 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
                const unsigned int* __restrict__ qcount, const uint32_t* __restrict__ queue) {
   const unsigned int cnt = *qcount;
   const int lane = threadIdx.x & 31;
+  const KintScalar* ks = nullptr;
+  if constexpr (GAUSS && sizeof(T) == 8) {
+    // one order for every pair: its node positions once per block
+    __shared__ KintScalar KS;
+    if (v_stride == 0 && cnt > 0) {
+      kint_scalar_setup(KS, fabs((double)v[0]));
+      ks = &KS;
+    }
+  }
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = warp * 32; b < (int64_t)cnt; b += nwarps * 32) {
@@ -96,7 +105,7 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
     const T vi = fabs(v[idx * v_stride]);
     const T xi = x[idx];
     const int m = (int)min((int64_t)32, (int64_t)cnt - b);
-    const T val = kint_warp_batch<DX, T>(vi, xi, m, lane, GAUSS);
+    const T val = kint_warp_batch<DX, T>(vi, xi, m, lane, GAUSS, ks);
     if (valid) out[idx] = val;
   }
 }

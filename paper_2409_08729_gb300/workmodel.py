@@ -74,19 +74,21 @@ def kint_rule(v, x):
     return np.where(packed, 24, ng), np.where(packed, 40, nh)
 
 
-def kint_slots(v, x):
+def kint_slots(v, x, scalar=False):
     """Work of one K-integral evaluation per pair (tight Gauss rule), in DFMA
-    slots; the node exps and logs are the integer-pipe ones."""
+    slots; the node exps and logs are the integer-pipe ones.  scalar=True for
+    a call with one order for all pairs (node positions u^beta and lgamma
+    computed once per block)."""
     ng, nh = kint_rule(v, x)
     split = ng > 64
     # g node: beta*log u, exp, 2x + u^beta, log, fma, - u^beta; then L - m, exp, accumulate
     # (split rule: 3 more for the offset form: s1 * r, the shift by C, the key add)
-    g_node = 6 + 2 * SLOT_IX_EXP + SLOT_IX_LOG + np.where(split, 3, 0)
+    g_node = (5 if scalar else 6 + SLOT_IX_EXP) + SLOT_IX_EXP + SLOT_IX_LOG + np.where(split, 3, 0)
     # h node: s + 2x, log, + y, fma; then L - m, exp, accumulate
     h_node = 5 + SLOT_IX_EXP + SLOT_IX_LOG
     # per pair (once per lane of its batch): beta (div), prefactor (lgamma,
     # log, 3 ops), final log and beta g + h; the warp sum (5 adds, all lanes)
-    per_pair = SLOT_DIV + SLOT_LGAMMA + SLOT_IX_LOG + 3 + SLOT_IX_LOG + 2 + 1 + 5
+    per_pair = SLOT_DIV + (0 if scalar else SLOT_LGAMMA) + SLOT_IX_LOG + 3 + SLOT_IX_LOG + 2 + 1 + 5
     # split rule: log s1, C, three panel widths (log + add each), the flat term (log, expm1, division)
     per_pair = per_pair + np.where(split, 2 + 4 * SLOT_LOG + 3 + SLOT_EXP + SLOT_DIV + 4, 0)
     return ng * g_node + nh * h_node + per_pair
