@@ -78,17 +78,25 @@ __device__ __forceinline__ float mu_expr32(float v, float x) {
 
 template <int KIND, int K>
 __device__ __forceinline__ float u_expr32(float v, float x) {
-  const float xp = x / v;
-  const float r = (xp < 1e18f) ? sqrtf(fmaf(xp, xp, 1.0f)) : xp;
-  const float t = 1.0f / r;
+  const float inv_v = 1.0f / v;
+  const float xp = x * inv_v;
+  float r, t;
+  if (xp < 1e18f) {
+    const float r2 = fmaf(xp, xp, 1.0f);
+    t = rsqrtf(r2);                                  // single-precision estimate (2 ulp)
+    r = r2 * t;
+  } else {
+    r = xp;
+    t = 1.0f / xp;
+  }
   const float p = t * t;
-  float q = t / v;
+  float q = t * inv_v;
   if (KIND == KIND_K) q = -q;
   float acc = debye_P<float>(K, p);
 #pragma unroll
   for (int k = K - 1; k >= 1; --k) acc = fmaf(acc, q, debye_P<float>(k, p));
   const float S = fabsf(fmaf(acc, q, 1.0f));
-  const float eta = r + logf(xp / (1.0f + r));
+  const float eta = r + logf(__fdividef(xp, 1.0f + r));
   if (KIND == KIND_I) return fmaf(v, eta, logf(S * rsqrtf((float)kTwoPi * v * r)));
   return fmaf(-v, eta, logf(S * sqrtf((float)kPi / (2.0f * v * r))));
 }
@@ -100,7 +108,7 @@ __device__ __forceinline__ float series_log_i32(float v, float x) {
   float term = 1.0f, T = 0.0f;
   float k = 1.0f;
   for (int it = 0; it < 400; ++it) {
-    term *= y / (k * (k + v));
+    term *= __fdividef(y, k * (k + v));             // 2 ulp per ratio: within the path's budget
     T += term;
     if (k > kpk && term <= 1.5e-8f * (1.0f + T)) break;
     k += 1.0f;
@@ -115,24 +123,50 @@ __device__ __forceinline__ float series_log_i32(float v, float x) {
 // x < 1e-3 (see kint_sums_split: the nodes anchored at s1 = 128 x carry their
 // terms less C = 2 v log s1 and are shifted by m - C).  Warp-cooperative; all
 // lanes pass the same pair.
-__device__ __forceinline__ float kint_gauss32(float v, float x, int lane) {
+// One order for every pair of a call: u_j^beta of the three u rules once per
+// block (as KintScalar; same operations, same results).
+struct KintScalar32 {
+  float ub24[24], ub32[32], ub64[64];
+};
+
+__device__ __forceinline__ void kint_scalar_setup32(KintScalar32& ks, float v) {
+  const int tid = threadIdx.x;
   const float beta = 16.0f / (2.0f * v + 1.0f);
-  const float logbeta = logf(beta);
+  if (tid < 24) ks.ub24[tid] = expf(beta * __ldg(lb_kqf_g24_logu + tid));
+  else if (tid < 56) ks.ub32[tid - 24] = expf(beta * __ldg(lb_kqf_g32_logu + tid - 24));
+  else if (tid < 120) ks.ub64[tid - 56] = expf(beta * __ldg(lb_kqf_g64_logu + tid - 56));
+  __syncthreads();
+}
+
+// The summand exps (arguments <= 0, the largest terms near 0) use the fast
+// single-precision exp: about 2e-7 relative error near 0, growing like
+// 6e-8 |argument| on terms that weigh e^-|argument|, so the sum moves by
+// about 2e-7 relative, well inside the FP32 path's 2e-6.
+// Warp maximum of a float through an order-preserving integer key (one
+// integer reduction instead of five shuffle rounds).
+__device__ __forceinline__ float warp_max32(float a) {
+  const int k = __float_as_int(a);
+  const int key = __reduce_max_sync(0xffffffffu, k >= 0 ? k : (k ^ 0x7fffffff));
+  return __int_as_float(key >= 0 ? key : (key ^ 0x7fffffff));
+}
+
+// beta = 16/(2v + 1) and log beta are per pair: the caller computes them
+// once per lane and passes the shuffled values.
+__device__ __forceinline__ float kint_gauss32(float v, float x, float beta, float logbeta, int lane,
+                                              const KintScalar32* ks = nullptr) {
   const float vm = v - 0.5f, vp = v + 0.5f, tx = 2.0f * x;
   if (v > 1.2f && v <= 5.0f) {
     // 24 g + 40 h nodes in two lane slots (as kint_sums_g24h40)
     const bool isg = lane < 24;
     const int jh = isg ? 0 : lane - 24;
-    const float s = isg ? expf(beta * __ldg(lb_kqf_g24_logu + lane)) : __ldg(lb_kqf_hl40_s + jh);
+    const float s = isg ? (ks ? ks->ub24[lane] : expf(beta * __ldg(lb_kqf_g24_logu + lane))) : __ldg(lb_kqf_hl40_s + jh);
     const float y0 = isg ? 0.0f : __ldg(lb_kqf_hl40_y + jh);
     const float c0 = isg ? __ldg(lb_kqf_g24_c + lane) + logbeta : __ldg(lb_kqf_hl40_c + jh);
     const float L0 = fmaf(vm, logf(tx + s) + y0, c0) - (isg ? s : 0.0f);
     const float sh = __ldg(lb_kqf_hl40_s + 8 + lane);
     const float L1 = fmaf(vm, __ldg(lb_kqf_hl40_y + 8 + lane) + logf(sh + tx), __ldg(lb_kqf_hl40_c + 8 + lane));
-    float m = fmaxf(L0, L1);
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    float sum = expf(L0 - m) + expf(L1 - m);
+    const float m = warp_max32(fmaxf(L0, L1));
+    float sum = __expf(L0 - m) + __expf(L1 - m);
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     return m + logf(sum);
@@ -158,13 +192,13 @@ __device__ __forceinline__ float kint_gauss32(float v, float x, int lane) {
         const int j = lane + 32 * k;
         const float logu = ng == 32 ? __ldg(lb_kqf_g32_logu + j) : __ldg(lb_kqf_g64_logu + j);
         const float c = ng == 32 ? __ldg(lb_kqf_g32_c + j) : __ldg(lb_kqf_g64_c + j);
-        const float ub = expf(beta * logu);
+        const float ub = ks ? (ng == 32 ? ks->ub32[j] : ks->ub64[j]) : expf(beta * logu);
         L[k] = c + logbeta - ub + vm * logf(tx + ub);
         live[k] = true;
       }
     } else if (k < 2) {                               // [0, s1]: s = s1 r, r = u^beta
       const int j = lane + 32 * k;
-      const float r = expf(beta * __ldg(lb_kqf_g64_logu + j));
+      const float r = ks ? ks->ub64[j] : expf(beta * __ldg(lb_kqf_g64_logu + j));
       L[k] = fmaf(vm, logf(r + 0.015625f), __ldg(lb_kqf_g64_c + j) + logbeta) - sx * r;
       live[k] = true;
       rel[k] = true;
@@ -219,13 +253,12 @@ __device__ __forceinline__ float kint_gauss32(float v, float x, int lane) {
   float m = Lflat + C;
 #pragma unroll
   for (int i = 0; i < 7; ++i) m = fmaxf(m, rel[i] ? L[i] + C : L[i]);
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  m = warp_max32(m);
   const float mr = m - C;
-  float s = (lane == 0 && Lflat > -INFINITY) ? expf(Lflat - mr) : 0.0f;
+  float s = (lane == 0 && Lflat > -INFINITY) ? __expf(Lflat - mr) : 0.0f;
 #pragma unroll
   for (int k = 0; k < 7; ++k)
-    if (live[k]) s += expf(L[k] - (rel[k] ? mr : m));
+    if (live[k]) s += __expf(L[k] - (rel[k] ? mr : m));
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return m + logf(s);

@@ -213,20 +213,30 @@ __device__ __forceinline__ void tile_eval(TileShared<T>& S, T* __restrict__ out,
 // integrals one pair at a time with the nodes spread over the lanes.
 template <bool DX, typename T>
 __device__ __forceinline__ T kint_warp_batch(T vi, T xi, int m, int lane, bool gauss,
-                                            const KintScalar* ks = nullptr) {
+                                            const KintScalar* ks = nullptr, const KintScalar32* ks32 = nullptr) {
   if constexpr (sizeof(T) == 8) {
     if (gauss) return kint_batch_gauss<DX>(vi, xi, m, lane, ks);
   }
   T pre;
   if constexpr (sizeof(T) == 8) pre = DX ? -(vi / xi + 1.0) : kint_prefactor(vi, xi);
   else pre = kint_prefactor32(vi, xi);
+  float beta_i = 0.0f, logbeta_i = 0.0f;
+  if constexpr (sizeof(T) == 4) {
+    beta_i = 16.0f / (2.0f * vi + 1.0f);
+    logbeta_i = logf(beta_i);
+  }
   T mine = 0;
   for (int e = 0; e < m; ++e) {
     const T ve = __shfl_sync(0xffffffffu, vi, e);
     const T xe = __shfl_sync(0xffffffffu, xi, e);
     T li;
-    if constexpr (sizeof(T) == 8) li = kint_log_simpson(ve, xe, lane);
-    else li = kint_gauss32(ve, xe, lane);
+    if constexpr (sizeof(T) == 8) {
+      li = kint_log_simpson(ve, xe, lane);
+    } else {
+      const float be = __shfl_sync(0xffffffffu, beta_i, e);
+      const float lbe = __shfl_sync(0xffffffffu, logbeta_i, e);
+      li = kint_gauss32(ve, xe, be, lbe, lane, ks32);
+    }
     if (lane == e) mine = li;
   }
   return pre + mine;

@@ -88,12 +88,19 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
   const unsigned int cnt = *qcount;
   const int lane = threadIdx.x & 31;
   const KintScalar* ks = nullptr;
+  const KintScalar32* ks32 = nullptr;
   if constexpr (GAUSS && sizeof(T) == 8) {
     // one order for every pair: its node positions once per block
     __shared__ KintScalar KS;
     if (v_stride == 0 && cnt > 0) {
       kint_scalar_setup(KS, fabs((double)v[0]));
       ks = &KS;
+    }
+  } else if constexpr (GAUSS && sizeof(T) == 4) {
+    __shared__ KintScalar32 KS32;
+    if (v_stride == 0 && cnt > 0) {
+      kint_scalar_setup32(KS32, fabsf((float)v[0]));
+      ks32 = &KS32;
     }
   }
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -105,7 +112,7 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
     const T vi = fabs(v[idx * v_stride]);
     const T xi = x[idx];
     const int m = (int)min((int64_t)32, (int64_t)cnt - b);
-    const T val = kint_warp_batch<DX, T>(vi, xi, m, lane, GAUSS, ks);
+    const T val = kint_warp_batch<DX, T>(vi, xi, m, lane, GAUSS, ks, ks32);
     if (valid) out[idx] = val;
   }
 }
