@@ -61,9 +61,10 @@ __device__ __forceinline__ double fm_exp_le(double y) {
 }
 
 // fm_exp_le without the low table part: within about 1 ulp instead of 0.5,
-// one FP64 operation less.  For the terms of a quadrature sum and for node
-// positions, where a 1-ulp error per term is far below the sum's own
-// rounding.
+// one FP64 operation less (for sums of many terms, where a 1-ulp error per
+// term is far below the sum's own rounding).  The kernels now take their
+// node exps from the integer pipes (lb_intmath.cuh); this one stays
+// available and measured for comparison.
 __device__ __forceinline__ double fm_exp_term(double y) {
   const bool under = (unsigned int)__double2hiint(y) > 0xC0862000u;
   if (under) y = -708.0;

@@ -6,8 +6,9 @@
 //   tile_bin   loads the tile (coalesced), writes domain-edge results,
 //              classifies the rest (Table "input ranges") and appends each
 //              pair's index to a shared-memory list per region;
-//   tile_eval  evaluates the per-thread expressions list by list, so every
-//              warp runs a single expression at a time;
+//   tile_eval  evaluates the per-thread expressions: warps take 32-pair
+//              chunks of the lists from shared counters, region by region,
+//              so every warp runs a single expression at a time;
 //   tile_kint  evaluates the K integral of the tile's fallback pairs, one
 //              warp per pair, 32 pairs per warp batch.
 // The per-call kernels (logbessel.cu) and the persistent serving kernel

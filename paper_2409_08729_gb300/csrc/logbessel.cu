@@ -6,14 +6,17 @@
 //   1. lb_tiles_kernel: persistent CTAs walk tiles of LB_TILE pairs.  Each
 //      thread loads LB_ITEMS pairs (coalesced), handles domain edges, and
 //      classifies the rest (Table "input ranges").  The tile's pairs are
-//      binned per region into shared-memory index lists, and the block then
-//      works through each list with all its threads, so every warp runs one
-//      expression (mu_20, U_13, power series) at a time.  K pairs of the
+//      binned per region into shared-memory index lists; the warps take
+//      32-pair chunks of the lists from shared counters, so every warp runs
+//      one expression (mu_20, U_K, power series) at a time.  K pairs of the
 //      fallback region are appended to a global queue instead.
 //   2. lb_kint_kernel: one warp per queued K pair evaluates the integral with
 //      the nodes spread over the lanes (lb_kint.cuh).
+// A call with one order for all pairs (v_stride 0) has its order's
+// constants computed once per block (ScalarOrder, KintScalar).
 //
-// All arithmetic of the plain form is FP64.
+// The plain form computes in FP64; its exps and logs are evaluated in
+// integer arithmetic where that is faster (lb_intmath.cuh).
 #include <cuda_runtime.h>
 
 #include <atomic>
