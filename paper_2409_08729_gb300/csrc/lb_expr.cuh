@@ -284,6 +284,14 @@ __device__ __forceinline__ double u_expr(double v, double x) {
 // division; B stays below 1e250 for n <= 80 and v <= 16.  All 32 lanes of the
 // warp must call it together.
 // ---------------------------------------------------------------------------
+// 0, 1, ..., 90 as doubles: the series loop reads k from here instead of
+// stepping a double counter (one FP64 operation per term less).
+static __constant__ double kSeriesK[91] = {
+    0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22,
+    23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45,
+    46, 47, 48, 49, 50, 51, 52, 53, 54, 55, 56, 57, 58, 59, 60, 61, 62, 63, 64, 65, 66, 67, 68,
+    69, 70, 71, 72, 73, 74, 75, 76, 77, 78, 79, 80, 81, 82, 83, 84, 85, 86, 87, 88, 89, 90};
+
 __device__ __forceinline__ double series_log_i(double v, double x) {
   int n = 1;
   {
@@ -302,13 +310,12 @@ __device__ __forceinline__ double series_log_i(double v, double x) {
   n = __reduce_max_sync(0xffffffffu, n);
   const double y = 0.25 * x * x;
   double A = 1.0, B = 1.0;
-  double kd = (double)n;            // one conversion; the loop steps it by -1
 #pragma unroll 1
   for (int k = n; k >= 1; --k) {
+    const double kd = kSeriesK[k];  // k as a double from constant memory (k is warp-uniform)
     const double d = kd * (kd + v);
     A = fma(d, B, y * A);
     B *= d;
-    kd -= 1.0;
   }
   double res = ix_log_call(A / B) - lgamma(v + 1.0);
   if (v != 0.0) res = fma(v, ix_log_call(0.5 * x), res);

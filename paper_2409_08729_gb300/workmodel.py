@@ -146,9 +146,9 @@ def series_terms(v, x):
 
 
 def series_slots(v, x):
-    # per term: k + v, d = k (k + v), y A, fma, B d, k - 1; plus A/B, log, lgamma, log(x/2), fma
+    # per term: k + v, d = k (k + v), y A, fma, B d; plus A/B, log, lgamma, log(x/2), fma
     n = series_terms(v, x)
-    return n * 6 + SLOT_DIV + SLOT_IX_LOG + SLOT_LGAMMA + SLOT_IX_LOG + 3
+    return n * 5 + SLOT_DIV + SLOT_IX_LOG + SLOT_LGAMMA + SLOT_IX_LOG + 3
 
 
 def mu_slots_scalar(v, x, K=20):
