@@ -384,13 +384,20 @@ def main():
     # DRAM traffic of the K-integral kernel: 37 B per queued pair (one ncu
     # capture, profiles/lb_kint_kernel_sweep_small.md), scaled to the pairs of
     # an average launch; it grows in proportion (per-pair gathers only).
-    kint_pairs_per_launch = (fb_mix.sum() + fb_per.sum()) * args.steps / max(prof["lb_kint_kernel"][0], 1)
-    traffic = {"lb_kint_kernel": 37.0 * kint_pairs_per_launch}
+    kint_pairs_per_launch = (fb_mix.sum() + fb_per.sum()) * args.steps / max(prof["lb_kint_kernel"][1], 1)
+    # DRAM traffic of the tiles kernel, from one ncu capture at 1M arguments
+    # per order (profiles/lb_tiles_kernel_sweep_small.md): 9.1 B per pair for
+    # a one-order call (x read; the results were still in L2 when it ended)
+    # and 16.3 B read + 5.2 B written per pair for a mixed-order call. Reads
+    # grow in proportion; the writes are a lower bound at full size.
+    tiles_bytes = 2 * args.steps * n_all * (9.1 + 16.3 + 5.2)
+    traffic = {"lb_kint_kernel": 37.0 * kint_pairs_per_launch,
+               "lb_tiles_kernel": tiles_bytes / max(prof["lb_tiles_kernel"][1], 1)}
     if name in work_slots:
         work = 2.0 * work_slots[name] * args.steps
         roof = {"bound": "alu", "kernel": name, "achieved": work / (kms / 1e3) / 1e9,
                 "peak": peak_flops / 1e9, "unit": "GFLOP/s", "frac": (work / (kms / 1e3)) / peak_flops,
-                "traffic": traffic.get(name), "launches": nl, "avg_launch_ms": kms / max(ntimed, 1),
+                "traffic": traffic.get(name), "launches": ntimed, "avg_launch_ms": kms / max(ntimed, 1),
                 "peak_source": "FP64 DFMA rate measured live by logbessel_measure_fp64 (x2 flops/FMA)"}
     other = {k: {"achieved_gflops": 2.0 * w * args.steps / (prof[k][2] / 1e3) / 1e9 if prof.get(k, (0, 0, 0))[2] else None}
              for k, w in work_slots.items()}
@@ -405,7 +412,7 @@ def main():
                        "mode": args.mode, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (>=160 MB per call), no flush"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clocks,
-            "kernels": {k: {"launches": v[0], "ms": v[2], **other.get(k, {})} for k, v in prof.items()},
+            "kernels": {k: {"launches": v[1], "ms": v[2], **other.get(k, {})} for k, v in prof.items()},
             "region_mix_mixed_call": mix,
             "fp64_rates": {k: v / 1e9 for k, v in rates.items()}, "slot_costs": slot_costs}
     line["max_rel_err"] = acc

@@ -178,13 +178,25 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
  * (0 = 8M pairs; at most 2^26) through three device buffers on three
  * internal streams, so the copy-in of one chunk, the evaluation of the
  * previous one and the copy-out of the one before overlap.  The call
- * returns when every result is in `out` (it synchronizes).  Device buffers
- * come from the stream-ordered allocator and are released before return.
+ * returns when every result is in `out` (it synchronizes).  The streams,
+ * events and one device buffer (three chunk slots of v, x and out, plus the
+ * K fallback queue: about 24 * chunk + 4 * chunk bytes in FP64) belong to the
+ * current device and are kept from one call to the next, grown when a call
+ * needs more; calls on the same device run one at a time (a lock).
  * Errors as for the device entry points; LB_ENOTSUP for derivatives in FP32
- * or the K derivative outside LB_TIGHT.
+ * or the K derivative outside LB_TIGHT; LB_ENOMEM when the buffer cannot be
+ * allocated.
  */
 lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
                          int64_t n, lb_mode mode, int64_t chunk);
+
+/*
+ * Release the streams, events and device buffer that logbessel_host keeps
+ * for the current device (after waiting for its streams).  The next
+ * logbessel_host call on that device creates them again.  Returns LB_OK, or
+ * LB_ECUDA when the current device cannot be read.
+ */
+lb_status logbessel_host_release(void);
 
 /*
  * Region id of every pair under the dispatch of `mode` (Table "input

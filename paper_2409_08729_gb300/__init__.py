@@ -165,6 +165,12 @@ def host_eval(fn, v, x, out=None, mode="tight", chunk=0):
     return out
 
 
+def host_release():
+    """Free the device buffer, streams and events that host_eval keeps for
+    the current device between calls."""
+    _binding.check(_binding.lib().logbessel_host_release())
+
+
 def classify(kind, v, x, mode="tight"):
     """Region id (uint8, see REGIONS) of every pair; kind is 'i' or 'k'."""
     vf, vs, xf, shape = _prep(v, x)

@@ -41,6 +41,8 @@ def lib():
             f.restype = i32
         L.logbessel_host.argtypes = [i32, i32, vp, i64, vp, vp, i64, i32, i64]
         L.logbessel_host.restype = i32
+        L.logbessel_host_release.argtypes = []
+        L.logbessel_host_release.restype = i32
         L.logbessel_vmf_log_c.argtypes = [i32, ctypes.c_double, vp, vp, i64, i32, vp]
         L.logbessel_vmf_log_c.restype = i32
         L.logbessel_classify.argtypes = [i32, i32, vp, i64, vp, vp, i64, i32, vp]

@@ -579,6 +579,57 @@ lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t 
   return launch(PS_AUX, st, [&] { lb_math_kernel<<<grid, LB_THREADS, 0, st>>>(which, in, out, n); });
 }
 
+// Streams, events and the device buffer of logbessel_host, kept per device
+// from one call to the next: allocating and releasing the few hundred MB of
+// chunk buffers on every call (the stream-ordered pool returns them to the
+// driver at each synchronization) costs more than a short call's evaluation.
+// A call holds its device's lock from start to end.
+struct HostPipe {
+  std::mutex mu;
+  bool init = false;
+  cudaStream_t st[3] = {};
+  cudaEvent_t ev_in[3] = {}, ev_comp[3] = {}, ev_out[3] = {};
+  char* dbuf = nullptr;
+  size_t bytes = 0;
+};
+constexpr int kMaxDevices = 64;
+
+HostPipe& host_pipe(int dev) {
+  static HostPipe pipes[kMaxDevices];
+  return pipes[dev];
+}
+
+void host_pipe_destroy(HostPipe& P) {
+  if (P.dbuf) cudaFree(P.dbuf);
+  for (int i = 0; i < 3; ++i) {
+    if (P.ev_in[i]) cudaEventDestroy(P.ev_in[i]);
+    if (P.ev_comp[i]) cudaEventDestroy(P.ev_comp[i]);
+    if (P.ev_out[i]) cudaEventDestroy(P.ev_out[i]);
+    if (P.st[i]) cudaStreamDestroy(P.st[i]);
+    P.ev_in[i] = P.ev_comp[i] = P.ev_out[i] = nullptr;
+    P.st[i] = nullptr;
+  }
+  P.dbuf = nullptr;
+  P.bytes = 0;
+  P.init = false;
+}
+
+bool host_pipe_init(HostPipe& P) {
+  bool ok = true;
+  for (int i = 0; i < 3 && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&P.st[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&P.ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&P.ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&P.ev_out[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    host_pipe_destroy(P);
+    return false;
+  }
+  P.init = true;
+  return true;
+}
+
 lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out,
                          int64_t n, lb_mode mode, int64_t chunk) {
   if (fn < 0 || fn > 3) return fail(LB_EINVAL, "fn must be 0..3 (got %s%lld)", "", (long long)fn);
@@ -588,66 +639,81 @@ lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride
   if (chunk > kChunk) chunk = kChunk;
   if ((fn >= 2 && dtype != LB_F64) || (fn == 3 && mode != LB_TIGHT))
     return fail(LB_ENOTSUP, "%sthe derivatives are implemented for LB_F64 (and LB_TIGHT for K) only", "", 0);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch("cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(LB_EINVAL, "device %s%lld out of range", "", (long long)dev);
+  HostPipe& P = host_pipe(dev);
+  std::lock_guard<std::mutex> lk(P.mu);
+  if (!P.init && !host_pipe_init(P))
+    return fail(LB_ENOMEM, "%slogbessel_host: stream or event creation failed", "", 0);
   const size_t es = dtype == LB_F64 ? 8 : 4;
   const int64_t nbuf = 3;                         // copy-in, compute and copy-out of three chunks overlap
-  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t ev_in[3] = {}, ev_comp[3] = {}, ev_out[3] = {};
-  char* dbuf = nullptr;
   const int64_t cap = n < chunk ? n : chunk;
   const size_t vbytes = (size_t)(v_stride ? cap : 1) * es, xbytes = (size_t)cap * es;
   const size_t slot = ((vbytes + 255) & ~(size_t)255) + 2 * ((xbytes + 255) & ~(size_t)255);
-  bool ok = true;
-  for (int i = 0; i < 3 && ok; ++i) ok = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking) == cudaSuccess;
-  for (int i = 0; i < 3 && ok; ++i)
-    ok = cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&ev_out[i], cudaEventDisableTiming) == cudaSuccess;
-  if (ok) ok = cudaMallocAsync((void**)&dbuf, slot * nbuf, st[1]) == cudaSuccess &&
-               cudaStreamSynchronize(st[1]) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    s = fail(LB_ENOMEM, "%slogbessel_host: stream, event or buffer allocation failed", "", 0);
+  const size_t need = slot * nbuf + 256 + 4 * (size_t)cap;   // + the K fallback queue
+  if (P.bytes < need) {
+    if (P.dbuf) cudaFree(P.dbuf);
+    P.dbuf = nullptr;
+    P.bytes = 0;
+    if (cudaMalloc((void**)&P.dbuf, need) != cudaSuccess) {
+      cudaGetLastError();
+      P.dbuf = nullptr;
+      return fail(LB_ENOMEM, "%slogbessel_host: cudaMalloc of %lld bytes failed", "", (long long)need);
+    }
+    P.bytes = need;
   }
-  for (int64_t c0 = 0, i = 0; ok && s == LB_OK && c0 < n; c0 += chunk, ++i) {
+  cudaStream_t* st = P.st;
+  void* ws = P.dbuf + slot * nbuf;
+  for (int64_t c0 = 0, i = 0; s == LB_OK && c0 < n; c0 += chunk, ++i) {
     const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
     const int b = (int)(i % nbuf);
-    char* dv = dbuf + b * slot;
+    char* dv = P.dbuf + b * slot;
     char* dx = dv + ((vbytes + 255) & ~(size_t)255);
     char* dout = dx + ((xbytes + 255) & ~(size_t)255);
-    if (i >= nbuf) cudaStreamWaitEvent(st[0], ev_out[b], 0);          // slot b's results are out
+    if (i >= nbuf) cudaStreamWaitEvent(st[0], P.ev_out[b], 0);     // slot b's results are out
     const char* hv = (const char*)v + (v_stride ? c0 * (int64_t)es : 0);
     cudaMemcpyAsync(dv, hv, (size_t)(v_stride ? cn : 1) * es, cudaMemcpyHostToDevice, st[0]);
     cudaMemcpyAsync(dx, (const char*)x + c0 * (int64_t)es, (size_t)cn * es, cudaMemcpyHostToDevice, st[0]);
-    cudaEventRecord(ev_in[b], st[0]);
-    cudaStreamWaitEvent(st[1], ev_in[b], 0);
+    cudaEventRecord(P.ev_in[b], st[0]);
+    cudaStreamWaitEvent(st[1], P.ev_in[b], 0);
+    // one pass per chunk (cn <= cap <= kChunk), the K queue in ws
     if (dtype == LB_F32) {
-      s = run32(fn == 0 ? KIND_I : KIND_K, (const float*)dv, v_stride, (const float*)dx, (float*)dout, cn, (int)mode, -1, st[1]);
+      const float *fv = (const float*)dv, *fx = (const float*)dx;
+      float* fo = (float*)dout;
+      s = fn == 0 ? run_impl<KIND_I, false, float>(fv, v_stride, fx, fo, cn, (int)mode, -1, st[1], nullptr, kChunk)
+                  : run_impl<KIND_K, false, float>(fv, v_stride, fx, fo, cn, (int)mode, -1, st[1], ws, kChunk);
     } else {
+      const double *dvv = (const double*)dv, *dxx = (const double*)dx;
+      double* dd = (double*)dout;
       switch (fn) {
-        case 0: s = run<KIND_I, false>((const double*)dv, v_stride, (const double*)dx, (double*)dout, cn, (int)mode, -1, st[1]); break;
-        case 1: s = run<KIND_K, false>((const double*)dv, v_stride, (const double*)dx, (double*)dout, cn, (int)mode, -1, st[1]); break;
-        case 2: s = run<KIND_I, true>((const double*)dv, v_stride, (const double*)dx, (double*)dout, cn, (int)mode, -1, st[1]); break;
-        default: s = run<KIND_K, true>((const double*)dv, v_stride, (const double*)dx, (double*)dout, cn, (int)mode, -1, st[1]); break;
+        case 0: s = run_impl<KIND_I, false, double>(dvv, v_stride, dxx, dd, cn, (int)mode, -1, st[1], nullptr, kChunk); break;
+        case 1: s = run_impl<KIND_K, false, double>(dvv, v_stride, dxx, dd, cn, (int)mode, -1, st[1], ws, kChunk); break;
+        case 2: s = run_impl<KIND_I, true, double>(dvv, v_stride, dxx, dd, cn, (int)mode, -1, st[1], nullptr, kChunk); break;
+        default: s = run_impl<KIND_K, true, double>(dvv, v_stride, dxx, dd, cn, (int)mode, -1, st[1], ws, kChunk); break;
       }
     }
-    cudaEventRecord(ev_comp[b], st[1]);
-    cudaStreamWaitEvent(st[2], ev_comp[b], 0);
+    cudaEventRecord(P.ev_comp[b], st[1]);
+    cudaStreamWaitEvent(st[2], P.ev_comp[b], 0);
     cudaMemcpyAsync((char*)out + c0 * (int64_t)es, dout, (size_t)cn * es, cudaMemcpyDeviceToHost, st[2]);
-    cudaEventRecord(ev_out[b], st[2]);
+    cudaEventRecord(P.ev_out[b], st[2]);
   }
   for (int i = 0; i < 3; ++i)
-    if (st[i] && cudaStreamSynchronize(st[i]) != cudaSuccess && s == LB_OK) s = check_launch("logbessel_host");
-  if (dbuf) {
-    cudaFreeAsync(dbuf, st[1]);
-    cudaStreamSynchronize(st[1]);
-  }
-  for (int i = 0; i < 3; ++i) {
-    if (ev_in[i]) cudaEventDestroy(ev_in[i]);
-    if (ev_comp[i]) cudaEventDestroy(ev_comp[i]);
-    if (ev_out[i]) cudaEventDestroy(ev_out[i]);
-    if (st[i]) cudaStreamDestroy(st[i]);
-  }
+    if (cudaStreamSynchronize(st[i]) != cudaSuccess && s == LB_OK) s = check_launch("logbessel_host");
   return s;
+}
+
+lb_status logbessel_host_release(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch("cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(LB_EINVAL, "device %s%lld out of range", "", (long long)dev);
+  HostPipe& P = host_pipe(dev);
+  std::lock_guard<std::mutex> lk(P.mu);
+  if (P.init) {
+    for (int i = 0; i < 3; ++i) cudaStreamSynchronize(P.st[i]);
+    host_pipe_destroy(P);
+  }
+  return LB_OK;
 }
 
 const char* logbessel_last_error(void) { return g_last_error.c_str(); }

@@ -36,3 +36,24 @@ def test_host_fp32_and_scalar_order(cuda, fn):
     xp = torch.from_numpy(x).pin_memory()
     got2 = lb.host_eval(fn, torch.tensor([2.5], dtype=torch.float32), xp)
     assert _close(got2.numpy(), dev, 2e-6)
+
+
+def test_host_buffers_kept_and_released(cuda):
+    """The device buffer and streams outlive a call: a smaller call reuses
+    them, a larger chunk grows them, host_release frees them and the next
+    call makes them again; chunk edges on tile boundaries give the same bits."""
+    v, x = W.robust_pairs(200001, seed=21, vmax=1e3, xmin=1e-4, xmax=1e3)
+    a = lb.host_eval("log_k", v, x, chunk=65536)
+    b = lb.host_eval("log_k", v[:1000], x[:1000])
+    c = lb.host_eval("log_k", v, x, chunk=1 << 20)
+    lb.host_release()
+    d = lb.host_eval("log_k", v, x, chunk=65536)
+    lb.host_release()
+    lb.host_release()
+    e = lb.host_eval("log_i", 7.0, x, chunk=131072)
+    ref_b = lb.log_k(torch.tensor(v[:1000], device=cuda), torch.tensor(x[:1000], device=cuda)).cpu().numpy()
+    ref_e = lb.log_i(7.0, torch.tensor(x, device=cuda)).cpu().numpy()
+    assert np.array_equal(a, c, equal_nan=True)
+    assert np.array_equal(a, d, equal_nan=True)
+    assert np.array_equal(b, ref_b, equal_nan=True)
+    assert np.array_equal(e, ref_e, equal_nan=True)
