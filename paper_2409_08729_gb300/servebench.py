@@ -111,7 +111,10 @@ def _run(n_req, seed, max_n, loads, device, pool_n, out_slots):
             res["batched_by_load"].append({
                 "offered_load": load, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)), "gevals": total / (t_last - t_first) / 1e9,
-                "kernel_launches": srv.stats()["kernel_launches"] - st0})
+                # the persistent kernel started before this run stays resident
+                # while work keeps arriving; it is relaunched only after idling out
+                "persistent_kernel_relaunches": srv.stats()["kernel_launches"] - st0,
+                "persistent_kernel_launches_since_start": srv.stats()["kernel_launches"]})
 
     # one library call per request, same arrivals, one stream, FIFO
     L = B.lib()
