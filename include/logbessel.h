@@ -180,7 +180,7 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
  * previous one and the copy-out of the one before overlap.  The call
  * returns when every result is in `out` (it synchronizes).  The streams,
  * events and one device buffer (three chunk slots of v, x and out, plus the
- * K fallback queue: about 24 * chunk + 4 * chunk bytes in FP64) belong to the
+ * K fallback queue: about 3 * 24 * chunk + 4 * chunk bytes in FP64) belong to the
  * current device and are kept from one call to the next, grown when a call
  * needs more; calls on the same device run one at a time (a lock).
  * Errors as for the device entry points; LB_ENOTSUP for derivatives in FP32
