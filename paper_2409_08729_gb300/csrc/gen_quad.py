@@ -18,6 +18,11 @@ N = 600.  These tables hold Gauss rules for the same two pieces instead:
   h piece: Gauss-Legendre in y = log s on [0, log 100] (s in [1, 100]),
            32, 40 or 48 nodes, for orders v <= 5;
            Gauss-Laguerre in t = s - 1, 32 nodes, for orders v > 5.
+  one-slot rules (values, 2 <= v <= 16.5): the split moved from s = 1 to
+           s0, so that the branch point s = 0 of (s (s + 2x))^(v-1/2) lies
+           s0 away from the Gauss-Laguerre nodes of [s0, inf) (t = s - s0);
+           [0, s0] with s = s0 u^beta and Gauss-Legendre in u.  s0 = 8 with
+           22 + 10 nodes (2 <= v < 7), s0 = 3 with 12 + 20 (7 <= v <= 16.5).
 
 Writes kquad_tables.h beside this file.  Nodes and weights are computed in
 40-digit arithmetic and rounded to double.
@@ -76,7 +81,7 @@ def main():
     parts = ["// Generated by gen_quad.py -- do not edit.",
              "// Gauss rules for the g and h pieces of the K integral (see gen_quad.py).",
              "#pragma once", "", "#define LB_KQ_SMAX %d" % SMAX, ""]
-    for N in (24, 32, 64):
+    for N in (12, 22, 24, 32, 64):
         u, w = gauss_legendre01(N)
         parts.append("// g piece, Gauss-Legendre on [0,1], %d nodes: log u_j and log w_j" % N)
         parts.append(arr("lb_kq_g%d_logu" % N, [mp.log(a) for a in u]))
@@ -102,6 +107,17 @@ def main():
     parts.append(arr("lb_kq_hq32_s", [1 + a for a in t]))
     parts.append(arr("lb_kq_hq32_y", [mp.log(1 + a) for a in t]))
     parts.append(arr("lb_kq_hq32_c", [mp.log(a) - 1 for a in lam]))
+    for N, s0 in ((10, 8), (20, 3)):
+        t, lam = gauss_laguerre(N)
+        tag = "hq%do%d" % (N, s0)
+        parts.append("// one-slot rule: Gauss-Laguerre in t = s - %d, %d nodes: %d + t_j, log(%d + t_j), log(lambda_j) - %d"
+                     % (s0, N, s0, s0, s0))
+        parts.append(arr("lb_kq_%s_s" % tag, [s0 + a for a in t]))
+        parts.append(arr("lb_kq_%s_y" % tag, [mp.log(s0 + a) for a in t]))
+        parts.append(arr("lb_kq_%s_c" % tag, [mp.log(a) - s0 for a in lam]))
+    parts.append("// log 8 and log 3, the split points of the one-slot rules")
+    parts.append("#define LB_KQ_LOG8 %r" % float(mp.log(8)))
+    parts.append("#define LB_KQ_LOG3 %r" % float(mp.log(3)))
     with open(out, "w") as f:
         f.write("\n".join(parts) + "\n")
 

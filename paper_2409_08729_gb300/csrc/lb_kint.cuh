@@ -14,7 +14,9 @@
 // maximum as shift.
 //
 // Rules:
-//   LB_TIGHT: Gauss rules (tables in kquad_tables.h).  For 1.2 < v <= 5: 24
+//   LB_TIGHT: Gauss rules (tables in kquad_tables.h).  Values (not the
+//     x-derivative) for 2 <= v <= 16.5: one lane slot, the split moved from
+//     s = 1 to s0 (kint_sums_one).  Otherwise, for 1.2 < v <= 5: 24
 //     g nodes and 40 h nodes (two full lane slots).  Otherwise g: Gauss-Legendre in u
 //     with 32 nodes (v >= 0.9 or x >= 0.25), 64 (v >= 0.4 or x >= 1e-3), or
 //     for v < 0.4, x < 1e-3 a split rule (kint_sums_split), because
@@ -58,7 +60,11 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
 // g rule 24 goes with h rule 3 (40 nodes in log s): for 1.2 < v <= 5 the
 // 24 + 40 nodes fill two 32-lane slots (the 32 + 48 of the general rule take
 // three), error map below 4e-17 over x in [1e-300, 30].
-__device__ __forceinline__ int kint_rule(double v, double x) {
+// h rules 4 and 5 are the one-slot rules of kint_sums_one (22 g + 10 h
+// nodes, s0 = 8, for 2 <= v < 7; 12 + 20, s0 = 3, for 7 <= v <= 16.5), for
+// values only: their error map covers log K, not its x-derivative.
+__device__ __forceinline__ int kint_rule(double v, double x, bool dx) {
+  if (!dx && v >= 2.0 && v <= 16.5) return v < 7.0 ? (22 | (4 << 8)) : (12 | (5 << 8));
   if (v > 1.2 && v <= 5.0) return 24 | (3 << 8);
   const int ng = (v >= 0.9 || x >= 0.25) ? 32 : ((v >= 0.4 || x >= 1e-3) ? 64 : 0);
   const int hr = (v <= 1.2) ? 0 : ((v <= 5.0) ? 1 : 2);
@@ -71,6 +77,7 @@ __device__ __forceinline__ int kint_rule(double v, double x) {
 // operations as the per-pair path: the results do not change).
 struct KintScalar {
   double ub24[24], ub32[32], ub64[64];
+  double sg[22];                                   // s0 u_j^beta of the one-slot rule of v (if any)
   double pre;                                      // log(sqrt(pi)) - lgamma(v + 1/2)
 };
 
@@ -82,6 +89,11 @@ __device__ __forceinline__ void kint_scalar_setup(KintScalar& ks, double v) {
   else if (tid < 56) ks.ub32[tid - 24] = ix_exp(beta * __ldg(lb_kq_g32_logu + tid - 24));
   else if (tid < 120) ks.ub64[tid - 56] = ix_exp(beta * __ldg(lb_kq_g64_logu + tid - 56));
   else if (tid == 120) ks.pre = kHalfLogPi - lgamma(v + 0.5);
+  else if (tid >= 128 && tid < 150 && v >= 2.0 && v <= 16.5) {
+    const int j = tid - 128;
+    if (v < 7.0) ks.sg[j] = ix_exp(fma(beta, __ldg(lb_kq_g22_logu + j), LB_KQ_LOG8));
+    else if (j < 12) ks.sg[j] = ix_exp(fma(beta, __ldg(lb_kq_g12_logu + j), LB_KQ_LOG3));
+  }
   __syncthreads();
 }
 
@@ -177,6 +189,40 @@ __device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta
     const double a0 = t0 / (tx + s), a1 = t1 / (sh + tx);
     s1 = fma(beta, isg ? a0 : 0.0, (isg ? 0.0 : a0) + a1);
   }
+}
+
+// One pair, one lane slot (values, 2 <= v <= 16.5).  int_0^inf F(s) ds is
+// split at s0 instead of 1: on [s0, inf), t = s - s0, the branch point s = 0
+// of (s (s + 2x))^(v-1/2) is s0 away from the Gauss-Laguerre nodes, so 10
+// or 20 of them reach 1e-17; [0, s0] takes s = s0 u^beta and Gauss-Legendre
+// in u on the remaining lanes.  A g node is c + (v+1/2) log s0 +
+// (v-1/2) log(2x + s) - s (beta multiplies the g sum), an h node
+// c + (v-1/2)(y + log(s + 2x)) with y = log s and -s0 in c.  Rule 4: s0 = 8,
+// 22 g + 10 h nodes (2 <= v < 7); rule 5: s0 = 3, 12 + 20 (7 <= v <= 16.5).
+// Error map against a 34-digit reference, over x in [1e-300, 30]: below
+// 1.5e-17 of the error scale max(1, |x d/dx log K|, |v d/dv log K|).
+__device__ __forceinline__ void kint_sums_one(double v, double x, double beta, int hr, int lane,
+                                              double& mm, double& s0, const KintScalar* ks) {
+  const bool r4 = hr == 4;
+  const int ng = r4 ? 22 : 12;
+  const double ls0 = r4 ? LB_KQ_LOG8 : LB_KQ_LOG3;
+  const double vm = v - 0.5, tx = 2.0 * x;
+  const bool isg = lane < ng;
+  double s, y, c;
+  if (isg) {
+    s = ks ? ks->sg[lane] : ix_exp(fma(beta, __ldg((r4 ? lb_kq_g22_logu : lb_kq_g12_logu) + lane), ls0));
+    y = 0.0;
+    c = fma(v + 0.5, ls0, __ldg((r4 ? lb_kq_g22_c : lb_kq_g12_c) + lane));
+  } else {
+    const int j = lane - ng;
+    s = __ldg((r4 ? lb_kq_hq10o8_s : lb_kq_hq20o3_s) + j);
+    y = __ldg((r4 ? lb_kq_hq10o8_y : lb_kq_hq20o3_y) + j);
+    c = __ldg((r4 ? lb_kq_hq10o8_c : lb_kq_hq20o3_c) + j);
+  }
+  const double L = fma(vm, ix_log(tx + s) + y, c) - (isg ? s : 0.0);
+  mm = key_to_double(__reduce_max_sync(0xffffffffu, order_key(L)));
+  const double t = ix_exp(L - mm);
+  s0 = isg ? beta * t : t;
 }
 
 // Split g rule (v < 0.4, x < 1e-3).  (2x + u^beta)^(v-1/2) turns within a
@@ -324,7 +370,7 @@ template <bool DX>
 __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane,
                                                    const KintScalar* ks = nullptr) {
   const double beta_i = 16.0 / (2.0 * vi + 1.0);
-  const int rule_i = kint_rule(vi, xi);
+  const int rule_i = kint_rule(vi, xi, DX);
   double m_i = 0.0, s0_i = 1.0, s1_i = 0.0;
   for (int e = 0; e < npairs; ++e) {
     const double v = __shfl_sync(0xffffffffu, vi, e);
@@ -333,7 +379,9 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     const int rule = __shfl_sync(0xffffffffu, rule_i, e);
     const int ng = rule & 0xff, hr = rule >> 8;
     double mm, s0, s1;
-    if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
+    s1 = 0.0;
+    if (!DX && hr >= 4) kint_sums_one(v, x, beta, hr, lane, mm, s0, ks);
+    else if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
     else if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1, ks);
     else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1, ks);
     s0 = warp_sum(s0);

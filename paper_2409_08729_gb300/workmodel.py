@@ -61,17 +61,24 @@ def set_costs(rates):
 REGION_K = {0: 20, 1: 13, 4: 3, 5: 4, 6: 6, 7: 9}   # region id -> number of expansion terms
 
 
-def kint_rule(v, x):
+def kint_rule(v, x, dx=False):
     """Node counts (g, h) of the tight K-integral rule for each pair (|v| given).
     The split g rule (v < 0.4, x < 1e-3) has 64 + 32 + 32 nodes, plus 32 more
-    below x ~ 4e-21; for 1.2 < v <= 5 the rule is 24 g + 40 h nodes."""
+    below x ~ 4e-21; for 1.2 < v <= 5 the rule is 24 g + 40 h nodes; values
+    (dx False) with 2 <= v <= 16.5 take the one-slot rules, 22 + 10 nodes
+    (v < 7) or 12 + 20."""
     v = np.asarray(v, dtype=np.float64)
     x = np.asarray(x, dtype=np.float64)
     split = np.where(np.log(128 * np.maximum(x, 1e-320)) + 40 < -4, 160, 128)
     ng = np.where((v >= 0.9) | (x >= 0.25), 32, np.where((v >= 0.4) | (x >= 1e-3), 64, split))
     nh = np.where(v <= 1.2, 32, np.where(v <= 5.0, 48, 32))
     packed = (v > 1.2) & (v <= 5.0)                 # 24 g + 40 h nodes
-    return np.where(packed, 24, ng), np.where(packed, 40, nh)
+    ng, nh = np.where(packed, 24, ng), np.where(packed, 40, nh)
+    if not dx:
+        one = (v >= 2.0) & (v <= 16.5)
+        ng = np.where(one, np.where(v < 7.0, 22, 12), ng)
+        nh = np.where(one, np.where(v < 7.0, 10, 20), nh)
+    return ng, nh
 
 
 def kint_slots(v, x, scalar=False):

@@ -1,0 +1,115 @@
+"""The Gauss rules of the K integral (kquad_tables.h), checked on the CPU.
+
+Each rule is summed the way lb_kint.cuh sums it, in 30-digit arithmetic from
+the double-precision table entries, and log K built from the prefactor of
+Rothwell's representation (paper Sec. 3.2):
+
+  log K_v(x) = log(pi)/2 - lgamma(v + 1/2) - v log(2x) - x + log int_0^inf F(s) ds,
+  F(s) = e^{-s} (s (s + 2x))^(v-1/2),
+
+against the oracle (double-double).  The error, in the units of the error
+metric (|err| / max(|log K|, c), c = max(1, |x d/dx log K|, |v d/dv log K|)),
+is the rule's truncation error plus the rounding of its table entries: what
+the kernel would reach in exact arithmetic.  Bounds are 2e-16, a fifth of
+the measured FP64 end-to-end maxima (rounding dominates), and 5e-17 for the
+one-slot rules, whose error map was drawn at 1.5e-17.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+mp = pytest.importorskip("mpmath")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TABLES = os.path.join(HERE, "..", "paper_2409_08729_gb300", "csrc", "kquad_tables.h")
+
+
+def _tables():
+    txt = open(TABLES).read()
+    out = {}
+    for m in re.finditer(r"static __device__ const double (\w+)\[(\d+)\] = \{([^}]*)\};", txt):
+        vals = [float(t) for t in m.group(3).replace("\n", " ").split(",") if t.strip()]
+        assert len(vals) == int(m.group(2)), m.group(1)
+        out[m.group(1)] = vals
+    for m in re.finditer(r"#define (LB_KQ_\w+) (\S+)", txt):
+        out[m.group(1)] = float(m.group(2))
+    return out
+
+
+T = _tables()
+
+
+def _g_fixed(v, x, N):
+    """beta sum_j e^{c_j + (v-1/2) log(2x + u_j^beta) - u_j^beta} (s = u^beta on [0, 1])."""
+    beta = mp.mpf(16) / (2 * v + 1)
+    tot = mp.mpf(0)
+    for lu, c in zip(T["lb_kq_g%d_logu" % N], T["lb_kq_g%d_c" % N]):
+        ub = mp.exp(beta * lu)
+        tot += mp.exp(c + (v - mp.mpf(0.5)) * mp.log(2 * x + ub) - ub)
+    return beta * tot
+
+
+def _h(v, x, tag):
+    """sum_j e^{c_j + (v-1/2)(y_j + log(s_j + 2x))} for the h table `tag`."""
+    tot = mp.mpf(0)
+    for s, y, c in zip(T["lb_kq_%s_s" % tag], T["lb_kq_%s_y" % tag], T["lb_kq_%s_c" % tag]):
+        tot += mp.exp(c + (v - mp.mpf(0.5)) * (y + mp.log(s + 2 * x)))
+    return tot
+
+
+def _g_one(v, x, N, ls0):
+    """The [0, s0] part of a one-slot rule: s_j = e^{beta log u_j + log s0}."""
+    beta = mp.mpf(16) / (2 * v + 1)
+    tot = mp.mpf(0)
+    for lu, c in zip(T["lb_kq_g%d_logu" % N], T["lb_kq_g%d_c" % N]):
+        s = mp.exp(beta * lu + ls0)
+        tot += mp.exp(c + (v + mp.mpf(0.5)) * ls0 + (v - mp.mpf(0.5)) * mp.log(2 * x + s) - s)
+    return beta * tot
+
+
+RULES = {
+    # name: (sum of the rule, the orders and arguments it serves)
+    "g32+hl32": (lambda v, x: _g_fixed(v, x, 32) + _h(v, x, "hl32"), [0.9, 0.97, 1.0, 1.2], [0.25, 1.0, 7.3, 25.0, 30.0]),
+    "g64+hl32": (lambda v, x: _g_fixed(v, x, 64) + _h(v, x, "hl32"), [0.4, 0.55, 0.89], [1e-3, 0.01, 0.2]),
+    "g24+hl40": (lambda v, x: _g_fixed(v, x, 24) + _h(v, x, "hl40"), [1.21, 1.5, 1.99, 3.3, 5.0], [1e-300, 1e-6, 0.04, 1.0, 9.0, 25.0]),
+    "g32+hq32": (lambda v, x: _g_fixed(v, x, 32) + _h(v, x, "hq32"), [5.01, 8.5, 16.0], [1e-300, 0.01, 1.0, 12.0, 25.0]),
+    "one, s0 = 8": (lambda v, x: _g_one(v, x, 22, mp.mpf(T["LB_KQ_LOG8"])) + _h(v, x, "hq10o8"),
+                    [2.0, 2.37, 3.9, 5.5, 6.99], [1e-300, 1e-8, 0.0128, 0.3, 1.0, 4.7, 13.0, 25.0, 30.0]),
+    "one, s0 = 3": (lambda v, x: _g_one(v, x, 12, mp.mpf(T["LB_KQ_LOG3"])) + _h(v, x, "hq20o3"),
+                    [7.0, 7.9, 9.3, 12.71, 16.0, 16.5], [1e-300, 1e-8, 0.0128, 0.3, 1.0, 4.7, 13.0, 25.0, 30.0]),
+}
+
+
+@pytest.mark.parametrize("name", list(RULES))
+def test_rule_error_map(name):
+    fn, vs, xs = RULES[name]
+    V, X = np.meshgrid(np.array(vs), np.array(xs), indexing="ij")
+    V, X = V.ravel(), X.ravel()
+    hi, lo = oracle.log_k(V, X, want_lo=True)
+    c = oracle.error_scale("k", V, X)
+    worst = 0.0
+    with mp.workdps(30):
+        for v, x, h, l, cc in zip(V, X, hi, lo, c):
+            vm, xm = mp.mpf(v), mp.mpf(x)
+            lk = (mp.log(mp.pi) / 2 - mp.loggamma(vm + mp.mpf(0.5)) - vm * mp.log(2 * xm) - xm
+                  + mp.log(fn(vm, xm)))
+            err = float(abs(lk - (mp.mpf(h) + mp.mpf(l)))) / max(abs(h), cc)
+            worst = max(worst, err)
+            assert err < (5e-17 if name.startswith("one") else 2e-16), (name, v, x, err)
+    assert worst > 0.0
+
+
+def test_one_slot_tables():
+    """The one-slot rules' tables: node counts and the split points."""
+    assert len(T["lb_kq_g22_logu"]) == 22 and len(T["lb_kq_hq10o8_s"]) == 10
+    assert len(T["lb_kq_g12_logu"]) == 12 and len(T["lb_kq_hq20o3_s"]) == 20
+    assert T["LB_KQ_LOG8"] == float(mp.log(8)) and T["LB_KQ_LOG3"] == float(mp.log(3))
+    # the Laguerre nodes start past the split point; weights sum to e^{-s0}
+    for tag, s0 in (("hq10o8", 8), ("hq20o3", 3)):
+        assert min(T["lb_kq_%s_s" % tag]) > s0
+        w = sum(mp.exp(c) for c in T["lb_kq_%s_c" % tag])
+        assert abs(w / mp.exp(-s0) - 1) < 1e-15
