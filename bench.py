@@ -264,6 +264,17 @@ def main():
                                          mode, 0))
 
         step_host()
+        # pinned-copy bandwidth of this machine, both directions, one at a time
+        # (the host side varies between boxes; the figure explains the e2e value)
+        link = {}
+        for name, src, dst in (("h2d_gbs", hx, x_all), ("d2h_gbs", x_all, hx)):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            tl = time.perf_counter()
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            link[name] = 3 * n_all * 8 / (time.perf_counter() - tl) / 1e9
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
@@ -279,7 +290,10 @@ def main():
         e2e = {"value": evals_per_step * args.steps * world / (ems / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 2 * (nv * 8 + n1 * 8 * nv + 2 * n_all * 8),
                "d2h_bytes_per_step": 4 * n_all * 8,
-               "api": "logbessel_host (C ABI, pinned host buffers, synchronous per call)"}
+               "api": "logbessel_host (C ABI, pinned host buffers, synchronous per call)",
+               "pinned_copy_gbs": link,
+               "copy_ms_per_step_at_that_rate": 1e3 * (2 * (nv * 8 + n1 * 8 * nv + 2 * n_all * 8) / link["h2d_gbs"]
+                                                       + 4 * n_all * 8 / link["d2h_gbs"]) / 1e9}
         del hx, hv, ho
 
     # ---- sampled accuracy of the timed outputs (FP64) against the oracle ----

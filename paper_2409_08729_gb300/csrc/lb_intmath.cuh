@@ -130,12 +130,10 @@ LB_IX_FN uint32_t ix_fbits(float f) {
 #endif
 }
 
-LB_IX_FN double ix_exp(double y) {
-  const uint64_t b = ix_bits(y);
-  const int E = (int)((b >> 52) & 0x7ff);
-  const bool neg = (b >> 63) != 0;
-  if (E < 959) return 1.0;                                  // |y| < 2^-64 (and zeros, subnormals)
-  if (((uint32_t)(b >> 32) & 0x7fffffffu) > 0x40862000u) return neg ? 0.0 : INFINITY;   // |y| > 708 (or NaN)
+// e^y = 2^(k/512) (1 + p) for 2^-64 <= |y| <= 708, y given by its bits b
+// (biased exponent E, sign neg): returns 2^(j/512) (1 + p) in Q62, in
+// [0.999, 2.002), and k.
+LB_IX_FN int64_t ix_exp_core(uint64_t b, int E, bool neg, int& kout) {
   // |y| in Q116 (exact: the 53-bit significand shifted left by E - 959 <= 73)
   const uint64_t M = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
   const int s = E - 959;
@@ -165,12 +163,41 @@ LB_IX_FN double ix_exp(double y) {
   a = LB_IX_E1 + (ix_mulhi(a, r) >> 9);
   const int64_t p = ix_mulhi(a, r);                         // Q71
   const int64_t t = (int64_t)LB_IX_LOAD(lb_ix_exp_t + (k & 511));   // 2^(j/512), Q62
-  const int64_t res = t + (ix_mulhi(t, p) >> 7);            // Q62, in [0.999, 2.002)
+  kout = k;
+  return t + (ix_mulhi(t, p) >> 7);                         // Q62, in [0.999, 2.002)
+}
+
+LB_IX_FN double ix_exp(double y) {
+  const uint64_t b = ix_bits(y);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const bool neg = (b >> 63) != 0;
+  if (E < 959) return 1.0;                                  // |y| < 2^-64 (and zeros, subnormals)
+  if (((uint32_t)(b >> 32) & 0x7fffffffu) > 0x40862000u) return neg ? 0.0 : INFINITY;   // |y| > 708 (or NaN)
+  int k;
+  const int64_t res = ix_exp_core(b, E, neg, k);
   const int lz = ix_clz((uint64_t)res);                     // 1 or 2
   const uint64_t m53 = (((uint64_t)res << (lz - 1)) + (1ull << 9)) >> 10;   // [2^52, 2^53]
   const int biased = (k >> 9) + 1024 - lz;
   if (biased <= 0) return 0.0;
   return ix_double(((uint64_t)(biased - 1) << 52) + m53);
+}
+
+// e^y in unsigned Q58 fixed point (e^y 2^58, rounded to the nearest
+// integer, ties up), for y < ln 2 (the result is below 2^59, so 32 of them
+// add up without overflow); y <= -42 gives 0 (e^y < 2^-60).  Within 0.6 of
+// the exact value, in units of 2^-58.  For sums of terms e^(L - max L):
+// fixed-point terms add exactly on the integer pipes.
+LB_IX_FN uint64_t ix_exp_q58(double y) {
+  const uint64_t b = ix_bits(y);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const bool neg = (b >> 63) != 0;
+  if (E < 959) return 1ull << 58;                           // |y| < 2^-64
+  if (neg && ((uint32_t)(b >> 32) & 0x7fffffffu) >= 0x40450000u) return 0;   // y <= -42
+  int k;
+  const int64_t res = ix_exp_core(b, E, neg, k);            // e^y = res 2^(k div 512 - 62)
+  const int sh = 4 - (k >> 9);                              // to Q58; k div 512 <= 0 for y < ln 2
+  if (sh >= 64) return 0;                                   // below 2^-59: rounds to 0
+  return ((uint64_t)res + (1ull << (sh - 1))) >> sh;
 }
 
 LB_IX_FN double ix_log(double z) {

@@ -16,7 +16,7 @@
 // Rules:
 //   LB_TIGHT: Gauss rules (tables in kquad_tables.h).  Values (not the
 //     x-derivative) for 2 <= v <= 16.5: one lane slot, the split moved from
-//     s = 1 to s0 (kint_sums_one).  Otherwise, for 1.2 < v <= 5: 24
+//     s = 1 to s0 (kint_sum_one).  Otherwise, for 1.2 < v <= 5: 24
 //     g nodes and 40 h nodes (two full lane slots).  Otherwise g: Gauss-Legendre in u
 //     with 32 nodes (v >= 0.9 or x >= 0.25), 64 (v >= 0.4 or x >= 1e-3), or
 //     for v < 0.4, x < 1e-3 a split rule (kint_sums_split), because
@@ -60,7 +60,7 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
 // g rule 24 goes with h rule 3 (40 nodes in log s): for 1.2 < v <= 5 the
 // 24 + 40 nodes fill two 32-lane slots (the 32 + 48 of the general rule take
 // three), error map below 4e-17 over x in [1e-300, 30].
-// h rules 4 and 5 are the one-slot rules of kint_sums_one (22 g + 10 h
+// h rules 4 and 5 are the one-slot rules of kint_sum_one (22 g + 10 h
 // nodes, s0 = 8, for 2 <= v < 7; 12 + 20, s0 = 3, for 7 <= v <= 16.5), for
 // values only: their error map covers log K, not its x-derivative.
 __device__ __forceinline__ int kint_rule(double v, double x, bool dx) {
@@ -195,24 +195,29 @@ __device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta
 // split at s0 instead of 1: on [s0, inf), t = s - s0, the branch point s = 0
 // of (s (s + 2x))^(v-1/2) is s0 away from the Gauss-Laguerre nodes, so 10
 // or 20 of them reach 1e-17; [0, s0] takes s = s0 u^beta and Gauss-Legendre
-// in u on the remaining lanes.  A g node is c + (v+1/2) log s0 +
-// (v-1/2) log(2x + s) - s (beta multiplies the g sum), an h node
+// in u on the remaining lanes.  A g node is c + gk + (v-1/2) log(2x + s) - s
+// with gk = (v+1/2) log s0 + log beta (per pair), an h node
 // c + (v-1/2)(y + log(s + 2x)) with y = log s and -s0 in c.  Rule 4: s0 = 8,
 // 22 g + 10 h nodes (2 <= v < 7); rule 5: s0 = 3, 12 + 20 (7 <= v <= 16.5).
 // Error map against a 34-digit reference, over x in [1e-300, 30]: below
 // 1.5e-17 of the error scale max(1, |x d/dx log K|, |v d/dv log K|).
-__device__ __forceinline__ void kint_sums_one(double v, double x, double beta, int hr, int lane,
-                                              double& mm, double& s0, const KintScalar* ks) {
+// The terms e^(L - mm) (each below 2, mm the warp maximum of L to 2^-20
+// relative, |L| < 2^19) are formed in Q58 fixed point and summed exactly on
+// the integer pipe (three 20-bit limbs, one warp reduction each): the FP64
+// pipe does only the node's logarithm arguments.  Returns the sum, on every
+// lane, in Q58.
+__device__ __forceinline__ uint64_t kint_sum_one(double v, double x, double beta, double gk, int hr, int lane,
+                                                 double& mm, const KintScalar* ks) {
   const bool r4 = hr == 4;
   const int ng = r4 ? 22 : 12;
-  const double ls0 = r4 ? LB_KQ_LOG8 : LB_KQ_LOG3;
   const double vm = v - 0.5, tx = 2.0 * x;
   const bool isg = lane < ng;
   double s, y, c;
   if (isg) {
-    s = ks ? ks->sg[lane] : ix_exp(fma(beta, __ldg((r4 ? lb_kq_g22_logu : lb_kq_g12_logu) + lane), ls0));
+    s = ks ? ks->sg[lane]
+           : ix_exp(fma(beta, __ldg((r4 ? lb_kq_g22_logu : lb_kq_g12_logu) + lane), r4 ? LB_KQ_LOG8 : LB_KQ_LOG3));
     y = 0.0;
-    c = fma(v + 0.5, ls0, __ldg((r4 ? lb_kq_g22_c : lb_kq_g12_c) + lane));
+    c = __ldg((r4 ? lb_kq_g22_c : lb_kq_g12_c) + lane) + gk;
   } else {
     const int j = lane - ng;
     s = __ldg((r4 ? lb_kq_hq10o8_s : lb_kq_hq20o3_s) + j);
@@ -221,8 +226,11 @@ __device__ __forceinline__ void kint_sums_one(double v, double x, double beta, i
   }
   const double L = fma(vm, ix_log(tx + s) + y, c) - (isg ? s : 0.0);
   mm = key_to_double(__reduce_max_sync(0xffffffffu, order_key(L)));
-  const double t = ix_exp(L - mm);
-  s0 = isg ? beta * t : t;
+  const uint64_t t = ix_exp_q58(L - mm);
+  const unsigned a0 = __reduce_add_sync(0xffffffffu, (unsigned)(t & 0xfffffu));
+  const unsigned a1 = __reduce_add_sync(0xffffffffu, (unsigned)(t >> 20) & 0xfffffu);
+  const unsigned a2 = __reduce_add_sync(0xffffffffu, (unsigned)(t >> 40));
+  return (uint64_t)a0 + ((uint64_t)a1 << 20) + ((uint64_t)a2 << 40);
 }
 
 // Split g rule (v < 0.4, x < 1e-3).  (2x + u^beta)^(v-1/2) turns within a
@@ -371,17 +379,29 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
                                                    const KintScalar* ks = nullptr) {
   const double beta_i = 16.0 / (2.0 * vi + 1.0);
   const int rule_i = kint_rule(vi, xi, DX);
+  // one-slot rules: the g nodes' common factor beta s0^(v+1/2), as a log
+  const double gk_i = (!DX && (rule_i >> 8) >= 4)
+                          ? fma(vi + 0.5, (rule_i >> 8) == 4 ? LB_KQ_LOG8 : LB_KQ_LOG3, ix_log(beta_i)) : 0.0;
   double m_i = 0.0, s0_i = 1.0, s1_i = 0.0;
+  uint64_t q_i = 0;                                // Q58 sum of a one-slot rule
   for (int e = 0; e < npairs; ++e) {
     const double v = __shfl_sync(0xffffffffu, vi, e);
     const double x = __shfl_sync(0xffffffffu, xi, e);
-    const double beta = __shfl_sync(0xffffffffu, beta_i, e);
     const int rule = __shfl_sync(0xffffffffu, rule_i, e);
     const int ng = rule & 0xff, hr = rule >> 8;
-    double mm, s0, s1;
-    s1 = 0.0;
-    if (!DX && hr >= 4) kint_sums_one(v, x, beta, hr, lane, mm, s0, ks);
-    else if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
+    const double beta = __shfl_sync(0xffffffffu, beta_i, e);
+    double mm;
+    if (!DX && hr >= 4) {
+      const double gk = __shfl_sync(0xffffffffu, gk_i, e);
+      const uint64_t q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
+      if (lane == e) {
+        m_i = mm;
+        q_i = q;
+      }
+      continue;
+    }
+    double s0, s1 = 0.0;
+    if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
     else if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1, ks);
     else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1, ks);
     s0 = warp_sum(s0);
@@ -393,6 +413,7 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     }
   }
   if (DX) return -(vi / xi + 1.0) + (2.0 * vi - 1.0) * (s1_i / s0_i);
+  if ((rule_i >> 8) >= 4) s0_i = __ull2double_rn(q_i) * 0x1p-58;   // exact scaling by a power of two
   const double pre = ks ? ks->pre - fma(vi, ix_log(2.0 * xi), xi) : kint_prefactor(vi, xi);
   return pre + m_i + ix_log(s0_i);
 }

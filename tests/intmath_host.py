@@ -15,6 +15,9 @@ _SRC = r'''
 #include "lb_intmath.cuh"
 extern "C" void ix_exp_arr(const double* y, double* o, long n) { for (long i = 0; i < n; ++i) o[i] = lb::ix_exp(y[i]); }
 extern "C" void ix_log_arr(const double* y, double* o, long n) { for (long i = 0; i < n; ++i) o[i] = lb::ix_log(y[i]); }
+extern "C" void ix_exp_q58_arr(const double* y, unsigned long long* o, long n) {
+  for (long i = 0; i < n; ++i) o[i] = lb::ix_exp_q58(y[i]);
+}
 '''
 _lib = None
 
@@ -46,3 +49,11 @@ def ix_exp(a):
 
 def ix_log(a):
     return _run("ix_log_arr", a)
+
+
+def ix_exp_q58(a):
+    """e^a in Q58 fixed point (uint64)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    o = np.empty(a.size, dtype=np.uint64)
+    lib().ix_exp_q58_arr(a.ctypes.data_as(ctypes.c_void_p), o.ctypes.data_as(ctypes.c_void_p), ctypes.c_long(a.size))
+    return o

@@ -4,7 +4,9 @@ import numpy as np
 import pytest
 
 import oracle
-from intmath_host import ix_exp, ix_log
+from fractions import Fraction
+
+from intmath_host import ix_exp, ix_exp_q58, ix_log
 
 
 def _ref(fn, a):
@@ -78,3 +80,32 @@ def test_exp_log_roundtrip(seed):
     y = rng.uniform(-700, 700, 20000)
     back = ix_log(ix_exp(y))
     assert np.max(np.abs(back - y) / np.maximum(np.abs(y), 1.0)) < 4e-16
+
+
+def test_exp_q58():
+    """e^y in Q58 fixed point: within 0.6 units of 2^-58 of the exact value
+    (double-double reference, summed exactly as fractions), y in [-45, ln 2)."""
+    rng = np.random.default_rng(13)
+    y = np.concatenate([rng.uniform(-45, 0.69, 3000), rng.uniform(-1, 0.01, 2000), -np.exp(rng.uniform(-70, 3, 1000)),
+                        np.log(2.0) / 512 * (np.arange(-600, 200) + 0.5), -np.arange(36, 46, 0.25),
+                        [0.0, -0.0, 2.0 ** -70, -2.0 ** -70, 0.5, -42.0, np.nextafter(-42.0, 0)]])
+    got = ix_exp_q58(y)
+    scale = Fraction(2) ** 58
+    for yi, g in zip(y, got):
+        hi, lo = oracle.dd_exp(float(yi))
+        exact = (Fraction(hi) + Fraction(lo)) * scale
+        assert abs(Fraction(int(g)) - exact) <= Fraction(6, 10), (yi, int(g), float(exact))
+    assert int(got[-7]) == 2 ** 58 and int(got[-6]) == 2 ** 58
+
+
+def test_exp_q58_sums():
+    """32 terms e^(L - max L) summed in Q58 (as the K-integral warp sums do)
+    match the double-double sum to 32 x 0.6 units of 2^-58."""
+    rng = np.random.default_rng(14)
+    for _ in range(50):
+        L = rng.normal(0, 8, 32)
+        y = L - L.max()
+        got = sum(int(t) for t in ix_exp_q58(y))
+        assert got < 2 ** 64
+        exact = sum((Fraction(h) + Fraction(l)) for h, l in (oracle.dd_exp(float(v)) for v in y)) * Fraction(2) ** 58
+        assert abs(got - exact) <= 32 * Fraction(6, 10)
