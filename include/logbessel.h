@@ -175,12 +175,12 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
  * 2 d/dx log I, 3 d/dx log K.  v, x, out are host pointers (pinned memory
  * lets the copies overlap with the computation; pageable memory works but
  * copies synchronously).  The pairs are processed in chunks of `chunk`
- * (0 = 8M pairs; at most 2^26) through three device buffers on three
+ * (0 = 8M pairs; at most 2^26) through four device chunk slots and three
  * internal streams, so the copy-in of one chunk, the evaluation of the
  * previous one and the copy-out of the one before overlap.  The call
  * returns when every result is in `out` (it synchronizes).  The streams,
- * events and one device buffer (three chunk slots of v, x and out, plus the
- * K fallback queue: about 3 * 24 * chunk + 4 * chunk bytes in FP64) belong to the
+ * events and one device buffer (four chunk slots of v, x and out, plus the
+ * K fallback queue: about 4 * 24 * chunk + 4 * chunk bytes in FP64) belong to the
  * current device and are kept from one call to the next, grown when a call
  * needs more; calls on the same device run one at a time (a lock).
  * Errors as for the device entry points; LB_ENOTSUP for derivatives in FP32
@@ -238,10 +238,11 @@ long long logbessel_launch_count(void);
 /*
  * Measure the FP64-pipe roofline of the current GPU (microbenchmarks with
  * every SM busy; runs about 0.2 s and synchronizes the stream).  rates is a
- * host array of 11 doubles that receives operations per second for: DFMA,
+ * host array of 13 doubles that receives operations per second for: DFMA,
  * exp, log, division, sqrt, lgamma (CUDA, double precision), and the
  * library's table-driven exp and log, its exp for quadrature terms (no low
- * table part), and its integer-pipe exp and log (11 doubles in all).
+ * table part), and its integer-pipe exp, log, reciprocal and 1/sqrt (13
+ * doubles in all).
  * Returns LB_EINVAL for
  * a NULL rates, LB_ENOMEM or LB_ECUDA on failure.
  */
@@ -253,8 +254,9 @@ lb_status logbessel_measure_fp64(double* rates, void* cuda_stream);
  * 2 CUDA exp, 3 CUDA log, 4 log(cyl_bessel_i0), 5 log(cyl_bessel_i1) (CUDA's
  * order-0/1 functions, the comparison system of paper Sec. 6.1), 6 the
  * table-driven exp without the low table part (quadrature terms; y <= 708),
- * 7 exp and 8 log in fixed-point integer arithmetic (exp: y <= 708).  in/out are
- * device arrays of n doubles.  LB_EINVAL for a bad which, size or pointer.
+ * 7 exp, 8 log, 9 reciprocal and 10 1/sqrt in fixed-point integer
+ * arithmetic (exp: y <= 708).  in/out are device arrays of n doubles.
+ * LB_EINVAL for a bad which, size or pointer.
  */
 lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t n, void* cuda_stream);
 

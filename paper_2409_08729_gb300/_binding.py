@@ -97,7 +97,7 @@ def launch_count():
 
 def measure_fp64(stream=None):
     """Measured FP64 rates of the current GPU: {'dfma','exp','log','div','sqrt','lgamma'} per second."""
-    rates = (ctypes.c_double * 11)()
+    rates = (ctypes.c_double * 13)()
     check(lib().logbessel_measure_fp64(rates, stream))
-    return dict(zip(("dfma", "exp", "log", "div", "sqrt", "lgamma", "fm_exp", "fm_log", "fm_exp_term", "ix_exp", "ix_log"),
-                    list(rates)))
+    return dict(zip(("dfma", "exp", "log", "div", "sqrt", "lgamma", "fm_exp", "fm_log", "fm_exp_term", "ix_exp", "ix_log",
+                     "ix_rcp", "ix_rsqrt"), list(rates)))

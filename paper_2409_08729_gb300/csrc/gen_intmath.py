@@ -12,6 +12,10 @@ in 64- and 128-bit integers instead of doubles:
        Q116 (the entry for j = 511 is this same constant).
   Horner coefficients of e^r - 1 and log(1 + r) in Q31 (inner steps, done
   with 32-bit multiplies) and Q62.
+  rcp and rsqrt reuse the log's C_j (m C_j / 2^13 = 1 + r): 1/m =
+       (C_j / 2^13) / (1 + r), m^-1/2 = sqrt(C_j / 2^13) (1 + r)^-1/2, with
+       sqrt(C_j / 2^13) in Q63 and the binomial coefficients of
+       (1 + r)^-1/2 (dyadic rationals) in Q30 and Q62.
 """
 import os
 import sys
@@ -82,6 +86,19 @@ def main():
         L.append("#define LB_IX_L%d %d" % (k, q(mp.mpf(1) / k, 31)))
     for k in (1, 2, 3):
         L.append("#define LB_IX_L%d %dll" % (k, q(mp.mpf(1) / k, 62)))
+    # rsqrt: sqrt(C_j / 2^13) in Q63 (at most 2^63, for j = 0)
+    rsq = [q(mp.sqrt(mp.mpf(cj) / 2 ** 13), 63) for cj in c]
+    assert all(v <= 1 << 63 for v in rsq)
+    L.append(arr("uint64_t", "lb_ix_rsq_t", rsq, u64))
+    # (1 + r)^-1/2 = 1 - r (1/2 - r (3/8 - r (5/16 - r (35/128 - r (63/256 - r 231/1024))))):
+    # the coefficients binom(2k, k) / 4^k; 3..6 in Q30, 1..2 in Q62 (all exact)
+    for k in range(1, 7):
+        ck = mp.binomial(2 * k, k) / mp.mpf(4) ** k
+        if k >= 3:
+            L.append("#define LB_IX_R%d %d" % (k, q(ck, 30)))
+        else:
+            L.append("#define LB_IX_R%d %dll" % (k, q(ck, 62)))
+    L.append("#define LB_IX_RSQRT_HALF 0x%016xull" % q(1 / mp.sqrt(2), 64))
     with open(out, "w") as f:
         f.write("\n".join(L) + "\n")
 

@@ -167,7 +167,8 @@ __device__ __forceinline__ double mu_expr(double v, double x) {
   }
   n = __reduce_max_sync(0xffffffffu, n);
   const double mu = 4.0 * v * v;
-  const double inv8x = (KIND == KIND_I ? -1.0 : 1.0) / (8.0 * x);     // the sign s folded in
+  const double rx = ix_rcp_call(8.0 * x);                             // 1/(8x) on the integer pipe
+  const double inv8x = (KIND == KIND_I) ? -rx : rx;                   // the sign s folded in
   double P = 1.0;
   // Unrolled, so 1/k and (2k-1)^2/k are constants and each term costs three
   // FP64 operations: a = mu/k - (2k-1)^2/k, P = 1 + (a s/(8x)) P.  Terms
@@ -240,16 +241,16 @@ __device__ __forceinline__ T debye_Q(int k, T p) {
 // ---------------------------------------------------------------------------
 template <int KIND, int K>
 __device__ __forceinline__ double u_expr(double v, double x) {
-  const double inv_v = 1.0 / v;
+  const double inv_v = ix_rcp_call(v);           // reciprocal and root on the integer pipe
   const double xp = x * inv_v;
   double r, t;
   if (LB_LT(xp, 1e150)) {
     const double r2 = fma(xp, xp, 1.0);
-    t = rsqrt(r2);                               // t = (1 + x'^2)^-1/2
+    t = ix_rsqrt_call(r2);                       // t = (1 + x'^2)^-1/2
     r = r2 * t;
   } else {
     r = xp;                                      // 1 + x'^2 rounds to x'^2
-    t = 1.0 / r;
+    t = ix_rcp_call(r);
   }
   const double p = t * t;
   double q = t * inv_v;
@@ -317,7 +318,7 @@ __device__ __forceinline__ double series_log_i(double v, double x) {
     A = fma(d, B, y * A);
     B *= d;
   }
-  double res = ix_log_call(A / B) - lgamma(v + 1.0);
+  double res = ix_log_call(A * ix_rcp_call(B)) - lgamma(v + 1.0);
   if (v != 0.0) res = fma(v, ix_log_call(0.5 * x), res);
   return res;
 }
@@ -396,7 +397,7 @@ __device__ __forceinline__ double mu_expr_so(const ScalarOrder& so, double x) {
     }
   }
   n = __reduce_max_sync(0xffffffffu, n);
-  const double w = 1.0 / (8.0 * x);
+  const double w = ix_rcp_call(8.0 * x);
   double P = 0.0;
 #pragma unroll
   for (int k = K; k >= 0; --k)
@@ -413,11 +414,11 @@ __device__ __forceinline__ double u_expr_so(const ScalarOrder& so, double x) {
   double r, t;
   if (LB_LT(xp, 1e150)) {
     const double r2 = fma(xp, xp, 1.0);
-    t = rsqrt(r2);
+    t = ix_rsqrt_call(r2);
     r = r2 * t;
   } else {
     r = xp;
-    t = 1.0 / r;
+    t = ix_rcp_call(r);
   }
   const double* C = K == 4 ? so.u4 : (K == 6 ? so.u6 : (K == 9 ? so.u9 : so.u13));
   double S = C[3 * K];

@@ -84,7 +84,7 @@ struct KintScalar {
 // All threads of the block call it; ends with a barrier.
 __device__ __forceinline__ void kint_scalar_setup(KintScalar& ks, double v) {
   const int tid = threadIdx.x;
-  const double beta = 16.0 / (2.0 * v + 1.0);
+  const double beta = 16.0 * ix_rcp(2.0 * v + 1.0);       // as in kint_batch_gauss
   if (tid < 24) ks.ub24[tid] = ix_exp(beta * __ldg(lb_kq_g24_logu + tid));
   else if (tid < 56) ks.ub32[tid - 24] = ix_exp(beta * __ldg(lb_kq_g32_logu + tid - 24));
   else if (tid < 120) ks.ub64[tid - 56] = ix_exp(beta * __ldg(lb_kq_g64_logu + tid - 56));
@@ -377,7 +377,7 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
 template <bool DX>
 __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane,
                                                    const KintScalar* ks = nullptr) {
-  const double beta_i = 16.0 / (2.0 * vi + 1.0);
+  const double beta_i = 16.0 * ix_rcp(2.0 * vi + 1.0);   // the reciprocal on the integer pipe
   const int rule_i = kint_rule(vi, xi, DX);
   // one-slot rules: the g nodes' common factor beta s0^(v+1/2), as a log
   const double gk_i = (!DX && (rule_i >> 8) >= 4)

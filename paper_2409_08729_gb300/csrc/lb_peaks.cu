@@ -8,8 +8,8 @@
 // The ratio DFMA rate / call rate is the number of DFMA issue slots one call
 // occupies, which the roofline accounting uses as the cost of a call.  The
 // table-driven exp (also without its low table part) and log of
-// lb_fastmath.cuh, and the integer-pipe exp and log of lb_intmath.cuh, are
-// measured the same way.
+// lb_fastmath.cuh, and the integer-pipe exp, log, reciprocal and 1/sqrt of
+// lb_intmath.cuh, are measured the same way.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,6 +43,8 @@ __device__ __forceinline__ double call_op(double a) {
   if (OP == 7) return lb::fm_exp_term(a) * 0.1;
   if (OP == 8) return lb::ix_exp(a) * 0.1;
   if (OP == 9) return lb::ix_log(a) + 2.0;
+  if (OP == 10) return lb::ix_rcp(a) + 2.0;
+  if (OP == 11) return lb::ix_rsqrt(a) + 2.0;
   return lgamma(a) + 2.0;
 }
 
@@ -70,7 +72,7 @@ extern "C" lb_status logbessel_measure_fp64(double* rates, void* cuda_stream) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   lb_status status = LB_OK;
-  for (int which = 0; which < 11 && status == LB_OK; ++which) {
+  for (int which = 0; which < 13 && status == LB_OK; ++which) {
     const int iters = which == 0 ? 1000 : (which == 5 ? 40 : 160);
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
@@ -86,7 +88,9 @@ extern "C" lb_status logbessel_measure_fp64(double* rates, void* cuda_stream) {
         case 7: peak_call<6><<<blocks, threads, 0, st>>>(buf, iters); break;
         case 8: peak_call<7><<<blocks, threads, 0, st>>>(buf, iters); break;
         case 9: peak_call<8><<<blocks, threads, 0, st>>>(buf, iters); break;
-        default: peak_call<9><<<blocks, threads, 0, st>>>(buf, iters); break;
+        case 10: peak_call<9><<<blocks, threads, 0, st>>>(buf, iters); break;
+        case 11: peak_call<10><<<blocks, threads, 0, st>>>(buf, iters); break;
+        default: peak_call<11><<<blocks, threads, 0, st>>>(buf, iters); break;
       }
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) { status = LB_ECUDA; break; }

@@ -189,7 +189,9 @@ __global__ void lb_math_kernel(int which, const double* __restrict__ in, double*
       case 5: r = log(cyl_bessel_i1(a)); break;
       case 6: r = fm_exp_term(a); break;
       case 7: r = ix_exp(a); break;
-      default: r = ix_log(a); break;
+      case 8: r = ix_log(a); break;
+      case 9: r = ix_rcp(a); break;
+      default: r = ix_rsqrt(a); break;
     }
     out[i] = r;
   }
@@ -571,13 +573,18 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
 }
 
 lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t n, void* cuda_stream) {
-  if (which < 0 || which > 8) return fail(LB_EINVAL, "which must be 0..8 (got %s%lld)", "", (long long)which);
+  if (which < 0 || which > 10) return fail(LB_EINVAL, "which must be 0..10 (got %s%lld)", "", (long long)which);
   if (n < 0 || (n > 0 && (!in || !out))) return fail(LB_EINVAL, "bad buffer or size %s%lld", "", (long long)n);
   if (n == 0) return LB_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int grid = sm_count() * 4;
   return launch(PS_AUX, st, [&] { lb_math_kernel<<<grid, LB_THREADS, 0, st>>>(which, in, out, n); });
 }
+
+// Chunk slots of the pipeline: one more than the three stages, so that a
+// copy that stalls for a while (the host memory is shared) does not stop
+// the evaluation of the next chunk.
+constexpr int kHostSlots = 4;
 
 // Streams, events and the device buffer of logbessel_host, kept per device
 // from one call to the next: allocating and releasing the few hundred MB of
@@ -588,7 +595,7 @@ struct HostPipe {
   std::mutex mu;
   bool init = false;
   cudaStream_t st[3] = {};
-  cudaEvent_t ev_in[3] = {}, ev_comp[3] = {}, ev_out[3] = {};
+  cudaEvent_t ev_in[kHostSlots] = {}, ev_comp[kHostSlots] = {}, ev_out[kHostSlots] = {};
   char* dbuf = nullptr;
   size_t bytes = 0;
 };
@@ -601,12 +608,14 @@ HostPipe& host_pipe(int dev) {
 
 void host_pipe_destroy(HostPipe& P) {
   if (P.dbuf) cudaFree(P.dbuf);
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < kHostSlots; ++i) {
     if (P.ev_in[i]) cudaEventDestroy(P.ev_in[i]);
     if (P.ev_comp[i]) cudaEventDestroy(P.ev_comp[i]);
     if (P.ev_out[i]) cudaEventDestroy(P.ev_out[i]);
-    if (P.st[i]) cudaStreamDestroy(P.st[i]);
     P.ev_in[i] = P.ev_comp[i] = P.ev_out[i] = nullptr;
+  }
+  for (int i = 0; i < 3; ++i) {
+    if (P.st[i]) cudaStreamDestroy(P.st[i]);
     P.st[i] = nullptr;
   }
   P.dbuf = nullptr;
@@ -616,9 +625,9 @@ void host_pipe_destroy(HostPipe& P) {
 
 bool host_pipe_init(HostPipe& P) {
   bool ok = true;
-  for (int i = 0; i < 3 && ok; ++i)
-    ok = cudaStreamCreateWithFlags(&P.st[i], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&P.ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
+  for (int i = 0; i < 3 && ok; ++i) ok = cudaStreamCreateWithFlags(&P.st[i], cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < kHostSlots && ok; ++i)
+    ok = cudaEventCreateWithFlags(&P.ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&P.ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&P.ev_out[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
@@ -647,7 +656,7 @@ lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride
   if (!P.init && !host_pipe_init(P))
     return fail(LB_ENOMEM, "%slogbessel_host: stream or event creation failed", "", 0);
   const size_t es = dtype == LB_F64 ? 8 : 4;
-  const int64_t nbuf = 3;                         // copy-in, compute and copy-out of three chunks overlap
+  const int64_t nbuf = kHostSlots;                // copy-in, compute and copy-out of successive chunks overlap
   const int64_t cap = n < chunk ? n : chunk;
   const size_t vbytes = (size_t)(v_stride ? cap : 1) * es, xbytes = (size_t)cap * es;
   const size_t slot = ((vbytes + 255) & ~(size_t)255) + 2 * ((xbytes + 255) & ~(size_t)255);

@@ -6,7 +6,8 @@ multiply-add or compare the method performs, and for each library call
 issue slots one call occupies on this GPU, i.e. (DFMA throughput) / (call
 throughput) less the one extra operation of the measuring loop, both
 measured with all SMs busy by logbessel_measure_fp64.  The table-driven exp
-and log of lb_fastmath.cuh are counted the same way.
+and log of lb_fastmath.cuh and the integer-pipe exp, log, reciprocal and
+1/sqrt of lb_intmath.cuh are counted the same way.
 FLOP = 2 x slots (an FMA counts two).
 
 The counts follow the code paths of lb_expr.cuh and lb_kint.cuh (tight mode,
@@ -37,12 +38,16 @@ SLOT_LOG = 14.0
 # DFMA slots that the time of one call at full throughput would hold
 SLOT_IX_EXP = 3.0
 SLOT_IX_LOG = 3.5
+# reciprocal and 1/sqrt on the integer pipes (lb_intmath.cuh), priced the same way
+SLOT_IX_RCP = 3.5
+SLOT_IX_RSQRT = 4.0
 
 
 def set_costs(rates):
     """Set the slot costs from measured rates (dict of operations per second,
     as returned by _binding.measure_fp64)."""
     global SLOT_DIV, SLOT_SQRT, SLOT_RSQRT, SLOT_LGAMMA, SLOT_EXP, SLOT_EXP_TERM, SLOT_LOG, SLOT_IX_EXP, SLOT_IX_LOG
+    global SLOT_IX_RCP, SLOT_IX_RSQRT
     d = rates["dfma"]
     SLOT_DIV = d / rates["div"] - 1.0
     SLOT_SQRT = SLOT_RSQRT = d / rates["sqrt"] - 1.0
@@ -54,8 +59,12 @@ def set_costs(rates):
     if "ix_exp" in rates:
         SLOT_IX_EXP = d / rates["ix_exp"] - 1.0
         SLOT_IX_LOG = d / rates["ix_log"] - 1.0
+    if "ix_rcp" in rates:
+        SLOT_IX_RCP = d / rates["ix_rcp"] - 1.0
+        SLOT_IX_RSQRT = d / rates["ix_rsqrt"] - 1.0
     return {"div": SLOT_DIV, "sqrt": SLOT_SQRT, "lgamma": SLOT_LGAMMA, "fm_exp": SLOT_EXP,
-            "fm_exp_term": SLOT_EXP_TERM, "fm_log": SLOT_LOG, "ix_exp": SLOT_IX_EXP, "ix_log": SLOT_IX_LOG}
+            "fm_exp_term": SLOT_EXP_TERM, "fm_log": SLOT_LOG, "ix_exp": SLOT_IX_EXP, "ix_log": SLOT_IX_LOG,
+            "ix_rcp": SLOT_IX_RCP, "ix_rsqrt": SLOT_IX_RSQRT}
 
 
 REGION_K = {0: 20, 1: 13, 4: 3, 5: 4, 6: 6, 7: 9}   # region id -> number of expansion terms
@@ -95,7 +104,7 @@ def kint_slots(v, x, scalar=False):
     h_node = 5 + SLOT_IX_EXP + SLOT_IX_LOG
     # per pair (once per lane of its batch): beta (div), prefactor (lgamma,
     # log, 3 ops), final log and beta g + h; the warp sum (5 adds, all lanes)
-    per_pair = SLOT_DIV + (0 if scalar else SLOT_LGAMMA) + SLOT_IX_LOG + 3 + SLOT_IX_LOG + 2 + 1 + 5
+    per_pair = SLOT_IX_RCP + 2 + (0 if scalar else SLOT_LGAMMA) + SLOT_IX_LOG + 3 + SLOT_IX_LOG + 2 + 1 + 5
     # split rule: log s1, C, three panel widths (log + add each), the flat term (log, expm1, division)
     per_pair = per_pair + np.where(split, 2 + 4 * SLOT_LOG + 3 + SLOT_EXP + SLOT_DIV + 4, 0)
     return ng * g_node + nh * h_node + per_pair
@@ -120,14 +129,14 @@ def mu_terms(v, x, K=20):
 
 def mu_slots(v, x, K=20):
     # per term: fma, multiply, fma; plus 4v^2, 1/(8x), S^2 and two products, log, fma
-    return mu_terms(v, x, K) * 3 + 2 + SLOT_DIV + 3 + SLOT_IX_LOG + 1
+    return mu_terms(v, x, K) * 3 + 2 + SLOT_IX_RCP + 4 + SLOT_IX_LOG + 1
 
 
 def u_slots(K):
     # 1/v, x/v, fma, rsqrt, r = r2 t, t*t, t/v, sum_k k Horner fmas of P_k, K in q,
     # eta (add, two logs, subtract, add), tail (3 multiplies, log, 2 multiplies, fma)
     horner = sum(k for k in range(1, K + 1)) + K
-    return (SLOT_DIV + 1 + 1 + SLOT_RSQRT + 1 + 1 + 1 + horner
+    return (SLOT_IX_RCP + 1 + 1 + SLOT_IX_RSQRT + 1 + 1 + 1 + horner
             + 1 + 2 * SLOT_IX_LOG + 1 + 1 + 3 + SLOT_IX_LOG + 3)
 
 
@@ -155,18 +164,18 @@ def series_terms(v, x):
 def series_slots(v, x):
     # per term: k + v, d = k (k + v), y A, fma, B d; plus A/B, log, lgamma, log(x/2), fma
     n = series_terms(v, x)
-    return n * 5 + SLOT_DIV + SLOT_IX_LOG + SLOT_LGAMMA + SLOT_IX_LOG + 3
+    return n * 5 + SLOT_IX_RCP + 1 + SLOT_IX_LOG + SLOT_LGAMMA + SLOT_IX_LOG + 3
 
 
 def mu_slots_scalar(v, x, K=20):
     # one order for all pairs: per term one fma; plus 1/(8x), S^2 and two products, log, fma
-    return mu_terms(v, x, K) * 1 + SLOT_DIV + 3 + SLOT_IX_LOG + 1
+    return mu_terms(v, x, K) * 1 + SLOT_IX_RCP + 1 + 3 + SLOT_IX_LOG + 1
 
 
 def u_slots_scalar(K):
     # x/v, fma, rsqrt, r2 t, Horner of degree 3K in t, eta (add, two logs, subtract, add),
     # tail (3 multiplies, log, 2 multiplies, fma)
-    return 1 + 1 + SLOT_RSQRT + 1 + 3 * K + 1 + 2 * SLOT_IX_LOG + 1 + 1 + 3 + SLOT_IX_LOG + 3
+    return 1 + 1 + SLOT_IX_RSQRT + 1 + 3 * K + 1 + 2 * SLOT_IX_LOG + 1 + 1 + 3 + SLOT_IX_LOG + 3
 
 
 def series_slots_scalar(v, x):

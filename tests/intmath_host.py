@@ -15,6 +15,8 @@ _SRC = r'''
 #include "lb_intmath.cuh"
 extern "C" void ix_exp_arr(const double* y, double* o, long n) { for (long i = 0; i < n; ++i) o[i] = lb::ix_exp(y[i]); }
 extern "C" void ix_log_arr(const double* y, double* o, long n) { for (long i = 0; i < n; ++i) o[i] = lb::ix_log(y[i]); }
+extern "C" void ix_rcp_arr(const double* y, double* o, long n) { for (long i = 0; i < n; ++i) o[i] = lb::ix_rcp(y[i]); }
+extern "C" void ix_rsqrt_arr(const double* y, double* o, long n) { for (long i = 0; i < n; ++i) o[i] = lb::ix_rsqrt(y[i]); }
 extern "C" void ix_exp_q58_arr(const double* y, unsigned long long* o, long n) {
   for (long i = 0; i < n; ++i) o[i] = lb::ix_exp_q58(y[i]);
 }
@@ -57,3 +59,11 @@ def ix_exp_q58(a):
     o = np.empty(a.size, dtype=np.uint64)
     lib().ix_exp_q58_arr(a.ctypes.data_as(ctypes.c_void_p), o.ctypes.data_as(ctypes.c_void_p), ctypes.c_long(a.size))
     return o
+
+
+def ix_rcp(a):
+    return _run("ix_rcp_arr", a)
+
+
+def ix_rsqrt(a):
+    return _run("ix_rsqrt_arr", a)

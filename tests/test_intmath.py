@@ -6,7 +6,7 @@ import pytest
 import oracle
 from fractions import Fraction
 
-from intmath_host import ix_exp, ix_exp_q58, ix_log
+from intmath_host import ix_exp, ix_exp_q58, ix_log, ix_rcp, ix_rsqrt
 
 
 def _ref(fn, a):
@@ -109,3 +109,53 @@ def test_exp_q58_sums():
         assert got < 2 ** 64
         exact = sum((Fraction(h) + Fraction(l)) for h, l in (oracle.dd_exp(float(v)) for v in y)) * Fraction(2) ** 58
         assert abs(got - exact) <= 32 * Fraction(6, 10)
+
+
+def _ulp_err_exact(got, exact):
+    """|got - exact| in ulps of exact (exact a Fraction)."""
+    e = abs(Fraction(got) - exact)
+    return float(e / Fraction(np.spacing(float(exact))))
+
+
+def _args(seed):
+    rng = np.random.default_rng(seed)
+    z = np.concatenate([np.exp(rng.uniform(-700, 700, 4000)), rng.uniform(1.0, 2.0, 3000),
+                        1.0 + np.arange(512) / 512.0, 1.0 + (np.arange(512) + 1) / 512.0 - 2.0 ** -52,
+                        1.0 + np.arange(1, 100) * 2.0 ** -52, 2.0 - np.arange(1, 100) * 2.0 ** -52,
+                        2.0 ** np.arange(-1022, 1022, 11), 3.0 * 2.0 ** np.arange(-1000, 1000, 13),
+                        [2.0 ** -1022, np.nextafter(2.0 ** 1022, 0), 3.0, 10.0, 0.1, 1e300]])
+    return z
+
+
+def test_rcp_accuracy():
+    """Integer-pipe 1/z within 0.51 ulp of the exact rational."""
+    z = _args(15)
+    got = ix_rcp(z)
+    worst = max(_ulp_err_exact(g, 1 / Fraction(float(v))) for g, v in zip(got, z))
+    assert worst < 0.51, worst
+
+
+def test_rsqrt_accuracy():
+    """Integer-pipe 1/sqrt(z) within 0.52 ulp (50-digit reference)."""
+    mp = pytest.importorskip("mpmath")
+    z = _args(16)
+    got = ix_rsqrt(z)
+    worst = 0.0
+    with mp.workdps(50):
+        for g, v in zip(got, z):
+            ref = 1 / mp.sqrt(mp.mpf(float(v)))
+            e = abs(mp.mpf(float(g)) - ref) / mp.mpf(float(np.spacing(float(ref))))
+            worst = max(worst, float(e))
+    assert worst < 0.52, worst
+
+
+def test_rcp_rsqrt_special():
+    """Exact cases and the arguments that go to the division / libm root."""
+    z = np.array([1.0, 2.0, 4.0, 0.25, 2.0 ** -1022, 2.0 ** 1021])
+    assert np.array_equal(ix_rcp(z), 1.0 / z)
+    assert np.array_equal(ix_rsqrt(np.array([1.0, 4.0, 0.25, 2.0 ** 1022, 2.0 ** -1022])),
+                          [1.0, 0.5, 2.0, 2.0 ** -511, 2.0 ** 511])
+    odd = ix_rcp(np.array([0.0, -2.0, np.inf, 5e-324, 2.0 ** 1023]))
+    assert odd[0] == np.inf and odd[1] == -0.5 and odd[2] == 0.0 and odd[4] == 2.0 ** -1023
+    r = ix_rsqrt(np.array([0.0, -1.0, np.inf]))
+    assert r[0] == np.inf and np.isnan(r[1]) and r[2] == 0.0
