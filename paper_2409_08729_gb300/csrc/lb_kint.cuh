@@ -191,6 +191,96 @@ __device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta
   }
 }
 
+// Exact warp maximum of doubles, on the integer pipe: key64 maps a double to
+// an int64 of the same order (negative values with all but the sign bit
+// flipped); the maximum key is found as its high word (one reduction) and
+// then the low word among the lanes that hold that high word (another).
+__device__ __forceinline__ long long key64(double a) {
+  const long long b = __double_as_longlong(a);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double warp_max_key64(long long k) {
+  const int khi = (int)(k >> 32);
+  const int mhi = __reduce_max_sync(0xffffffffu, khi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, khi == mhi ? (unsigned)k : 0u);
+  const long long m = (long long)(((unsigned long long)(unsigned)mhi << 32) | mlo);
+  return __longlong_as_double(m ^ ((m >> 63) & 0x7fffffffffffffffll));
+}
+
+// Warp sum of values below 2^63 (the result must stay below 2^64), exact,
+// on the integer pipe: three limbs of 20, 20 and 23 bits, one warp
+// reduction each (a limb sum stays below 2^28).
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t t) {
+  const unsigned a0 = __reduce_add_sync(0xffffffffu, (unsigned)(t & 0xfffffu));
+  const unsigned a1 = __reduce_add_sync(0xffffffffu, (unsigned)(t >> 20) & 0xfffffu);
+  const unsigned a2 = __reduce_add_sync(0xffffffffu, (unsigned)(t >> 40));
+  return (uint64_t)a0 + ((uint64_t)a1 << 20) + ((uint64_t)a2 << 40);
+}
+
+// Values (not the x-derivative) with the fixed or packed rules: the same
+// nodes as kint_sums_fixed / kint_sums_g24h40, with log beta (gk) added to
+// the g nodes' logarithms instead of beta multiplying their sum, and the
+// terms e^(L - mm) summed in Q56 fixed point on the integer pipe (mm the
+// exact maximum, so each term is at most 1; at most 4 terms per lane, so
+// the warp sum stays at most 2^63).
+__device__ __forceinline__ uint64_t kint_sumq_fixed(double v, double x, double beta, double gk, int ng, int hr,
+                                                    int lane, double& mm, const KintScalar* ks) {
+  const double vm = v - 0.5, tx = 2.0 * x;
+  const double* gu = ng == 32 ? lb_kq_g32_logu : lb_kq_g64_logu;
+  const double* gc = ng == 32 ? lb_kq_g32_c : lb_kq_g64_c;
+  const double* hs = hr == 0 ? lb_kq_hl32_s : (hr == 1 ? lb_kq_hl48_s : lb_kq_hq32_s);
+  const double* hy = hr == 0 ? lb_kq_hl32_y : (hr == 1 ? lb_kq_hl48_y : lb_kq_hq32_y);
+  const double* hc = hr == 0 ? lb_kq_hl32_c : (hr == 1 ? lb_kq_hl48_c : lb_kq_hq32_c);
+  const int nh = hr == 1 ? 48 : 32;
+  double L[4];
+  long long key = (long long)0x8000000000000000ull;   // below every key
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    L[k] = 0.0;
+    if (32 * k < ng) {
+      const int j = lane + 32 * k;
+      const double ub = ks ? (ng == 32 ? ks->ub32[j] : ks->ub64[j]) : ix_exp(beta * __ldg(gu + j));
+      L[k] = fma(vm, ix_log(tx + ub), __ldg(gc + j) + gk) - ub;
+      key = max(key, key64(L[k]));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int j = lane + 32 * k;
+    L[2 + k] = 0.0;
+    if (j < nh) {
+      const double sj = __ldg(hs + j);
+      L[2 + k] = fma(vm, __ldg(hy + j) + ix_log(sj + tx), __ldg(hc + j));
+      key = max(key, key64(L[2 + k]));
+    }
+  }
+  mm = warp_max_key64(key);
+  uint64_t q = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool live = (k < 2) ? (32 * k < ng) : (lane + 32 * (k - 2) < nh);
+    if (live) q += ix_exp_q58(L[k] - mm) >> 2;
+  }
+  return warp_sum_u64(q);
+}
+
+__device__ __forceinline__ uint64_t kint_sumq_g24h40(double v, double x, double beta, double gk, int lane,
+                                                     double& mm, const KintScalar* ks) {
+  const double vm = v - 0.5, tx = 2.0 * x;
+  const bool isg = lane < 24;
+  const int jh = isg ? 0 : lane - 24;
+  double s;
+  if (isg) s = ks ? ks->ub24[lane] : ix_exp(beta * __ldg(lb_kq_g24_logu + lane));
+  else s = __ldg(lb_kq_hl40_s + jh);
+  const double y0 = isg ? 0.0 : __ldg(lb_kq_hl40_y + jh);
+  const double c0 = isg ? __ldg(lb_kq_g24_c + lane) + gk : __ldg(lb_kq_hl40_c + jh);
+  const double L0 = fma(vm, ix_log(tx + s) + y0, c0) - (isg ? s : 0.0);
+  const double sh = __ldg(lb_kq_hl40_s + 8 + lane);
+  const double L1 = fma(vm, __ldg(lb_kq_hl40_y + 8 + lane) + ix_log(sh + tx), __ldg(lb_kq_hl40_c + 8 + lane));
+  mm = warp_max_key64(max(key64(L0), key64(L1)));
+  return warp_sum_u64((ix_exp_q58(L0 - mm) >> 2) + (ix_exp_q58(L1 - mm) >> 2));
+}
+
 // One pair, one lane slot (values, 2 <= v <= 16.5).  int_0^inf F(s) ds is
 // split at s0 instead of 1: on [s0, inf), t = s - s0, the branch point s = 0
 // of (s (s + 2x))^(v-1/2) is s0 away from the Gauss-Laguerre nodes, so 10
@@ -201,11 +291,10 @@ __device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta
 // 22 g + 10 h nodes (2 <= v < 7); rule 5: s0 = 3, 12 + 20 (7 <= v <= 16.5).
 // Error map against a 34-digit reference, over x in [1e-300, 30]: below
 // 1.5e-17 of the error scale max(1, |x d/dx log K|, |v d/dv log K|).
-// The terms e^(L - mm) (each below 2, mm the warp maximum of L to 2^-20
-// relative, |L| < 2^19) are formed in Q58 fixed point and summed exactly on
-// the integer pipe (three 20-bit limbs, one warp reduction each): the FP64
-// pipe does only the node's logarithm arguments.  Returns the sum, on every
-// lane, in Q58.
+// The terms e^(L - mm) (each at most 1: mm is the exact warp maximum of L)
+// are formed in Q58 fixed point and summed exactly on the integer pipe
+// (warp_sum_u64): the FP64 pipe does only the node's logarithm arguments.
+// Returns the sum, on every lane, in Q58.
 __device__ __forceinline__ uint64_t kint_sum_one(double v, double x, double beta, double gk, int hr, int lane,
                                                  double& mm, const KintScalar* ks) {
   const bool r4 = hr == 4;
@@ -225,12 +314,8 @@ __device__ __forceinline__ uint64_t kint_sum_one(double v, double x, double beta
     c = __ldg((r4 ? lb_kq_hq10o8_c : lb_kq_hq20o3_c) + j);
   }
   const double L = fma(vm, ix_log(tx + s) + y, c) - (isg ? s : 0.0);
-  mm = key_to_double(__reduce_max_sync(0xffffffffu, order_key(L)));
-  const uint64_t t = ix_exp_q58(L - mm);
-  const unsigned a0 = __reduce_add_sync(0xffffffffu, (unsigned)(t & 0xfffffu));
-  const unsigned a1 = __reduce_add_sync(0xffffffffu, (unsigned)(t >> 20) & 0xfffffu);
-  const unsigned a2 = __reduce_add_sync(0xffffffffu, (unsigned)(t >> 40));
-  return (uint64_t)a0 + ((uint64_t)a1 << 20) + ((uint64_t)a2 << 40);
+  mm = warp_max_key64(key64(L));
+  return warp_sum_u64(ix_exp_q58(L - mm));
 }
 
 // Split g rule (v < 0.4, x < 1e-3).  (2x + u^beta)^(v-1/2) turns within a
@@ -379,11 +464,16 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
                                                    const KintScalar* ks = nullptr) {
   const double beta_i = 16.0 * ix_rcp(2.0 * vi + 1.0);   // the reciprocal on the integer pipe
   const int rule_i = kint_rule(vi, xi, DX);
-  // one-slot rules: the g nodes' common factor beta s0^(v+1/2), as a log
-  const double gk_i = (!DX && (rule_i >> 8) >= 4)
-                          ? fma(vi + 0.5, (rule_i >> 8) == 4 ? LB_KQ_LOG8 : LB_KQ_LOG3, ix_log(beta_i)) : 0.0;
+  // values: the g nodes' common factor as a log, beta (s0^(v+1/2) beta for
+  // the one-slot rules), added to their logarithms
+  double gk_i = 0.0;
+  if (!DX) {
+    gk_i = ix_log(beta_i);
+    if ((rule_i >> 8) >= 4) gk_i = fma(vi + 0.5, (rule_i >> 8) == 4 ? LB_KQ_LOG8 : LB_KQ_LOG3, gk_i);
+  }
   double m_i = 0.0, s0_i = 1.0, s1_i = 0.0;
-  uint64_t q_i = 0;                                // Q58 sum of a one-slot rule
+  uint64_t q_i = 0;                                // fixed-point sum (values, all rules but the split one)
+  int qb_i = 0;                                    // its fraction bits
   for (int e = 0; e < npairs; ++e) {
     const double v = __shfl_sync(0xffffffffu, vi, e);
     const double x = __shfl_sync(0xffffffffu, xi, e);
@@ -391,12 +481,22 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     const int ng = rule & 0xff, hr = rule >> 8;
     const double beta = __shfl_sync(0xffffffffu, beta_i, e);
     double mm;
-    if (!DX && hr >= 4) {
+    if (!DX && ng != 0) {
       const double gk = __shfl_sync(0xffffffffu, gk_i, e);
-      const uint64_t q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
+      uint64_t q;
+      int qb = 56;
+      if (hr >= 4) {
+        q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
+        qb = 58;
+      } else if (ng == 24) {
+        q = kint_sumq_g24h40(v, x, beta, gk, lane, mm, ks);
+      } else {
+        q = kint_sumq_fixed(v, x, beta, gk, ng, hr, lane, mm, ks);
+      }
       if (lane == e) {
         m_i = mm;
         q_i = q;
+        qb_i = qb;
       }
       continue;
     }
@@ -413,7 +513,7 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     }
   }
   if (DX) return -(vi / xi + 1.0) + (2.0 * vi - 1.0) * (s1_i / s0_i);
-  if ((rule_i >> 8) >= 4) s0_i = __ull2double_rn(q_i) * 0x1p-58;   // exact scaling by a power of two
+  if (qb_i) s0_i = __ull2double_rn(q_i) * (qb_i == 58 ? 0x1p-58 : 0x1p-56);   // exact scalings
   const double pre = ks ? ks->pre - fma(vi, ix_log(2.0 * xi), xi) : kint_prefactor(vi, xi);
   return pre + m_i + ix_log(s0_i);
 }
