@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("kind", ["i", "k"])
 def test_forced_equals_dispatch_inside(cuda, kind):
     """U_K and the K integral are per pair: bit for bit.  mu_20 and the
-    series sum the warp's largest term count: within 1e-15."""
+    series sum the warp's largest term count, so the two agree to rounding
+    (within the 4e-15 gate, in the error metric's units)."""
     v, x = W.robust_pairs(200000, seed=31, vmax=2e3, xmin=1e-4, xmax=2e3)
     vt, xt = torch.tensor(v, device=cuda), torch.tensor(x, device=cuda)
     reg = lb.classify(kind, vt, xt).cpu().numpy()
@@ -32,8 +33,10 @@ def test_forced_equals_dispatch_inside(cuda, kind):
         if name.startswith("u") or (kind == "k" and name == "fallback"):
             np.testing.assert_array_equal(got, full[sel])
         else:
-            e = np.abs(got - full[sel]) / np.maximum(np.abs(full[sel]), 1.0)
-            assert e.max() < 1e-15, (name, e.max())
+            # two valid evaluations, each within the gate of the oracle: the
+            # error metric's units (scale max(|f|, c), c = max(1, |x df/dx|, |v df/dv|))
+            e = oracle.rel_err(got, full[sel], oracle.error_scale(kind, v[sel], x[sel]))
+            assert e.max() < 4e-15, (name, e.max())
         checked += int(sel.sum())
     assert checked > 100000
 
