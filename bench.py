@@ -278,11 +278,15 @@ def main():
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
+        esampler = ClockSampler(local_rank)
+        esampler.start()
+        time.sleep(0.3)
         t0h = time.perf_counter()
         for _ in range(args.steps):
             step_host()
         torch.cuda.synchronize()
         ems = (time.perf_counter() - t0h) * 1e3
+        eclocks = esampler.stop()
         if pg:
             t = torch.tensor([ems], dtype=torch.float64, device=dev)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
@@ -291,7 +295,7 @@ def main():
                "h2d_bytes_per_step": 2 * (nv * 8 + n1 * 8 * nv + 2 * n_all * 8),
                "d2h_bytes_per_step": 4 * n_all * 8,
                "api": "logbessel_host (C ABI, pinned host buffers, synchronous per call)",
-               "pinned_copy_gbs": link,
+               "pinned_copy_gbs": link, "clocks": eclocks,
                "copy_ms_per_step_at_that_rate": 1e3 * (2 * (nv * 8 + n1 * 8 * nv + 2 * n_all * 8) / link["h2d_gbs"]
                                                        + 4 * n_all * 8 / link["d2h_gbs"]) / 1e9}
         del hx, hv, ho
