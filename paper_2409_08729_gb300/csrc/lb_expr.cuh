@@ -285,13 +285,21 @@ __device__ __forceinline__ double u_expr(double v, double x) {
 // division; B stays below 1e250 for n <= 80 and v <= 16.  All 32 lanes of the
 // warp must call it together.
 // ---------------------------------------------------------------------------
-// 0, 1, ..., 90 as doubles: the series loop reads k from here instead of
-// stepping a double counter (one FP64 operation per term less).
+// k and k^2 for k = 0, 1, ..., 90 as doubles (exact): the series loop reads
+// them from constant memory (k is warp-uniform) and forms d_k = k (k + v) as
+// one FMA, k v + k^2, instead of an addition and a multiplication.
 static __constant__ double kSeriesK[91] = {
-    0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22,
-    23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45,
-    46, 47, 48, 49, 50, 51, 52, 53, 54, 55, 56, 57, 58, 59, 60, 61, 62, 63, 64, 65, 66, 67, 68,
-    69, 70, 71, 72, 73, 74, 75, 76, 77, 78, 79, 80, 81, 82, 83, 84, 85, 86, 87, 88, 89, 90};
+    0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
+    26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 46, 47, 48, 49,
+    50, 51, 52, 53, 54, 55, 56, 57, 58, 59, 60, 61, 62, 63, 64, 65, 66, 67, 68, 69, 70, 71, 72, 73,
+    74, 75, 76, 77, 78, 79, 80, 81, 82, 83, 84, 85, 86, 87, 88, 89, 90};
+static __constant__ double kSeriesK2[91] = {
+    0, 1, 4, 9, 16, 25, 36, 49, 64, 81, 100, 121, 144, 169, 196, 225, 256, 289, 324, 361, 400, 441,
+    484, 529, 576, 625, 676, 729, 784, 841, 900, 961, 1024, 1089, 1156, 1225, 1296, 1369, 1444,
+    1521, 1600, 1681, 1764, 1849, 1936, 2025, 2116, 2209, 2304, 2401, 2500, 2601, 2704, 2809, 2916,
+    3025, 3136, 3249, 3364, 3481, 3600, 3721, 3844, 3969, 4096, 4225, 4356, 4489, 4624, 4761, 4900,
+    5041, 5184, 5329, 5476, 5625, 5776, 5929, 6084, 6241, 6400, 6561, 6724, 6889, 7056, 7225, 7396,
+    7569, 7744, 7921, 8100};
 
 __device__ __forceinline__ double series_log_i(double v, double x) {
   int n = 1;
@@ -313,8 +321,7 @@ __device__ __forceinline__ double series_log_i(double v, double x) {
   double A = 1.0, B = 1.0;
 #pragma unroll 1
   for (int k = n; k >= 1; --k) {
-    const double kd = kSeriesK[k];  // k as a double from constant memory (k is warp-uniform)
-    const double d = kd * (kd + v);
+    const double d = fma(kSeriesK[k], v, kSeriesK2[k]);   // k (k + v), exact up to one rounding
     A = fma(d, B, y * A);
     B *= d;
   }

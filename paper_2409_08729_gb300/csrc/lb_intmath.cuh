@@ -267,12 +267,13 @@ LB_IX_FN double ix_log(double z) {
 
 // Shared reduction of ix_rcp and ix_rsqrt: z = 2^e m, m in [1, 2),
 // j = the top 9 fraction bits, r = m C_j / 2^13 - 1 (exact, |r| < 2^-9.8)
-// returned as 2^65 r (the low 64 bits of M C_j, as in ix_log).
-LB_IX_FN int64_t ix_reduce_cj(uint64_t b, int& e, int& j) {
+// returned as 2^65 r (the low 64 bits of M C_j, as in ix_log), and C_j.
+LB_IX_FN int64_t ix_reduce_cj(uint64_t b, int& e, int& j, uint64_t& cj) {
   e = (int)(b >> 52) - 1023;
   const uint64_t F = b & 0x000fffffffffffffull;
   j = (int)(F >> 43);
-  return (int64_t)((F | 0x0010000000000000ull) * (uint64_t)LB_IX_LOAD(lb_ix_log_c + j));
+  cj = (uint64_t)LB_IX_LOAD(lb_ix_log_c + j);
+  return (int64_t)((F | 0x0010000000000000ull) * cj);
 }
 
 // Double from W in [2^61, 2^63) (value W 2^-62, rounded to 53 bits) times 2^-h.
@@ -291,7 +292,8 @@ LB_IX_FN double ix_rcp(double z) {
   const uint32_t hi = (uint32_t)(b >> 32);
   if (hi < 0x00100000u || hi >= 0x7fd00000u) return 1.0 / z;
   int e, j;
-  const int64_t r = ix_reduce_cj(b, e, j);                  // Q65
+  uint64_t cj;
+  const int64_t r = ix_reduce_cj(b, e, j, cj);              // Q65
   const int32_t r32 = (int32_t)(r >> 32);                   // Q33
   int32_t a = (1 << 30) - (ix_mulhi32(1 << 30, r32) >> 1);  // Q30: 1 - r
   a = (1 << 30) - (ix_mulhi32(a, r32) >> 1);
@@ -300,7 +302,7 @@ LB_IX_FN double ix_rcp(double z) {
   p = (1ll << 62) - (ix_mulhi(r, p) >> 1);
   p = (1ll << 62) - (ix_mulhi(r, p) >> 1);                  // 1/(1 + r), Q62
   // (C_j / 2^13) p in Q62: (2 p) (C_j 2^50) / 2^64
-  const uint64_t W = ix_umulhi((uint64_t)p << 1, (uint64_t)LB_IX_LOAD(lb_ix_log_c + j) << 50);
+  const uint64_t W = ix_umulhi((uint64_t)p << 1, cj << 50);
   return ix_pack(W, e);
 }
 
@@ -313,7 +315,8 @@ LB_IX_FN double ix_rsqrt(double z) {
   const uint32_t hi = (uint32_t)(b >> 32);
   if (hi < 0x00100000u || hi >= 0x7ff00000u) return 1.0 / sqrt(z);
   int e, j;
-  const int64_t r = ix_reduce_cj(b, e, j);                  // Q65
+  uint64_t cj;
+  const int64_t r = ix_reduce_cj(b, e, j, cj);              // Q65
   const int32_t r32 = (int32_t)(r >> 32);                   // Q33
   int32_t a = LB_IX_R5 - (ix_mulhi32(LB_IX_R6, r32) >> 1);  // Q30
   a = LB_IX_R4 - (ix_mulhi32(a, r32) >> 1);

@@ -162,9 +162,9 @@ def series_terms(v, x):
 
 
 def series_slots(v, x):
-    # per term: k + v, d = k (k + v), y A, fma, B d; plus A/B, log, lgamma, log(x/2), fma
+    # per term: d = k v + k^2 (fma), y A, fma, B d; plus A/B, log, lgamma, log(x/2), fma
     n = series_terms(v, x)
-    return n * 5 + SLOT_IX_RCP + 1 + SLOT_IX_LOG + SLOT_LGAMMA + SLOT_IX_LOG + 3
+    return n * 4 + SLOT_IX_RCP + 1 + SLOT_IX_LOG + SLOT_LGAMMA + SLOT_IX_LOG + 3
 
 
 def mu_slots_scalar(v, x, K=20):
