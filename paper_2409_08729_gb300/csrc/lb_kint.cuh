@@ -71,6 +71,17 @@ __device__ __forceinline__ int kint_rule(double v, double x, bool dx) {
   return ng | (hr << 8);
 }
 
+// Code path of a pair's rule, for sorting pairs by rule: 0 the split rule,
+// 1 and 2 the one-slot rules, 3 the packed rule, 4 and 5 the fixed rules
+// with 32 and 64 g nodes.
+__device__ __forceinline__ int kint_class(double v, double x, bool dx) {
+  const int rule = kint_rule(v, x, dx);
+  const int ng = rule & 0xff, hr = rule >> 8;
+  if (ng == 0) return 0;
+  if (hr >= 4) return hr - 3;
+  return ng == 24 ? 3 : (ng == 32 ? 4 : 5);
+}
+
 // One order for every pair of a call (v_stride 0): the g-node positions
 // u_j^beta of the three u rules and the order's part of the prefactor are
 // the same for every pair, so a block computes them once (with the same
@@ -474,42 +485,54 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
   double m_i = 0.0, s0_i = 1.0, s1_i = 0.0;
   uint64_t q_i = 0;                                // fixed-point sum (values, all rules but the split one)
   int qb_i = 0;                                    // its fraction bits
-  for (int e = 0; e < npairs; ++e) {
-    const double v = __shfl_sync(0xffffffffu, vi, e);
-    const double x = __shfl_sync(0xffffffffu, xi, e);
-    const int rule = __shfl_sync(0xffffffffu, rule_i, e);
+  // The pairs are taken rule by rule (lanes with the same rule found by a
+  // ballot), so each rule's code runs for all its pairs of the batch before
+  // the next rule's: in a batch that mixes rules, switching code paths at
+  // every pair thrashed the instruction cache.  The order of the pairs does
+  // not change any result.
+  unsigned rem = npairs >= 32 ? 0xffffffffu : ((1u << npairs) - 1u);
+  while (rem) {
+    const int rule = __shfl_sync(0xffffffffu, rule_i, __ffs(rem) - 1);
+    unsigned grp = __ballot_sync(0xffffffffu, rule_i == rule) & rem;
+    rem &= ~grp;
     const int ng = rule & 0xff, hr = rule >> 8;
-    const double beta = __shfl_sync(0xffffffffu, beta_i, e);
-    double mm;
     if (!DX && ng != 0) {
-      const double gk = __shfl_sync(0xffffffffu, gk_i, e);
-      uint64_t q;
-      int qb = 56;
-      if (hr >= 4) {
-        q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
-        qb = 58;
-      } else if (ng == 24) {
-        q = kint_sumq_g24h40(v, x, beta, gk, lane, mm, ks);
-      } else {
-        q = kint_sumq_fixed(v, x, beta, gk, ng, hr, lane, mm, ks);
-      }
-      if (lane == e) {
-        m_i = mm;
-        q_i = q;
-        qb_i = qb;
+      const int qb = hr >= 4 ? 58 : 56;
+      for (; grp; grp &= grp - 1) {
+        const int e = __ffs(grp) - 1;
+        const double v = __shfl_sync(0xffffffffu, vi, e);
+        const double x = __shfl_sync(0xffffffffu, xi, e);
+        const double beta = __shfl_sync(0xffffffffu, beta_i, e);
+        const double gk = __shfl_sync(0xffffffffu, gk_i, e);
+        double mm;
+        uint64_t q;
+        if (hr >= 4) q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
+        else if (ng == 24) q = kint_sumq_g24h40(v, x, beta, gk, lane, mm, ks);
+        else q = kint_sumq_fixed(v, x, beta, gk, ng, hr, lane, mm, ks);
+        if (lane == e) {
+          m_i = mm;
+          q_i = q;
+          qb_i = qb;
+        }
       }
       continue;
     }
-    double s0, s1 = 0.0;
-    if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
-    else if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1, ks);
-    else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1, ks);
-    s0 = warp_sum(s0);
-    if (DX) s1 = warp_sum(s1);
-    if (lane == e) {
-      m_i = mm;
-      s0_i = s0;
-      s1_i = s1;
+    for (; grp; grp &= grp - 1) {
+      const int e = __ffs(grp) - 1;
+      const double v = __shfl_sync(0xffffffffu, vi, e);
+      const double x = __shfl_sync(0xffffffffu, xi, e);
+      const double beta = __shfl_sync(0xffffffffu, beta_i, e);
+      double mm, s0, s1 = 0.0;
+      if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
+      else if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1, ks);
+      else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1, ks);
+      s0 = warp_sum(s0);
+      if (DX) s1 = warp_sum(s1);
+      if (lane == e) {
+        m_i = mm;
+        s0_i = s0;
+        s1_i = s1;
+      }
     }
   }
   if (DX) return -(vi / xi + 1.0) + (2.0 * vi - 1.0) * (s1_i / s0_i);

@@ -108,15 +108,52 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
   }
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t b = warp * 32; b < (int64_t)cnt; b += nwarps * 32) {
-    const int64_t q = b + lane;
-    const bool valid = q < (int64_t)cnt;
-    const int64_t idx = (int64_t)queue[valid ? q : b];
-    const T vi = fabs(v[idx * v_stride]);
-    const T xi = x[idx];
-    const int m = (int)min((int64_t)32, (int64_t)cnt - b);
-    const T val = kint_warp_batch<DX, T>(vi, xi, m, lane, GAUSS, ks, ks32);
-    if (valid) out[idx] = val;
+  // When the queue gives every warp at least one pass of 256 pairs (FP64
+  // Gauss rules), a warp takes 256 at a time and sorts them by quadrature
+  // rule (a counting sort by ballots, into its slice of shared memory)
+  // before evaluating them 32 at a time: a batch then holds one or two
+  // rules, where an unsorted one switched between up to six code paths and
+  // thrashed the instruction cache.  A pair's result does not depend on its
+  // batch.  Otherwise a warp takes the queue 32 pairs at a time, in order.
+  __shared__ uint32_t sidx[LB_THREADS / 32][256];
+  uint32_t* my = sidx[threadIdx.x >> 5];
+  const bool sorted = GAUSS && sizeof(T) == 8 && (int64_t)cnt >= nwarps * 256;
+  const int P = sorted ? 256 : 32;
+  for (int64_t b = warp * P; b < (int64_t)cnt; b += nwarps * P) {
+    const int m = (int)min((int64_t)P, (int64_t)cnt - b);
+    if (sorted) {
+      uint32_t id[8];
+      int cls[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int t = 32 * j + lane;
+        id[j] = t < m ? queue[b + t] : 0u;
+        cls[j] = t < m ? kint_class((double)fabs(v[(int64_t)id[j] * v_stride]), (double)x[id[j]], DX) : 6;
+      }
+      int run = 0;
+      const unsigned lt = (1u << lane) - 1u;
+#pragma unroll 1
+      for (int c = 0; c < 6; ++c) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const unsigned mk = __ballot_sync(0xffffffffu, cls[j] == c);
+          if (cls[j] == c) my[run + __popc(mk & lt)] = id[j];
+          run += __popc(mk);
+        }
+      }
+      __syncwarp();
+    }
+    for (int k = 0; 32 * k < m; ++k) {
+      const int t = 32 * k + lane;
+      const bool valid = t < m;
+      const int src = valid ? t : 32 * k;
+      const int64_t idx = (int64_t)(sorted ? my[src] : queue[b + src]);
+      const T vi = fabs(v[idx * v_stride]);
+      const T xi = x[idx];
+      const T val = kint_warp_batch<DX, T>(vi, xi, min(32, m - 32 * k), lane, GAUSS, ks, ks32);
+      if (valid) out[idx] = val;
+    }
+    if (sorted) __syncwarp();
   }
 }
 
