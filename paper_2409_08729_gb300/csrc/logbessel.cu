@@ -108,52 +108,58 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
   }
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // When the queue gives every warp at least one pass of 256 pairs (FP64
-  // Gauss rules), a warp takes 256 at a time and sorts them by quadrature
-  // rule (a counting sort by ballots, into its slice of shared memory)
-  // before evaluating them 32 at a time: a batch then holds one or two
-  // rules, where an unsorted one switched between up to six code paths and
-  // thrashed the instruction cache.  A pair's result does not depend on its
-  // batch.  Otherwise a warp takes the queue 32 pairs at a time, in order.
-  __shared__ uint32_t sidx[LB_THREADS / 32][256];
-  uint32_t* my = sidx[threadIdx.x >> 5];
-  const bool sorted = GAUSS && sizeof(T) == 8 && (int64_t)cnt >= nwarps * 256;
-  const int P = sorted ? 256 : 32;
-  for (int64_t b = warp * P; b < (int64_t)cnt; b += nwarps * P) {
-    const int m = (int)min((int64_t)P, (int64_t)cnt - b);
-    if (sorted) {
-      uint32_t id[8];
-      int cls[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int t = 32 * j + lane;
-        id[j] = t < m ? queue[b + t] : 0u;
-        cls[j] = t < m ? kint_class((double)fabs(v[(int64_t)id[j] * v_stride]), (double)x[id[j]], DX) : 6;
-      }
-      int run = 0;
-      const unsigned lt = (1u << lane) - 1u;
-#pragma unroll 1
-      for (int c = 0; c < 6; ++c) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const unsigned mk = __ballot_sync(0xffffffffu, cls[j] == c);
-          if (cls[j] == c) my[run + __popc(mk & lt)] = id[j];
-          run += __popc(mk);
+  // When the queue gives every warp at least one window of 256 pairs (FP64
+  // Gauss rules), the queue is processed in six phases, one quadrature rule
+  // class each (split, 64 and 32 g nodes, packed, the two one-slot rules):
+  // in phase c a warp scans its windows for the pairs of class c, collects
+  // them in a ring in its slice of shared memory and evaluates them 32 at a
+  // time.  So the warps of an SM run one rule's code at a time; with the
+  // classes mixed, every warp switching between up to six code paths, the
+  // instruction cache thrashed (the K call of the robustness sweep took 2.2x
+  // the time of its rule classes evaluated one after another).  Each phase
+  // re-reads the queue and the pairs' (v, x), a few bytes per pair.  A
+  // pair's result does not depend on its batch.  Shorter queues are taken
+  // in order, 32 pairs at a time.
+  __shared__ uint32_t ring[LB_THREADS / 32][512];
+  uint32_t* my = ring[threadIdx.x >> 5];
+  const bool phased = GAUSS && sizeof(T) == 8 && (int64_t)cnt >= nwarps * 256;
+  const int P = phased ? 256 : 32;
+  const int nphase = phased ? 6 : 1;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned head = 0, nb = 0;                       // ring: first entry, entries held (warp-uniform)
+  for (int ph = 0; ph < nphase; ++ph) {
+    const int c = phased ? (ph == 0 ? 0 : 6 - ph) : -1;   // costliest class first; -1: every pair
+    for (int64_t b = warp * P;; b += nwarps * P) {
+      const bool last = b >= (int64_t)cnt;
+      if (!last) {
+        const int m = (int)min((int64_t)P, (int64_t)cnt - b);
+        for (int j = 0; 32 * j < m; ++j) {
+          const int t = 32 * j + lane;
+          uint32_t id = 0;
+          bool take = false;
+          if (t < m) {
+            id = queue[b + t];
+            take = c < 0 || kint_class((double)fabs(v[(int64_t)id * v_stride]), (double)x[id], DX) == c;
+          }
+          const unsigned mk = __ballot_sync(0xffffffffu, take);
+          if (take) my[(head + nb + __popc(mk & lt)) & 511u] = id;   // nb <= 31 + 256 < 512: no overrun
+          nb += __popc(mk);
         }
+        __syncwarp();
+      }
+      while (nb >= 32 || (last && nb > 0)) {
+        const int k = nb < 32 ? (int)nb : 32;
+        const int64_t idx = (int64_t)my[(head + (lane < k ? lane : 0)) & 511u];
+        const T vi = fabs(v[idx * v_stride]);
+        const T xi = x[idx];
+        const T val = kint_warp_batch<DX, T>(vi, xi, k, lane, GAUSS, ks, ks32);
+        if (lane < k) out[idx] = val;
+        head += k;
+        nb -= k;
       }
       __syncwarp();
+      if (last) break;
     }
-    for (int k = 0; 32 * k < m; ++k) {
-      const int t = 32 * k + lane;
-      const bool valid = t < m;
-      const int src = valid ? t : 32 * k;
-      const int64_t idx = (int64_t)(sorted ? my[src] : queue[b + src]);
-      const T vi = fabs(v[idx * v_stride]);
-      const T xi = x[idx];
-      const T val = kint_warp_batch<DX, T>(vi, xi, min(32, m - 32 * k), lane, GAUSS, ks, ks32);
-      if (valid) out[idx] = val;
-    }
-    if (sorted) __syncwarp();
   }
 }
 
