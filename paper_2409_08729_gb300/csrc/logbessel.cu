@@ -108,27 +108,31 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
   }
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // When the queue gives every warp at least one window of 256 pairs (FP64
-  // Gauss rules), the queue is processed in six phases, one quadrature rule
-  // class each (split, 64 and 32 g nodes, packed, the two one-slot rules):
-  // in phase c a warp scans its windows for the pairs of class c, collects
-  // them in a ring in its slice of shared memory and evaluates them 32 at a
-  // time.  So the warps of an SM run one rule's code at a time; with the
-  // classes mixed, every warp switching between up to six code paths, the
+  // FP64 Gauss rules: the queue is processed in up to six phases, one
+  // quadrature rule class each (split, 64 and 32 g nodes, packed, the two
+  // one-slot rules): in phase c a warp scans its windows of the queue (256
+  // pairs when the queue gives every warp a full window, else 32) for the
+  // pairs of class c, collects them in a ring in its slice of shared memory
+  // and evaluates them 32 at a time; phase 0 also notes which classes the
+  // warp's windows hold, and the phases of absent classes are skipped.  So
+  // the warps of an SM run one rule's code at a time; with the classes
+  // mixed, every warp switching between up to six code paths, the
   // instruction cache thrashed (the K call of the robustness sweep took 2.2x
-  // the time of its rule classes evaluated one after another).  Each phase
+  // the time of its rule classes evaluated one after another).  A phase
   // re-reads the queue and the pairs' (v, x), a few bytes per pair.  A
-  // pair's result does not depend on its batch.  Shorter queues are taken
-  // in order, 32 pairs at a time.
+  // pair's result does not depend on its batch.  Other kernels take the
+  // queue in order, 32 pairs at a time.
   __shared__ uint32_t ring[LB_THREADS / 32][512];
   uint32_t* my = ring[threadIdx.x >> 5];
-  const bool phased = GAUSS && sizeof(T) == 8 && (int64_t)cnt >= nwarps * 256;
-  const int P = phased ? 256 : 32;
+  const bool phased = GAUSS && sizeof(T) == 8;
+  const int P = phased && (int64_t)cnt >= nwarps * 256 ? 256 : 32;
   const int nphase = phased ? 6 : 1;
   const unsigned lt = (1u << lane) - 1u;
   unsigned head = 0, nb = 0;                       // ring: first entry, entries held (warp-uniform)
+  unsigned seen = 0;                               // classes in this warp's windows (phase 0 finds them)
   for (int ph = 0; ph < nphase; ++ph) {
     const int c = phased ? (ph == 0 ? 0 : 6 - ph) : -1;   // costliest class first; -1: every pair
+    if (ph > 0 && !(seen & (1u << c))) continue;
     for (int64_t b = warp * P;; b += nwarps * P) {
       const bool last = b >= (int64_t)cnt;
       if (!last) {
@@ -136,11 +140,13 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
         for (int j = 0; 32 * j < m; ++j) {
           const int t = 32 * j + lane;
           uint32_t id = 0;
-          bool take = false;
+          int cl = -1;
           if (t < m) {
             id = queue[b + t];
-            take = c < 0 || kint_class((double)fabs(v[(int64_t)id * v_stride]), (double)x[id], DX) == c;
+            if (c >= 0) cl = kint_class((double)fabs(v[(int64_t)id * v_stride]), (double)x[id], DX);
           }
+          const bool take = t < m && cl == c;
+          if (ph == 0 && c >= 0) seen |= __reduce_or_sync(0xffffffffu, cl >= 0 ? 1u << cl : 0u);
           const unsigned mk = __ballot_sync(0xffffffffu, take);
           if (take) my[(head + nb + __popc(mk & lt)) & 511u] = id;   // nb <= 31 + 256 < 512: no overrun
           nb += __popc(mk);
