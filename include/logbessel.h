@@ -99,7 +99,8 @@ lb_status logbessel_k(lb_dtype dtype, const void* v, int64_t v_stride, const voi
 /*
  * Caller-supplied workspace.  The K entry points queue the pairs that take
  * the integral (the fallback region) in device scratch: 256 bytes for a
- * counter plus 4 bytes per pair of a pass.  logbessel_k and logbessel_k_dx
+ * counter and the mask of the quadrature rules queued, plus 4 bytes per pair
+ * of a pass.  logbessel_k and logbessel_k_dx
  * take it from the stream-ordered allocator; these variants take it from the
  * caller and allocate nothing.
  *
@@ -135,7 +136,7 @@ lb_status logbessel_k_dx_ws(lb_dtype dtype, const void* v, int64_t v_stride, con
  * launches nothing.  The first call on a device looks up the scratch
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture on the device.  Every call shares the one
- * array and clears its counter on the stream: calls whose work overlaps on
+ * array and clears its counter and mask on the stream: calls whose work overlaps on
  * the GPU (different streams, or concurrent host threads) race and must be
  * serialized by the caller.  Other arguments, results and errors as in
  * logbessel_k; LB_ENOTSUP for LB_F32.

@@ -76,7 +76,18 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
         if (tid == 0) S.qbase = atomicAdd(qcount, (unsigned int)c);
         __syncthreads();
         const unsigned int b = S.qbase;
-        for (int j = tid; j < c; j += LB_THREADS) queue[b + j] = (uint32_t)(t0 + S.lists[R_FALLBACK][j]);
+        unsigned cls = 0;                          // quadrature rule classes of the queued pairs
+        for (int j = tid; j < c; j += LB_THREADS) {
+          const int li = S.lists[R_FALLBACK][j];
+          queue[b + j] = (uint32_t)(t0 + li);
+          if constexpr (sizeof(T) == 8) {
+            if (mode == MODE_TIGHT) cls |= 1u << kint_class(fabs((double)S.sv[li]), (double)S.sx[li], DX);
+          }
+        }
+        if constexpr (sizeof(T) == 8) {
+          cls = __reduce_or_sync(0xffffffffu, cls);
+          if ((tid & 31) == 0 && cls) atomicOr(qcount + 1, cls);
+        }
       }
     }
     __syncthreads();
@@ -108,31 +119,31 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
   }
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // FP64 Gauss rules: the queue is processed in up to six phases, one
-  // quadrature rule class each (split, 64 and 32 g nodes, packed, the two
-  // one-slot rules): in phase c a warp scans its windows of the queue (256
-  // pairs when the queue gives every warp a full window, else 32) for the
-  // pairs of class c, collects them in a ring in its slice of shared memory
-  // and evaluates them 32 at a time; phase 0 also notes which classes the
-  // warp's windows hold, and the phases of absent classes are skipped.  So
-  // the warps of an SM run one rule's code at a time; with the classes
-  // mixed, every warp switching between up to six code paths, the
-  // instruction cache thrashed (the K call of the robustness sweep took 2.2x
-  // the time of its rule classes evaluated one after another).  A phase
-  // re-reads the queue and the pairs' (v, x), a few bytes per pair.  A
-  // pair's result does not depend on its batch.  Other kernels take the
-  // queue in order, 32 pairs at a time.
+  // FP64 Gauss rules with pairs of several quadrature rule classes queued
+  // (split, 64 and 32 g nodes, packed, the two one-slot rules; the tile
+  // kernel marks the classes it queues): the queue is processed in phases,
+  // one present class each, costliest first: in phase c a warp scans its
+  // windows of the queue (256 pairs when the queue gives every warp a full
+  // window, else 32) for the pairs of class c, collects them in a ring in
+  // its slice of shared memory and evaluates them 32 at a time.  So the
+  // warps of an SM run one rule's code at a time; with the classes mixed,
+  // every warp switching between up to six code paths, the instruction
+  // cache thrashed (the K call of the robustness sweep took 2.2x the time of
+  // its rule classes evaluated one after another).  A phase re-reads the
+  // queue and the pairs' (v, x), a few bytes per pair.  A pair's result
+  // does not depend on its batch.  A queue of one class, and the other
+  // kernels, take the queue in order, 32 pairs at a time.
   __shared__ uint32_t ring[LB_THREADS / 32][512];
   uint32_t* my = ring[threadIdx.x >> 5];
-  const bool phased = GAUSS && sizeof(T) == 8;
+  const unsigned present = (GAUSS && sizeof(T) == 8) ? qcount[1] : 0u;
+  const bool phased = __popc(present) > 1;
   const int P = phased && (int64_t)cnt >= nwarps * 256 ? 256 : 32;
   const int nphase = phased ? 6 : 1;
   const unsigned lt = (1u << lane) - 1u;
   unsigned head = 0, nb = 0;                       // ring: first entry, entries held (warp-uniform)
-  unsigned seen = 0;                               // classes in this warp's windows (phase 0 finds them)
   for (int ph = 0; ph < nphase; ++ph) {
     const int c = phased ? (ph == 0 ? 0 : 6 - ph) : -1;   // costliest class first; -1: every pair
-    if (ph > 0 && !(seen & (1u << c))) continue;
+    if (phased && !(present & (1u << c))) continue;
     for (int64_t b = warp * P;; b += nwarps * P) {
       const bool last = b >= (int64_t)cnt;
       if (!last) {
@@ -146,7 +157,6 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
             if (c >= 0) cl = kint_class((double)fabs(v[(int64_t)id * v_stride]), (double)x[id], DX);
           }
           const bool take = t < m && cl == c;
-          if (ph == 0 && c >= 0) seen |= __reduce_or_sync(0xffffffffu, cl >= 0 ? 1u << cl : 0u);
           const unsigned mk = __ballot_sync(0xffffffffu, take);
           if (take) my[(head + nb + __popc(mk & lt)) & 511u] = id;   // nb <= 31 + 256 < 512: no overrun
           nb += __popc(mk);
@@ -356,7 +366,8 @@ lb_status validate(lb_dtype dtype, const void* v, int64_t v_stride, const void* 
 const int64_t kChunk = (int64_t)1 << 26;
 
 // Enqueue the evaluation of n pairs.  The K fallback goes through a queue
-// of 32-bit pair offsets in scratch memory (qcount: one counter, queue:
+// of 32-bit pair offsets in scratch memory (qcount: the counter and the
+// mask of the quadrature rule classes queued, queue:
 // min(n, chunk) entries), processed chunk by chunk; `scratch` supplies it,
 // or, when NULL, it comes from the stream-ordered allocator.
 template <int KIND, bool DX, typename T>
@@ -387,7 +398,7 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
   lb_status status = LB_OK;
   for (int64_t c0 = 0; c0 < n && status == LB_OK; c0 += chunk) {
     const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
-    if (cudaMemsetAsync(qcount, 0, sizeof(unsigned int), st) != cudaSuccess) { status = check_launch("cudaMemsetAsync"); break; }
+    if (cudaMemsetAsync(qcount, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) { status = check_launch("cudaMemsetAsync"); break; }
     const T* vc = v + c0 * v_stride;
     const T* xc = x + c0;
     T* oc = out + c0;
