@@ -97,16 +97,19 @@ def kint_slots(v, x, scalar=False):
     computed once per block)."""
     ng, nh = kint_rule(v, x)
     split = ng > 64
-    # g node: beta*log u, exp, 2x + u^beta, log, fma, - u^beta; then L - m, exp, accumulate
-    # (split rule: 3 more for the offset form: s1 * r, the shift by C, the key add)
-    g_node = (5 if scalar else 6 + SLOT_IX_EXP) + SLOT_IX_EXP + SLOT_IX_LOG + np.where(split, 3, 0)
-    # h node: s + 2x, log, + y, fma; then L - m, exp, accumulate
-    h_node = 5 + SLOT_IX_EXP + SLOT_IX_LOG
-    # per pair (once per lane of its batch): beta (div), prefactor (lgamma,
-    # log, 3 ops), final log and beta g + h; the warp sum (5 adds, all lanes)
-    per_pair = SLOT_IX_RCP + 2 + (0 if scalar else SLOT_LGAMMA) + SLOT_IX_LOG + 3 + SLOT_IX_LOG + 2 + 1 + 5
-    # split rule: log s1, C, three panel widths (log + add each), the flat term (log, expm1, division)
-    per_pair = per_pair + np.where(split, 2 + 4 * SLOT_LOG + 3 + SLOT_EXP + SLOT_DIV + 4, 0)
+    # g node: beta*log u (+ log s0), exp, 2x + s, log, c + log beta, fma, - s;
+    # then L - m and the exp (the sum is formed in fixed point on the integer
+    # pipe; the split rule adds in FP64 and has 3 more for its offset form)
+    g_node = (5 if scalar else 6 + SLOT_IX_EXP) + SLOT_IX_EXP + SLOT_IX_LOG + np.where(split, 4, 0)
+    # h node: s + 2x, log, + y, fma; then L - m, exp (split rule: + 1 add)
+    h_node = 4 + SLOT_IX_EXP + SLOT_IX_LOG + np.where(split, 1, 0)
+    # per pair (once per lane of its batch): beta (reciprocal, 2 ops), lgamma,
+    # prefactor (log, 3 ops), log beta (+ fma), final log and add, the fixed
+    # sum to double (2 ops)
+    per_pair = SLOT_IX_RCP + 2 + (0 if scalar else SLOT_LGAMMA) + SLOT_IX_LOG + 3 + SLOT_IX_LOG + 2 + SLOT_IX_LOG + 1 + 2
+    # split rule: log s1, C, three panel widths (log + add each), the flat
+    # term (log, expm1, division), its FP64 warp sum (5 adds)
+    per_pair = per_pair + np.where(split, 2 + 4 * SLOT_LOG + 3 + SLOT_EXP + SLOT_DIV + 4 + 5, 0)
     return ng * g_node + nh * h_node + per_pair
 
 
