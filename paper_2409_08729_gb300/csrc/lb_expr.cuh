@@ -148,47 +148,24 @@ __device__ __forceinline__ int classify(double v, double x, int mode) {
 // found with a single-precision pass and made uniform across the warp, so
 // the double-precision Horner loop never diverges.  All 32 lanes of the
 // warp must call it together.
-// Single-precision estimates of the number of terms the mu_K expression and
-// the I power series sum for one pair (the expressions take the warp's
-// maximum; the tile kernel also sorts its lists by them).  mu_K: the first
-// k whose term ratio product falls below 1.4e-17 (2^-56), else K; unrolled,
-// so (2k-1)^2 and 1/k are constants.  Series: terms past the peak index
-// (-v + sqrt(x^2 + v^2))/2 until one falls below 1.4e-17 of the running sum.
-template <int K>
-__device__ __forceinline__ int mu_terms_est(float vf, float xf) {
-  int n = K;
-  const float muf = 4.0f * vf * vf, inv8xf = __fdividef(1.0f, 8.0f * xf);
-  float t = 1.0f;
-  bool found = false;
-#pragma unroll
-  for (int k = 1; k <= K; ++k) {
-    t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * (inv8xf * (1.0f / (float)k));
-    const bool hit = !found && fabsf(t) < 1.4e-17f;
-    n = hit ? k : n;
-    found = found || hit;
-  }
-  return n;
-}
-
-__device__ __forceinline__ int series_terms_est(float vf, float xf) {
-  int n = 1;
-  const float yf = 0.25f * xf * xf;
-  const float kpk = 0.5f * (sqrtf(fmaf(xf, xf, vf * vf)) - vf);
-  float term = 1.0f, T = 0.0f, kf = 0.0f;
-#pragma unroll 1
-  for (int k = 1; k <= 90; ++k) {
-    kf += 1.0f;
-    term *= __fdividef(yf, kf * (kf + vf));      // an estimate: the fast division suffices
-    T += term;
-    n = k;
-    if (kf > kpk && term <= 1.4e-17f * (1.0f + T)) break;
-  }
-  return n;
-}
-
 template <int KIND, int K>
 __device__ __forceinline__ double mu_expr(double v, double x) {
-  int n = __reduce_max_sync(0xffffffffu, mu_terms_est<K>((float)v, (float)x));
+  // single-precision estimate of the number of terms
+  int n = K;
+  {
+    // unrolled, so (2k-1)^2 and 1/k are constants: no division, no branch
+    const float muf = 4.0f * (float)v * (float)v, inv8xf = __fdividef(1.0f, 8.0f * (float)x);
+    float t = 1.0f;
+    bool found = false;
+#pragma unroll
+    for (int k = 1; k <= K; ++k) {
+      t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * (inv8xf * (1.0f / (float)k));
+      const bool hit = !found && fabsf(t) < 1.4e-17f;
+      n = hit ? k : n;
+      found = found || hit;
+    }
+  }
+  n = __reduce_max_sync(0xffffffffu, n);
   const double mu = 4.0 * v * v;
   const double rx = ix_rcp_call(8.0 * x);                             // 1/(8x) on the integer pipe
   const double inv8x = (KIND == KIND_I) ? -rx : rx;                   // the sign s folded in
@@ -325,7 +302,21 @@ static __constant__ double kSeriesK2[91] = {
     7569, 7744, 7921, 8100};
 
 __device__ __forceinline__ double series_log_i(double v, double x) {
-  const int n = __reduce_max_sync(0xffffffffu, series_terms_est((float)v, (float)x));
+  int n = 1;
+  {
+    const float yf = 0.25f * (float)x * (float)x, vf = (float)v;
+    const float kpk = 0.5f * (sqrtf(fmaf((float)x, (float)x, vf * vf)) - vf);
+    float term = 1.0f, T = 0.0f, kf = 0.0f;
+#pragma unroll 1
+    for (int k = 1; k <= 90; ++k) {
+      kf += 1.0f;
+      term *= __fdividef(yf, kf * (kf + vf));      // an estimate: the fast division suffices
+      T += term;
+      n = k;
+      if (kf > kpk && term <= 1.4e-17f * (1.0f + T)) break;
+    }
+  }
+  n = __reduce_max_sync(0xffffffffu, n);
   const double y = 0.25 * x * x;
   double A = 1.0, B = 1.0;
 #pragma unroll 1
@@ -399,7 +390,20 @@ __device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
 template <int KIND>
 __device__ __forceinline__ double mu_expr_so(const ScalarOrder& so, double x) {
   constexpr int K = 20;
-  const int n = __reduce_max_sync(0xffffffffu, mu_terms_est<K>((float)so.v, (float)x));
+  int n = K;
+  {
+    const float muf = 4.0f * (float)so.v * (float)so.v, inv8xf = __fdividef(1.0f, 8.0f * (float)x);
+    float t = 1.0f;
+    bool found = false;
+#pragma unroll
+    for (int k = 1; k <= K; ++k) {
+      t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * (inv8xf * (1.0f / (float)k));
+      const bool hit = !found && fabsf(t) < 1.4e-17f;
+      n = hit ? k : n;
+      found = found || hit;
+    }
+  }
+  n = __reduce_max_sync(0xffffffffu, n);
   const double w = ix_rcp_call(8.0 * x);
   double P = 0.0;
 #pragma unroll
@@ -435,7 +439,21 @@ __device__ __forceinline__ double u_expr_so(const ScalarOrder& so, double x) {
 
 __device__ __forceinline__ double series_so(const ScalarOrder& so, double x) {
   const double v = so.v;
-  const int n = __reduce_max_sync(0xffffffffu, series_terms_est((float)v, (float)x));
+  int n = 1;
+  {
+    const float yf = 0.25f * (float)x * (float)x, vf = (float)v;
+    const float kpk = 0.5f * (sqrtf(fmaf((float)x, (float)x, vf * vf)) - vf);
+    float term = 1.0f, T = 0.0f, kf = 0.0f;
+#pragma unroll 1
+    for (int k = 1; k <= 90; ++k) {
+      kf += 1.0f;
+      term *= __fdividef(yf, kf * (kf + vf));
+      T += term;
+      n = k;
+      if (kf > kpk && term <= 1.4e-17f * (1.0f + T)) break;
+    }
+  }
+  n = __reduce_max_sync(0xffffffffu, n);
   const double y = 0.25 * x * x;
   double P = 1.0;
 #pragma unroll 1

@@ -86,68 +86,6 @@ __device__ __forceinline__ T tile_expr(int r, T v, T x) {
   }
 }
 
-// Stable counting sort of region R's list by the pair's estimated number of
-// terms (mu_20: the count; series: the count / 4), so that the 32-pair
-// chunks a warp takes hold pairs of nearly the same count: a warp sums its
-// slowest lane's count, and on the paper-shaped sweep unsorted chunks summed
-// 40 % (mu_20) and 53 % (series) more terms than their pairs need.  The
-// order is (key, list position), the same on every run.  Scratch: the lists
-// of R_SPECIAL (never filled) and R_MU3 (filled only in MODE_PAPER_CPU, which
-// does not sort).  All threads of the block call it.
-template <typename T>
-__device__ __noinline__ void tile_sort_by_terms(TileShared<T>& S, int R, bool series) {
-  const int c = S.counts[R];
-  if (c <= 32) return;                             // a single chunk either way
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned int lt = (1u << lane) - 1u;
-  uint16_t* tmp = S.lists[R_SPECIAL];
-  uint16_t (*cnt)[LB_THREADS / 32][32] = reinterpret_cast<uint16_t (*)[LB_THREADS / 32][32]>(S.lists[R_MU3]);
-  for (int j = tid; j < LB_ITEMS * (LB_THREADS / 32) * 32; j += LB_THREADS) S.lists[R_MU3][j] = 0;
-  __syncthreads();
-  int key[LB_ITEMS], rk[LB_ITEMS];
-  uint16_t li[LB_ITEMS];
-#pragma unroll
-  for (int it = 0; it < LB_ITEMS; ++it) {
-    const int j = it * LB_THREADS + tid;
-    key[it] = -1;
-    li[it] = 0;
-    if (j < c) {
-      li[it] = S.lists[R][j];
-      const float vf = (float)S.sv[li[it]], xf = (float)S.sx[li[it]];
-      key[it] = series ? (series_terms_est(vf, xf) >> 2) : mu_terms_est<20>(vf, xf);
-    }
-    const unsigned int m = __match_any_sync(0xffffffffu, key[it]);
-    rk[it] = __popc(m & lt);
-    if (key[it] >= 0 && lane == __ffs(m) - 1) cnt[it][warp][key[it]] = (uint16_t)__popc(m);
-  }
-  __syncthreads();
-  if (tid < 32) {                                  // lane k: key k's offsets in (item round, warp) order
-    int acc = 0;
-    for (int it = 0; it < LB_ITEMS; ++it)
-      for (int w = 0; w < LB_THREADS / 32; ++w) {
-        const int n = cnt[it][w][tid];
-        cnt[it][w][tid] = (uint16_t)acc;
-        acc += n;
-      }
-    int base = acc;                                // exclusive scan of the key totals
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, base, o);
-      if (tid >= o) base += u;
-    }
-    base -= acc;
-    for (int it = 0; it < LB_ITEMS; ++it)
-      for (int w = 0; w < LB_THREADS / 32; ++w) cnt[it][w][tid] = (uint16_t)(cnt[it][w][tid] + base);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int it = 0; it < LB_ITEMS; ++it)
-    if (key[it] >= 0) tmp[cnt[it][warp][key[it]] + rk[it]] = li[it];
-  __syncthreads();
-  for (int j = tid; j < c; j += LB_THREADS) S.lists[R][j] = tmp[j];
-  __syncthreads();
-}
-
 // Load, edge-handle, classify and bin pairs [t0, min(t0 + LB_TILE, n)).
 // All threads of the block call it; it ends with a barrier.  Binning is by
 // warp ballots and a per-region prefix over (item round, warp), so every
@@ -208,10 +146,6 @@ __device__ __forceinline__ void tile_bin(TileShared<T>& S, const T* __restrict__
     if (reg[it] >= 0) S.lists[reg[it]][S.wcount[it][warp][reg[it]] + rank[it]] = (uint16_t)(it * LB_THREADS + tid);
   if (tid < 8) S.next_chunk[tid] = 0;
   __syncthreads();
-  if (mode != MODE_PAPER_CPU) {
-    tile_sort_by_terms<T>(S, R_MU20, false);
-    if (KIND == KIND_I) tile_sort_by_terms<T>(S, R_FALLBACK, true);
-  }
 }
 
 // The FP64 expressions with the order's constants of a ScalarOrder block.
