@@ -734,8 +734,24 @@ lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride
   }
   cudaStream_t* st = P.st;
   void* ws = P.dbuf + slot * nbuf;
-  for (int64_t c0 = 0, i = 0; s == LB_OK && c0 < n; c0 += chunk, ++i) {
-    const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
+  // Pieces: chunk/8, chunk/4, chunk/2, then whole chunks, and at the end
+  // halves of what remains down to chunk/8, so that the first copy-in and
+  // the last copy-out, which nothing overlaps, are short; piece edges stay
+  // on tile boundaries (chunk a multiple of 8 tiles), so the results equal
+  // those of one pass.
+  const bool ramp = chunk % (8 * LB_TILE) == 0;
+  int64_t cn = 0;
+  for (int64_t c0 = 0, i = 0; s == LB_OK && c0 < n; c0 += cn, ++i) {
+    const int64_t r = n - c0;
+    cn = chunk;
+    if (ramp) {
+      if (i < 3) cn = chunk >> (3 - i);
+      if (r <= chunk) {
+        const int64_t half = (r / 2) / LB_TILE * LB_TILE;
+        cn = half > chunk / 8 ? half : chunk / 8;
+      }
+    }
+    if (cn > r) cn = r;
     const int b = (int)(i % nbuf);
     char* dv = P.dbuf + b * slot;
     char* dx = dv + ((vbytes + 255) & ~(size_t)255);
