@@ -178,7 +178,9 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
  * copies synchronously).  The pairs are processed in chunks of `chunk`
  * (0 = 8M pairs; at most 2^26) through four device chunk slots and three
  * internal streams, so the copy-in of one chunk, the evaluation of the
- * previous one and the copy-out of the one before overlap.  The call
+ * previous one and the copy-out of the one before overlap; when chunk is a
+ * multiple of 8192 the first and last pieces are smaller (down to chunk/8)
+ * to shorten the unoverlapped copies, with results equal to one pass.  The call
  * returns when every result is in `out` (it synchronizes).  The streams,
  * events and one device buffer (four chunk slots of v, x and out, plus the
  * K fallback queue: about 4 * 24 * chunk + 4 * chunk bytes in FP64) belong to the
