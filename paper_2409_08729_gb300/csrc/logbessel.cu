@@ -46,16 +46,6 @@ namespace {
 #define LB_KINT_CTAS_PER_SM 4
 #endif
 
-// Quadrature rule class of a K-integral pair (|v| given), for the phases
-// of lb_kint_kernel: the FP64 classes of kint_class; in FP32, 0 for the
-// general rule and 1 for the packed 24 + 40 node rule (1.2 < v <= 5), the
-// two code paths of kint_gauss32.
-template <typename T, bool DX>
-__device__ __forceinline__ int kint_class_t(T v, T x) {
-  if constexpr (sizeof(T) == 8) return kint_class(v, x, DX);
-  else return (v > 1.2f && v <= 5.0f) ? 1 : 0;
-}
-
 // Tile kernel: classify, bin per region in shared memory, evaluate the
 // per-thread expressions (lb_tile.cuh); K fallback pairs go to a global queue
 // for lb_kint_kernel.  T = double (FP64) or float (FP32-mixed).
@@ -90,10 +80,14 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
         for (int j = tid; j < c; j += LB_THREADS) {
           const int li = S.lists[R_FALLBACK][j];
           queue[b + j] = (uint32_t)(t0 + li);
-          if (mode == MODE_TIGHT) cls |= 1u << kint_class_t<T, DX>(S.sv[li], S.sx[li]);
+          if constexpr (sizeof(T) == 8) {
+            if (mode == MODE_TIGHT) cls |= 1u << kint_class(fabs((double)S.sv[li]), (double)S.sx[li], DX);
+          }
         }
-        cls = __reduce_or_sync(0xffffffffu, cls);
-        if ((tid & 31) == 0 && cls) atomicOr(qcount + 1, cls);
+        if constexpr (sizeof(T) == 8) {
+          cls = __reduce_or_sync(0xffffffffu, cls);
+          if ((tid & 31) == 0 && cls) atomicOr(qcount + 1, cls);
+        }
       }
     }
     __syncthreads();
@@ -125,10 +119,9 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
   }
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // Gauss rules with pairs of several quadrature rule classes queued (FP64:
-  // split, 64 and 32 g nodes, packed, the two one-slot rules; FP32: general
-  // and packed; the tile kernel marks the classes it queues): the queue is
-  // processed in phases,
+  // FP64 Gauss rules with pairs of several quadrature rule classes queued
+  // (split, 64 and 32 g nodes, packed, the two one-slot rules; the tile
+  // kernel marks the classes it queues): the queue is processed in phases,
   // one present class each, costliest first: in phase c a warp scans its
   // windows of the queue (256 pairs when the queue gives every warp a full
   // window, else 32) for the pairs of class c, collects them in a ring in
@@ -142,7 +135,7 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
   // kernels, take the queue in order, 32 pairs at a time.
   __shared__ uint32_t ring[LB_THREADS / 32][512];
   uint32_t* my = ring[threadIdx.x >> 5];
-  const unsigned present = GAUSS ? qcount[1] : 0u;
+  const unsigned present = (GAUSS && sizeof(T) == 8) ? qcount[1] : 0u;
   const bool phased = __popc(present) > 1;
   const int P = phased && (int64_t)cnt >= nwarps * 256 ? 256 : 32;
   const int nphase = phased ? 6 : 1;
@@ -161,7 +154,7 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
           int cl = -1;
           if (t < m) {
             id = queue[b + t];
-            if (c >= 0) cl = kint_class_t<T, DX>(fabs(v[(int64_t)id * v_stride]), x[id]);
+            if (c >= 0) cl = kint_class((double)fabs(v[(int64_t)id * v_stride]), (double)x[id], DX);
           }
           const bool take = t < m && cl == c;
           const unsigned mk = __ballot_sync(0xffffffffu, take);
