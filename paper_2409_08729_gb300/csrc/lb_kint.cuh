@@ -523,9 +523,12 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
       const double x = __shfl_sync(0xffffffffu, xi, e);
       const double beta = __shfl_sync(0xffffffffu, beta_i, e);
       double mm, s0, s1 = 0.0;
-      if (ng == 0) kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
-      else if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1, ks);
-      else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1, ks);
+      if (ng == 0) {
+        kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
+      } else if constexpr (DX) {                 // values take the fixed-point sums above
+        if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1, ks);
+        else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1, ks);
+      }
       s0 = warp_sum(s0);
       if (DX) s1 = warp_sum(s1);
       if (lane == e) {
