@@ -96,6 +96,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time (ms): the job takes as long as its slowest
+    rank.  `dist` is torch.distributed with a process group, or None."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gevals(evals_per_step, steps, world, ms):
+    """Whole-job throughput: the evaluations of all ranks (each rank runs the
+    same workload: weak scaling) over the slowest rank's time."""
+    return evals_per_step * steps * world / (ms / 1e3) / 1e9
+
+
 def oracle_sample(n_per_v, seed):
     from paper_2409_08729_gb300.workloads import sweep_pairs
     v, x = sweep_pairs(n_per_v, seed=seed)
@@ -236,11 +253,8 @@ def main():
     prof = B.profile_read()
     B.profile_enable(False)
     clocks = sampler.stop()
-    if pg:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = evals_per_step * args.steps * world / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms, pg, dev)
+    value = job_gevals(evals_per_step, args.steps, world, ms)
 
     # ---- end to end: the same step through logbessel_host on pinned host
     # buffers (copy-in, evaluation and copy-out of chunks overlap inside) ----
@@ -287,11 +301,8 @@ def main():
         torch.cuda.synchronize()
         ems = (time.perf_counter() - t0h) * 1e3
         eclocks = esampler.stop()
-        if pg:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": evals_per_step * args.steps * world / (ems / 1e3) / 1e9, "unit": UNIT,
+        ems = max_over_ranks(ems, pg, dev)
+        e2e = {"value": job_gevals(evals_per_step, args.steps, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": 2 * (nv * 8 + n1 * 8 * nv + 2 * n_all * 8),
                "d2h_bytes_per_step": 4 * n_all * 8,
                "api": "logbessel_host (C ABI, pinned host buffers, synchronous per call)",
@@ -345,8 +356,8 @@ def main():
             step32()
         g1.record(stream)
         torch.cuda.synchronize()
-        ms32 = g0.elapsed_time(g1)
-        fp32 = {"value": evals_per_step * args.steps * world / (ms32 / 1e3) / 1e9, "unit": UNIT,
+        ms32 = max_over_ranks(g0.elapsed_time(g1), pg, dev)
+        fp32 = {"value": job_gevals(evals_per_step, args.steps, world, ms32), "unit": UNIT,
                 "ms_per_step": ms32 / args.steps, "dtype": "f32 inputs/outputs, FP32-pipe evaluation"}
         if rank == 0 and args.err_sample > 0:
             import oracle
