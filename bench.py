@@ -148,7 +148,10 @@ def reference_arm(args, rank, world):
     wall = time.perf_counter() - t0
     value = 2 * per_v * 11 * args.steps / wall / 1e9
     sample = "%d pairs per step (%d per order, log I + log K), drawn from the sweep" % (11 * per_v, per_v)
+    # rank 0 alone runs the oracle: the value is that one process's
+    # throughput on the host cores, not a whole-job figure over N ranks
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "ranks_used": 1, "value_scope": "rank 0 only (the oracle on the host cores; other ranks idle)",
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": 22 * per_v},
@@ -189,7 +192,7 @@ def main():
     import torch
     import paper_2409_08729_gb300 as lb
     from paper_2409_08729_gb300 import _binding as B
-    from paper_2409_08729_gb300 import workmodel as WM
+    from benchmarks import workmodel as WM
     from paper_2409_08729_gb300.workloads import SWEEP_ORDERS, sweep_device
     lb.build_library()
 
@@ -449,17 +452,17 @@ def main():
     del outs
     torch.cuda.empty_cache()
     if rank == 0 and args.robust_n > 0:
-        from paper_2409_08729_gb300 import robustbench
+        from benchmarks import robustbench
         line["robustness_sweep"] = robustbench.run(n=args.robust_n, device=str(dev),
                                                    per_region=1000 if args.err_sample > 0 else 0,
                                                    check=args.err_sample > 0)
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_paper_tables:
-        from paper_2409_08729_gb300 import paperbench
+        from benchmarks import paperbench
         line["paper_workloads"] = paperbench.run(device=str(dev))
         torch.cuda.empty_cache()
     if rank == 0 and args.serve_requests > 0:
-        from paper_2409_08729_gb300 import servebench
+        from benchmarks import servebench
         line["serving"] = servebench.run(n_req=args.serve_requests, seed=0, device=str(dev))
     if rank == 0:
         r, threads, n = time_oracle(args.cpu_per_v)

@@ -14,7 +14,7 @@ times are CUDA-event averages over `reps` calls after one warm-up call.
 """
 import torch
 
-from . import _binding as B
+from paper_2409_08729_gb300 import _binding as B
 
 
 def _time(fn, reps):

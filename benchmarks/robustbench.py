@@ -13,9 +13,9 @@ the FP32-mixed form is compared with the oracle at its own (rounded) inputs.
 import numpy as np
 import torch
 
-from . import _binding as B
-from . import classify
-from .workloads import robust_device
+from paper_2409_08729_gb300 import _binding as B
+from paper_2409_08729_gb300 import classify
+from paper_2409_08729_gb300.workloads import robust_device
 
 REGION_NAMES = {0: "mu20", 1: "u13", 2: "fallback", 3: "special", 4: "mu3", 5: "u4", 6: "u6", 7: "u9"}
 

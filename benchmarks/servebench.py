@@ -15,8 +15,8 @@ import time
 import numpy as np
 import torch
 
-from . import _binding as B
-from .serve import Server
+from paper_2409_08729_gb300 import _binding as B
+from paper_2409_08729_gb300.serve import Server
 
 
 def _mix(n_req, seed, max_n):
@@ -162,6 +162,6 @@ if __name__ == "__main__":
     ap.add_argument("--loads", default="0.5,0.8,0.95")
     ap.add_argument("--seed", type=int, default=0)
     a = ap.parse_args()
-    from . import build_library
+    from paper_2409_08729_gb300 import build_library
     build_library()
     print(json.dumps(run(n_req=a.requests, seed=a.seed, load=[float(t) for t in a.loads.split(",")])), flush=True)

@@ -135,7 +135,10 @@ lb_status logbessel_k_dx_ws(lb_dtype dtype, const void* v, int64_t v_stride, con
  * 1048576 pairs per call; a larger n returns LB_EINVAL with a message and
  * launches nothing.  The first call on a device looks up the scratch
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture on the device.  Every call shares the one
+ * call before any stream capture on the device.  The address is kept for the
+ * life of the process: after cudaDeviceReset (or any other teardown of the
+ * device's primary context) the module reloads elsewhere, so this entry point
+ * must not be called again in that process.  Every call shares the one
  * array and clears its counter and mask on the stream: calls whose work overlaps on
  * the GPU (different streams, or concurrent host threads) race and must be
  * serialized by the caller.  Other arguments, results and errors as in

@@ -756,12 +756,14 @@ lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride
     char* dv = P.dbuf + b * slot;
     char* dx = dv + ((vbytes + 255) & ~(size_t)255);
     char* dout = dx + ((xbytes + 255) & ~(size_t)255);
-    if (i >= nbuf) cudaStreamWaitEvent(st[0], P.ev_out[b], 0);     // slot b's results are out
     const char* hv = (const char*)v + (v_stride ? c0 * (int64_t)es : 0);
-    cudaMemcpyAsync(dv, hv, (size_t)(v_stride ? cn : 1) * es, cudaMemcpyHostToDevice, st[0]);
-    cudaMemcpyAsync(dx, (const char*)x + c0 * (int64_t)es, (size_t)cn * es, cudaMemcpyHostToDevice, st[0]);
-    cudaEventRecord(P.ev_in[b], st[0]);
-    cudaStreamWaitEvent(st[1], P.ev_in[b], 0);
+    if ((i >= nbuf && cudaStreamWaitEvent(st[0], P.ev_out[b], 0) != cudaSuccess) ||   // slot b's results are out
+        cudaMemcpyAsync(dv, hv, (size_t)(v_stride ? cn : 1) * es, cudaMemcpyHostToDevice, st[0]) != cudaSuccess ||
+        cudaMemcpyAsync(dx, (const char*)x + c0 * (int64_t)es, (size_t)cn * es, cudaMemcpyHostToDevice, st[0]) != cudaSuccess ||
+        cudaEventRecord(P.ev_in[b], st[0]) != cudaSuccess || cudaStreamWaitEvent(st[1], P.ev_in[b], 0) != cudaSuccess) {
+      s = check_launch("logbessel_host: copy-in");
+      break;
+    }
     // one pass per chunk (cn <= cap <= kChunk), the K queue in ws
     if (dtype == LB_F32) {
       const float *fv = (const float*)dv, *fx = (const float*)dx;
@@ -778,13 +780,18 @@ lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride
         default: s = run_impl<KIND_K, true, double>(dvv, v_stride, dxx, dd, cn, (int)mode, -1, st[1], ws, kChunk); break;
       }
     }
-    cudaEventRecord(P.ev_comp[b], st[1]);
-    cudaStreamWaitEvent(st[2], P.ev_comp[b], 0);
-    cudaMemcpyAsync((char*)out + c0 * (int64_t)es, dout, (size_t)cn * es, cudaMemcpyDeviceToHost, st[2]);
-    cudaEventRecord(P.ev_out[b], st[2]);
+    if (s != LB_OK) break;
+    if (cudaEventRecord(P.ev_comp[b], st[1]) != cudaSuccess || cudaStreamWaitEvent(st[2], P.ev_comp[b], 0) != cudaSuccess ||
+        cudaMemcpyAsync((char*)out + c0 * (int64_t)es, dout, (size_t)cn * es, cudaMemcpyDeviceToHost, st[2]) != cudaSuccess ||
+        cudaEventRecord(P.ev_out[b], st[2]) != cudaSuccess) {
+      s = check_launch("logbessel_host: copy-out");
+      break;
+    }
   }
   for (int i = 0; i < 3; ++i)
     if (cudaStreamSynchronize(st[i]) != cudaSuccess && s == LB_OK) s = check_launch("logbessel_host");
+  // an asynchronous error of the last copies surfaces here, not in a later call
+  if (s == LB_OK) s = check_launch("logbessel_host");
   return s;
 }
 

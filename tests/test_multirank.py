@@ -63,4 +63,6 @@ def test_reference_arm_two_ranks():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    # rank 0 alone ran the oracle: the value is not a whole-job figure
+    assert d["ranks_used"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle"
