@@ -9,6 +9,10 @@ log I_v(x) from the positive-term power series (paper Sec. 3.1, the infinite
 series of I_v), log K_v(x) from the integral int_0^inf exp(-x cosh t) cosh(vt)
 dt (DLMF 10.32.9) by the trapezoid rule.  Neither uses the paper's asymptotic
 expansions or its Rothwell integral, so the two sides share no formula.
+The same source also builds on the C type long double (binary128 on aarch64,
+80-bit on x86-64) with libm's long double functions: ``log_i_ld``,
+``log_k_ld``; its agreement with the double-double build pins the
+double-double arithmetic layer.
 """
 import ctypes
 import os
@@ -19,29 +23,62 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "logbessel_oracle.c")
 _SO = os.path.join(_HERE, "_build", "liblogbessel_oracle.so")
+# the same evaluators compiled on the C type long double (binary128 on
+# aarch64, 80-bit x87 on x86-64) instead of double-double
+_SO_LD = os.path.join(_HERE, "_build", "liblogbessel_oracle_ld.so")
 
 OP_LOG_I, OP_LOG_K, OP_DLOG_I, OP_DLOG_K, OP_DV_I, OP_DV_K, OP_VMF = range(7)
 
 _lib = None
 
 
-def build(force=False):
-    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
-    os.makedirs(os.path.dirname(_SO), exist_ok=True)
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
-        return _SO
-    tmp = _SO + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
-           _SRC, "-o", tmp, "-lm"]
+def _compile(so, defines):
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    if os.path.exists(so) and os.path.getmtime(so) >= os.path.getmtime(_SRC):
+        return so
+    tmp = so + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread"] + defines + \
+          [_SRC, "-o", tmp, "-lm"]
     subprocess.check_call(cmd)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
+
+
+def build(force=False):
+    """Compile the oracle with gcc (no fast-math, no FMA contraction): the
+    double-double build and the long double build of the same source."""
+    if force:
+        for so in (_SO, _SO_LD):
+            if os.path.exists(so):
+                os.remove(so)
+    _compile(_SO_LD, ["-DORACLE_LONG_DOUBLE"])
+    return _compile(_SO, [])
+
+
+def _declare(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_eval.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_int64, ctypes.c_int]
+    lib.oracle_eval.restype = ctypes.c_int
+    lib.oracle_significand_bits.argtypes = []
+    lib.oracle_significand_bits.restype = ctypes.c_int
+    return lib
+
+
+_lib_ld = None
+
+
+def _load_ld():
+    global _lib_ld
+    if _lib_ld is None:
+        build()
+        _lib_ld = _declare(ctypes.CDLL(_SO_LD))
+    return _lib_ld
 
 
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        lib = _declare(ctypes.CDLL(build()))
         dp = ctypes.POINTER(ctypes.c_double)
         lib.oracle_eval.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_int64, ctypes.c_int]
         lib.oracle_eval.restype = ctypes.c_int
@@ -59,8 +96,8 @@ def default_threads():
     return os.cpu_count() or 1
 
 
-def _eval(op, a, b, threads=None, want_lo=False):
-    lib = _load()
+def _eval(op, a, b, threads=None, want_lo=False, lib=None):
+    lib = lib or _load()
     a, b = np.broadcast_arrays(np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64))
     shape = a.shape
     a = np.ascontiguousarray(a.ravel())
@@ -86,6 +123,23 @@ def log_i(v, x, threads=None, want_lo=False):
 def log_k(v, x, threads=None, want_lo=False):
     """log K_v(x) (double, or (hi, lo) pair with want_lo)."""
     return _eval(OP_LOG_K, v, x, threads, want_lo)
+
+
+def long_double_bits():
+    """Significand bits of the long double build: 113 (binary128, aarch64
+    Linux) or 64 (x87 extended, x86-64)."""
+    return _load_ld().oracle_significand_bits()
+
+
+def log_i_ld(v, x, threads=None):
+    """log I_v(x) from the long double build of the same evaluator, as a
+    (hi, lo) pair of doubles (hi + lo carries the long double result)."""
+    return _eval(OP_LOG_I, v, x, threads, True, _load_ld())
+
+
+def log_k_ld(v, x, threads=None):
+    """log K_v(x) from the long double build, as a (hi, lo) pair."""
+    return _eval(OP_LOG_K, v, x, threads, True, _load_ld())
 
 
 def dlog_i_dx(v, x, threads=None):

@@ -42,11 +42,14 @@
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread (no fast-math).
  */
+#define _DEFAULT_SOURCE   /* lgammal_r */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <pthread.h>
 
+#ifndef ORACLE_LONG_DOUBLE
 /* ------------------------------------------------------------------ */
 /* double-double arithmetic                                            */
 /* ------------------------------------------------------------------ */
@@ -212,6 +215,61 @@ static dd dd_lgamma(dd z) {
   }
   return dd_sub(res, shift_log);
 }
+#define ORACLE_NOISE_UNIT 1e-31   /* resolution of phi near its peak (double-double) */
+
+#else /* ORACLE_LONG_DOUBLE */
+/* ------------------------------------------------------------------ */
+/* the same evaluators in the C type long double                       */
+/* ------------------------------------------------------------------ */
+/* A second build of this file (-DORACLE_LONG_DOUBLE) runs the evaluators
+ * below unchanged on the C type long double instead of double-double:
+ * binary128 (113-bit significand) on aarch64 Linux, the x87 80-bit format
+ * (64-bit significand) on x86-64.  Every double-double operation maps to one
+ * long double operation, and exp, log, log1p and lgamma to libm's expl,
+ * logl, log1pl and lgammal_r, so the two builds share the algorithm and
+ * nothing of the arithmetic: their agreement checks the double-double layer
+ * (to ~1e-30 where binary128 exists).  The field lo stays zero. */
+typedef long double ldbl;
+typedef struct { ldbl hi, lo; } dd;
+
+static inline dd dd_make(ldbl hi, ldbl lo) { dd r = {hi + lo, 0.0L}; return r; }
+static inline dd dd_from(double a) { return dd_make((ldbl)a, 0.0L); }
+static inline dd two_prod(double a, double b) { return dd_make((ldbl)a * (ldbl)b, 0.0L); }
+static inline dd dd_add(dd a, dd b) { return dd_make(a.hi + b.hi, 0.0L); }
+static inline dd dd_neg(dd a) { return dd_make(-a.hi, 0.0L); }
+static inline dd dd_sub(dd a, dd b) { return dd_make(a.hi - b.hi, 0.0L); }
+static inline dd dd_add_d(dd a, double b) { return dd_make(a.hi + (ldbl)b, 0.0L); }
+static inline dd dd_mul(dd a, dd b) { return dd_make(a.hi * b.hi, 0.0L); }
+static inline dd dd_mul_d(dd a, double b) { return dd_make(a.hi * (ldbl)b, 0.0L); }
+static inline dd dd_div(dd a, dd b) { return dd_make(a.hi / b.hi, 0.0L); }
+static inline dd dd_ldexp(dd a, int e) { return dd_make(ldexpl(a.hi, e), 0.0L); }
+static inline double dd_to_d(dd a) { return (double)a.hi; }
+
+/* ln 2 and pi, the published digits */
+static const dd DD_LN2 = {0.693147180559945309417232121458176568L, 0.0L};
+static const dd DD_PI = {3.141592653589793238462643383279502884L, 0.0L};
+
+static void init_tables(void) {}
+
+/* the same range as the double-double exp: +inf above 709, 0 below -745 */
+static dd dd_exp(dd a) {
+  if (a.hi > 709.0L) return dd_from(INFINITY);
+  if (a.hi < -745.0L) return dd_from(0.0);
+  return dd_make(expl(a.hi), 0.0L);
+}
+static dd dd_log(dd a) {
+  if (a.hi <= 0.0L) return dd_from(a.hi == 0.0L ? -INFINITY : NAN);
+  return dd_make(logl(a.hi), 0.0L);
+}
+static dd dd_log1p(dd t) { return dd_make(log1pl(t.hi), 0.0L); }
+static dd dd_lgamma(dd z) {
+  int sign;
+  return dd_make(lgammal_r(z.hi, &sign), 0.0L);
+}
+
+/* resolution of phi near its peak: a few units of the long double epsilon */
+#define ORACLE_NOISE_UNIT (8.0 * (double)LDBL_EPSILON)
+#endif /* ORACLE_LONG_DOUBLE */
 
 /* ------------------------------------------------------------------ */
 /* log I_v(x): positive-term series from the peak term                 */
@@ -319,7 +377,7 @@ static dd log_k_dd(dd v, double x) {
    * than 1e-18 (relative), the new sum is accurate far beyond 1e-30.  The
    * double-double noise floor of phi where the integrand matters
    * (|x cosh t| <= |phi_max| + 90 + v t there) bounds what can be resolved. */
-  double noise = 1e-31 * (1.0 + fabs(pmax.hi) + 100.0 + 2.0 * vd * thi);
+  double noise = ORACLE_NOISE_UNIT * (1.0 + fabs((double)pmax.hi) + 100.0 + 2.0 * vd * thi);
   if (noise < 1e-18) noise = 1e-18;
   for (int level = 0; level < 16; ++level) {
     dd add = dd_from(0.0);
@@ -491,4 +549,14 @@ void oracle_dd_log1p(double hi, double lo, double* out2) { init_tables(); dd r =
 void oracle_dd_const(int which, double* out2) {
   dd r = which == 0 ? DD_LN2 : DD_PI;
   out2[0] = r.hi; out2[1] = r.lo;
+}
+
+/* Significand bits of the arithmetic this build evaluates in: 106 for
+ * double-double (two 53-bit doubles), LDBL_MANT_DIG for the long double build. */
+int oracle_significand_bits(void) {
+#ifdef ORACLE_LONG_DOUBLE
+  return LDBL_MANT_DIG;
+#else
+  return 106;
+#endif
 }
