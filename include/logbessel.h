@@ -269,13 +269,20 @@ lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t 
 /*
  * Continuous-batching server (serving loop).  Requests of any size arrive
  * from host threads; a scheduler thread admits them as request slots and
- * device memory (a fixed arena) free up, copies their inputs to the GPU, and
- * publishes their tiles to a persistent kernel, which interleaves the tiles
- * of all resident requests, so requests that arrive while others run overlap
- * on the device.  Results are copied back into the caller's buffer.
+ * device memory (a fixed arena) free up, copies the inputs of host requests
+ * to the GPU, and publishes their work to a persistent kernel, which
+ * interleaves the work of all resident requests, so requests that arrive
+ * while others run overlap on the device.  A request runs the two stages of
+ * a direct call: tiles (classify, bin, expressions), then for log K the
+ * integral of the fallback pairs, queued per quadrature rule class and
+ * evaluated in windows of one class each (paper Sec. 3.2; Sec. 4.3 groups
+ * pairs by expression for the same reason: one code path per warp).
+ * Results of host requests are copied back into the caller's buffer.
  *
- *   arena_bytes  device memory for request buffers (>= 1 MiB); a request
- *                needs about 3 n elements (v, x, out), rounded to 256 B
+ *   arena_bytes  device memory for request buffers (>= 1 MiB); a host
+ *                request needs 3 n elements (v, x, out), a log K request
+ *                also its queues: 24 n bytes (FP64, LB_TIGHT: six rule
+ *                classes) or 4 n bytes; each part rounded to 256 B
  *   max_slots    requests resident on the device at once (1..4096)
  *   ctas_per_sm  persistent thread blocks per SM (1..8)
  *   idle_ms      a thread block with no work for this long exits; the
@@ -294,6 +301,16 @@ lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t 
  * (result in the host buffer).  lb_server_release forgets a finished ticket.
  * lb_server_destroy stops the kernel and frees everything.  The paper has no
  * serving component; this is the batched front end of the same kernels.
+ *
+ * lb_server_submit_device: the same request on DEVICE buffers v, x, out of
+ * the server's device; nothing is copied and the results are written to out
+ * in place.  The inputs must be complete when the request is admitted: pass
+ * a cudaEvent_t recorded after the work that writes them as ready_event (the
+ * server starts the request once the event has completed; the event must
+ * stay valid until lb_server_wait returns LB_OK), or NULL when they are
+ * already complete.  When lb_server_wait returns LB_OK the results are in
+ * out and the server no longer reads v and x.  The arena then holds only the
+ * K queues (none for log I).
  */
 typedef struct lb_server lb_server;
 typedef struct {
@@ -306,6 +323,9 @@ typedef struct {
 lb_status lb_server_create(const lb_server_config* cfg, lb_server** server);
 lb_status lb_server_submit(lb_server* server, int kind, lb_dtype dtype, const void* v, int64_t v_stride,
                            const void* x, void* out, int64_t n, lb_mode mode, long long* ticket);
+lb_status lb_server_submit_device(lb_server* server, int kind, lb_dtype dtype, const void* v, int64_t v_stride,
+                                  const void* x, void* out, int64_t n, lb_mode mode, void* ready_event,
+                                  long long* ticket);
 lb_status lb_server_wait(lb_server* server, long long ticket, double timeout_s);
 lb_status lb_server_ticket_info(lb_server* server, long long ticket, int* done, double* t_submit,
                                 double* t_admit, double* t_done);

@@ -1,8 +1,9 @@
 """Continuous-batching server over the C ABI (lb_server_* in include/logbessel.h).
 
-Requests carry host arrays; the native scheduler admits them as slots and
-device memory free up, and a persistent kernel interleaves the tiles of all
-resident requests.  This module only marshals arguments.
+Requests carry host arrays (submit) or CUDA tensors (submit_device, evaluated
+in place); the native scheduler admits them as slots and device memory free
+up, and a persistent kernel interleaves the work of all resident requests.
+This module only marshals arguments.
 """
 import ctypes
 
@@ -25,6 +26,7 @@ def _lib():
         vp, i64, i32, ll = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_longlong
         L.lb_server_create.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(vp)]
         L.lb_server_submit.argtypes = [vp, i32, i32, vp, i64, vp, vp, i64, i32, ctypes.POINTER(ll)]
+        L.lb_server_submit_device.argtypes = [vp, i32, i32, vp, i64, vp, vp, i64, i32, vp, ctypes.POINTER(ll)]
         L.lb_server_wait.argtypes = [vp, ll, ctypes.c_double]
         dp = ctypes.POINTER(ctypes.c_double)
         L.lb_server_ticket_info.argtypes = [vp, ll, ctypes.POINTER(i32), dp, dp, dp]
@@ -33,7 +35,8 @@ def _lib():
         L.lb_server_destroy.argtypes = [vp]
         L.lb_server_last_error.argtypes = []
         L.lb_server_last_error.restype = ctypes.c_char_p
-        for nm in ("lb_server_create", "lb_server_submit", "lb_server_wait", "lb_server_ticket_info",
+        for nm in ("lb_server_create", "lb_server_submit", "lb_server_submit_device", "lb_server_wait",
+                   "lb_server_ticket_info",
                    "lb_server_release", "lb_server_stats", "lb_server_destroy"):
             getattr(L, nm).restype = i32
         L._serve_ready = True
@@ -74,6 +77,53 @@ class Server:
         _check(_lib().lb_server_submit(self._h, _KIND.get(kind, -1), _DT[dx], pv, 0 if nv == 1 else 1, px, po, nx,
                                        B.MODES.get(mode, -1), ctypes.byref(t)))
         self._keep[t.value] = (ov, ox, oo)
+        return t.value
+
+    def submit_device(self, kind, v, x, out, mode="tight", ready="stream"):
+        """Queue one request on CUDA tensors of the server's device (v one
+        order or one per pair, x and out contiguous, one dtype); the results
+        are written to out in place.  `ready` says when the inputs are
+        complete: "stream" (default) records an event on the current stream,
+        so inputs written by work queued before the call are used; a
+        torch.cuda.Event recorded after the writes; or None when they are
+        complete already.  The tensors must stay alive until wait()."""
+        import torch
+        for a in (v, x, out):
+            if not isinstance(a, torch.Tensor) or a.device.type != "cuda" or not a.is_contiguous():
+                raise ValueError("submit_device takes contiguous CUDA tensors")
+        if not (v.dtype == x.dtype == out.dtype) or x.dtype not in (torch.float32, torch.float64):
+            raise TypeError("v, x, out must share dtype float32 or float64")
+        if out.numel() != x.numel() or v.numel() not in (1, x.numel()):
+            raise ValueError("shape mismatch")
+        if isinstance(ready, str):
+            ready = torch.cuda.Event()
+            ready.record(torch.cuda.current_stream(x.device))
+        code = B.LB_F64 if x.dtype == torch.float64 else B.LB_F32
+        t = ctypes.c_longlong()
+        _check(_lib().lb_server_submit_device(self._h, _KIND.get(kind, -1), code, v.data_ptr(),
+                                              0 if v.numel() == 1 else 1, x.data_ptr(), out.data_ptr(),
+                                              x.numel(), B.MODES.get(mode, -1),
+                                              ctypes.c_void_p(ready.cuda_event if ready is not None else None),
+                                              ctypes.byref(t)))
+        self._keep[t.value] = (v, x, out, ready)
+        return t.value
+
+    def submit_ptr(self, kind, dtype, v, v_stride, x, out, n, device=False, mode="tight"):
+        """Queue one request given raw pointers (ints): kind 'i' or 'k',
+        dtype LB_F64 or LB_F32, v_stride 0 or 1; host pointers, or device
+        pointers with device=True (inputs complete now).  For callers that
+        keep their buffers alive themselves and submit at high rates: no
+        argument inspection, no references kept."""
+        t = ctypes.c_longlong()
+        L = _lib()
+        if device:
+            st = L.lb_server_submit_device(self._h, _KIND[kind], dtype, v, v_stride, x, out, n, B.MODES[mode], None,
+                                           ctypes.byref(t))
+        else:
+            st = L.lb_server_submit(self._h, _KIND[kind], dtype, v, v_stride, x, out, n, B.MODES[mode],
+                                    ctypes.byref(t))
+        if st != B.LB_OK:
+            _check(st)
         return t.value
 
     def wait(self, ticket, timeout=60.0):

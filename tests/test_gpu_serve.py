@@ -1,16 +1,33 @@
-"""Serving loop: results equal the one-call path alone and in the mix;
-admission by memory; bounded waits; relaunch after idle."""
+"""Serving loop: every served request matches the oracle (FP64 gate 4e-15,
+FP32-mixed 2e-6 at its float inputs) and the one-call path, alone and in the
+mix; host and device-resident requests; admission by memory; bounded waits;
+relaunch after idle."""
 import time
 
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2409_08729_gb300 as lb
 from paper_2409_08729_gb300.serve import Server
 from paper_2409_08729_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+TOL = {np.dtype(np.float64): 4e-15, np.dtype(np.float32): 2e-6}
+
+
+def _oracle_ok(kind, v, x, o, per_request=256, seed=0):
+    """A sample of the request's outputs (all of them for small requests)
+    against the oracle at the request's own inputs (float inputs widened
+    exactly), in the error metric of the parity tests."""
+    n = x.size
+    idx = np.arange(n) if n <= per_request else np.random.default_rng(seed).choice(n, per_request, replace=False)
+    vv = (v if v.size > 1 else np.broadcast_to(v, x.shape))[idx].astype(np.float64)
+    xx = x[idx].astype(np.float64)
+    ref = oracle.log_i(vv, xx) if kind == "i" else oracle.log_k(vv, xx)
+    err = oracle.rel_err(o[idx].astype(np.float64), ref, oracle.error_scale(kind, vv, xx))
+    return float(err.max()) <= TOL[o.dtype], float(err.max())
 
 
 def _requests(n_req, seed, max_n=60000):
@@ -48,13 +65,93 @@ def test_mix_equals_alone(cuda):
         tickets = [srv.submit(k, v, x, o) for k, v, x, o in reqs]
         for t in tickets:
             srv.wait(t, timeout=120)
-        for (k, v, x, o) in reqs:
+        for i, (k, v, x, o) in enumerate(reqs):
+            ok, worst = _oracle_ok(k, v, x, o, seed=i)
+            assert ok, (i, k, o.dtype, x.size, worst)
             assert _close(o, _alone(k, v, x, cuda), o.dtype)
         st = srv.stats()
         assert st["completed"] == len(reqs) and st["in_flight"] == 0
 
 
+def _device_requests(reqs, dev):
+    out = []
+    for k, v, x, o in reqs:
+        tv = torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+        tx = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        out.append((k, tv, tx, torch.full_like(tx, float("nan"))))
+    return out
+
+
+def test_device_requests_match_oracle(cuda):
+    """Requests on device buffers (evaluated in place, nothing copied): every
+    result against the oracle on a sample and against the one-call path."""
+    reqs = _requests(48, seed=6)
+    dreqs = _device_requests(reqs, cuda)
+    with Server(arena_bytes=256 << 20, max_slots=32) as srv:
+        tickets = [srv.submit_device(k, tv, tx, to) for k, tv, tx, to in dreqs]
+        for t in tickets:
+            srv.wait(t, timeout=120)
+    for i, ((k, v, x, _), (_, tv, tx, to)) in enumerate(zip(reqs, dreqs)):
+        o = to.cpu().numpy()
+        ok, worst = _oracle_ok(k, v, x, o, seed=100 + i)
+        assert ok, (i, k, o.dtype, x.size, worst)
+        assert _close(o, _alone(k, v, x, cuda), o.dtype)
+
+
+def test_host_and_device_requests_together(cuda):
+    """Host and device requests submitted interleaved share the device; a
+    K-heavy device request (every pair in the integral, all six rule classes)
+    is served in the mix and equals the same request served alone."""
+    reqs = _requests(30, seed=7)
+    rng = np.random.default_rng(7)
+    vk = np.concatenate([rng.uniform(0.0, 16.0, 20000), [0.1, 0.3, 1.0, 3.0, 10.0]])
+    xk = np.concatenate([np.exp(rng.uniform(np.log(1e-8), np.log(25.0), 20000)), [1e-5, 1e-300, 0.5, 2.0, 24.0]])
+    tv, tx = torch.tensor(vk, device=cuda), torch.tensor(xk, device=cuda)
+    heavy_mix, heavy_alone = torch.empty_like(tx), torch.empty_like(tx)
+    with Server(arena_bytes=128 << 20, max_slots=16) as srv:
+        srv.wait(srv.submit_device("k", tv, tx, heavy_alone), timeout=120)
+        ts = []
+        for i, (k, v, x, o) in enumerate(reqs):
+            ts.append(srv.submit(k, v, x, o))
+            if i == 10:
+                ts.append(srv.submit_device("k", tv, tx, heavy_mix))
+        for t in ts:
+            srv.wait(t, timeout=120)
+    assert torch.equal(heavy_mix, heavy_alone)
+    ok, worst = _oracle_ok("k", vk, xk, heavy_mix.cpu().numpy(), per_request=2000)
+    assert ok, worst
+    for i, (k, v, x, o) in enumerate(reqs):
+        ok, worst = _oracle_ok(k, v, x, o, seed=200 + i)
+        assert ok, (i, worst)
+
+
+def test_device_request_waits_for_its_inputs(cuda):
+    """A device request starts only once its ready event has completed: the
+    inputs written on a side stream after a long kernel are the ones used."""
+    n = 300000
+    v, x = W.robust_pairs(n, seed=8, vmax=1e4, xmin=1e-3, xmax=1e4)
+    tv = torch.zeros(n, dtype=torch.float64, device=cuda)
+    tx = torch.ones(n, dtype=torch.float64, device=cuda)
+    out = torch.empty_like(tx)
+    side = torch.cuda.Stream(cuda)
+    side.wait_stream(torch.cuda.current_stream(cuda))     # after the fills above
+    hv, hx = torch.from_numpy(v).pin_memory(), torch.from_numpy(x).pin_memory()
+    with Server(arena_bytes=64 << 20, max_slots=4) as srv:
+        with torch.cuda.stream(side):
+            torch.cuda._sleep(50_000_000)          # keep the side stream busy for a while
+            tv.copy_(hv, non_blocking=True)
+            tx.copy_(hx, non_blocking=True)
+            ready = torch.cuda.Event()
+            ready.record(side)
+        t = srv.submit_device("i", tv, tx, out, ready=ready)
+        srv.wait(t, timeout=120)
+    ok, worst = _oracle_ok("i", v, x, out.cpu().numpy(), per_request=2000)
+    assert ok, worst
+
+
 def test_one_at_a_time_equals_mix(cuda):
+    """Each request served alone and served in the mix gives the same bits
+    (a pair's result does not depend on the tile or window it shares)."""
     reqs = _requests(12, seed=2, max_n=20000)
     outs_alone = []
     with Server(arena_bytes=64 << 20, max_slots=8) as srv:
@@ -67,7 +164,7 @@ def test_one_at_a_time_equals_mix(cuda):
         for t in ts:
             srv.wait(t, timeout=60)
     for (k, v, x, o), a in zip(reqs, outs_alone):
-        assert _close(o, a, o.dtype)
+        assert np.array_equal(o, a, equal_nan=True)
 
 
 def test_admission_by_memory(cuda):
@@ -78,8 +175,10 @@ def test_admission_by_memory(cuda):
         ts = [srv.submit(k, v, x, o) for k, v, x, o in reqs]
         for t in ts:
             srv.wait(t, timeout=120)
-        for (k, v, x, o) in reqs:
+        for i, (k, v, x, o) in enumerate(reqs):
             assert _close(o, _alone(k, v, x, cuda), o.dtype)
+            ok, worst = _oracle_ok(k, v, x, o, per_request=64, seed=300 + i)
+            assert ok, (i, worst)
 
 
 def test_rejections_and_timeout(cuda):
@@ -90,7 +189,8 @@ def test_rejections_and_timeout(cuda):
         assert "arena" in str(e.value)
         with pytest.raises(lb.LogBesselError):
             srv.submit("q", big[:4], big[:4], np.empty(4))
-        v, x = W.robust_pairs(30000, seed=4, vmax=16, xmin=1e-3, xmax=25)     # K integral heavy
+        # K integral heavy; 15000 pairs: 360 KB of v, x, out and 360 KB of class queues
+        v, x = W.robust_pairs(15000, seed=4, vmax=16, xmin=1e-3, xmax=25)
         o = np.empty_like(x)
         t = srv.submit("k", v, x, o)
         try:
@@ -99,6 +199,11 @@ def test_rejections_and_timeout(cuda):
             assert err.status == 4      # LB_ETIMEOUT; the request stays queued
         srv.wait(t, timeout=60)
         assert _close(o, _alone("k", v, x, cuda), np.float64)
+        # a device request whose K queues alone exceed the arena is rejected too
+        tb = torch.ones(50000, dtype=torch.float64, device=cuda)
+        with pytest.raises(lb.LogBesselError) as e:
+            srv.submit_device("k", tb, tb, torch.empty_like(tb))
+        assert "arena" in str(e.value)
 
 
 def test_relaunch_after_idle(cuda):
