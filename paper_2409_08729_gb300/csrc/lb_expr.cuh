@@ -145,26 +145,50 @@ __device__ __forceinline__ int classify(double v, double x, int mode) {
 // ---------------------------------------------------------------------------
 // The number of terms actually summed is the smallest n <= K after which
 // the terms fall below 2^-56 (a later term is then below the rounding of S),
-// found with a single-precision pass and made uniform across the warp, so
-// the double-precision Horner loop never diverges.  All 32 lanes of the
-// warp must call it together.
-template <int KIND, int K>
-__device__ __forceinline__ double mu_expr(double v, double x) {
-  // single-precision estimate of the number of terms
+// found with a single-precision pass (mu_terms) and made uniform across the
+// warp, so the double-precision Horner loop never diverges.  The tile kernel
+// estimates n while it bins the pairs and orders each region by it, so the
+// warps' lanes need similar counts.
+template <int K>
+__device__ __forceinline__ int mu_terms(float v, float x) {
   int n = K;
-  {
-    // unrolled, so (2k-1)^2 and 1/k are constants: no division, no branch
-    const float muf = 4.0f * (float)v * (float)v, inv8xf = __fdividef(1.0f, 8.0f * (float)x);
-    float t = 1.0f;
-    bool found = false;
+  // unrolled, so (2k-1)^2 and 1/k are constants: no division, no branch
+  const float muf = 4.0f * v * v, inv8xf = __fdividef(1.0f, 8.0f * x);
+  float t = 1.0f;
+  bool found = false;
 #pragma unroll
-    for (int k = 1; k <= K; ++k) {
-      t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * (inv8xf * (1.0f / (float)k));
-      const bool hit = !found && fabsf(t) < 1.4e-17f;
-      n = hit ? k : n;
-      found = found || hit;
-    }
+  for (int k = 1; k <= K; ++k) {
+    t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * (inv8xf * (1.0f / (float)k));
+    const bool hit = !found && fabsf(t) < 1.4e-17f;
+    n = hit ? k : n;
+    found = found || hit;
   }
+  return n;
+}
+
+// Terms of the power series of log I (series_log_i, series_so): the count
+// after which a term falls below 2^-56 of the running sum past the peak
+// index (Eq. "K"), by a single-precision pass; at most 90.
+__device__ __forceinline__ int series_terms(float v, float x) {
+  int n = 1;
+  const float yf = 0.25f * x * x;
+  const float kpk = 0.5f * (sqrtf(fmaf(x, x, v * v)) - v);
+  float term = 1.0f, T = 0.0f, kf = 0.0f;
+#pragma unroll 1
+  for (int k = 1; k <= 90; ++k) {
+    kf += 1.0f;
+    term *= __fdividef(yf, kf * (kf + v));         // an estimate: the fast division suffices
+    T += term;
+    n = k;
+    if (kf > kpk && term <= 1.4e-17f * (1.0f + T)) break;
+  }
+  return n;
+}
+
+// mu_K with the lane's term count n given (at most K); all 32 lanes of the
+// warp call it together.
+template <int KIND, int K>
+__device__ __forceinline__ double mu_expr_n(double v, double x, int n) {
   n = __reduce_max_sync(0xffffffffu, n);
   const double mu = 4.0 * v * v;
   const double rx = ix_rcp_call(8.0 * x);                             // 1/(8x) on the integer pipe
@@ -187,6 +211,11 @@ __device__ __forceinline__ double mu_expr(double v, double x) {
   const double ax = fabs(inv8x);
   if (KIND == KIND_I) return fma(0.5, ix_log_call(S2 * ax * (8.0 / kTwoPi)), x);
   return fma(0.5, ix_log_call(S2 * ax * (4.0 * kPi)), -x);
+}
+
+template <int KIND, int K>
+__device__ __forceinline__ double mu_expr(double v, double x) {
+  return mu_expr_n<KIND, K>(v, x, mu_terms<K>((float)v, (float)x));
 }
 
 // P_k(p) of the Debye polynomial u_k(t) = t^k P_k(t^2); k is a compile-time
@@ -301,21 +330,7 @@ static __constant__ double kSeriesK2[91] = {
     5041, 5184, 5329, 5476, 5625, 5776, 5929, 6084, 6241, 6400, 6561, 6724, 6889, 7056, 7225, 7396,
     7569, 7744, 7921, 8100};
 
-__device__ __forceinline__ double series_log_i(double v, double x) {
-  int n = 1;
-  {
-    const float yf = 0.25f * (float)x * (float)x, vf = (float)v;
-    const float kpk = 0.5f * (sqrtf(fmaf((float)x, (float)x, vf * vf)) - vf);
-    float term = 1.0f, T = 0.0f, kf = 0.0f;
-#pragma unroll 1
-    for (int k = 1; k <= 90; ++k) {
-      kf += 1.0f;
-      term *= __fdividef(yf, kf * (kf + vf));      // an estimate: the fast division suffices
-      T += term;
-      n = k;
-      if (kf > kpk && term <= 1.4e-17f * (1.0f + T)) break;
-    }
-  }
+__device__ __forceinline__ double series_log_i_n(double v, double x, int n) {
   n = __reduce_max_sync(0xffffffffu, n);
   const double y = 0.25 * x * x;
   double A = 1.0, B = 1.0;
@@ -328,6 +343,10 @@ __device__ __forceinline__ double series_log_i(double v, double x) {
   double res = ix_log_call(A * ix_rcp_call(B)) - lgamma(v + 1.0);
   if (v != 0.0) res = fma(v, ix_log_call(0.5 * x), res);
   return res;
+}
+
+__device__ __forceinline__ double series_log_i(double v, double x) {
+  return series_log_i_n(v, x, series_terms((float)v, (float)x));
 }
 
 // ---------------------------------------------------------------------------
@@ -388,21 +407,8 @@ __device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
 }
 
 template <int KIND>
-__device__ __forceinline__ double mu_expr_so(const ScalarOrder& so, double x) {
+__device__ __forceinline__ double mu_expr_so(const ScalarOrder& so, double x, int n) {
   constexpr int K = 20;
-  int n = K;
-  {
-    const float muf = 4.0f * (float)so.v * (float)so.v, inv8xf = __fdividef(1.0f, 8.0f * (float)x);
-    float t = 1.0f;
-    bool found = false;
-#pragma unroll
-    for (int k = 1; k <= K; ++k) {
-      t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * (inv8xf * (1.0f / (float)k));
-      const bool hit = !found && fabsf(t) < 1.4e-17f;
-      n = hit ? k : n;
-      found = found || hit;
-    }
-  }
   n = __reduce_max_sync(0xffffffffu, n);
   const double w = ix_rcp_call(8.0 * x);
   double P = 0.0;
@@ -437,22 +443,8 @@ __device__ __forceinline__ double u_expr_so(const ScalarOrder& so, double x) {
   return fma(-v, eta, 0.5 * ix_log_call(w * (0.5 * kPi)));
 }
 
-__device__ __forceinline__ double series_so(const ScalarOrder& so, double x) {
+__device__ __forceinline__ double series_so(const ScalarOrder& so, double x, int n) {
   const double v = so.v;
-  int n = 1;
-  {
-    const float yf = 0.25f * (float)x * (float)x, vf = (float)v;
-    const float kpk = 0.5f * (sqrtf(fmaf((float)x, (float)x, vf * vf)) - vf);
-    float term = 1.0f, T = 0.0f, kf = 0.0f;
-#pragma unroll 1
-    for (int k = 1; k <= 90; ++k) {
-      kf += 1.0f;
-      term *= __fdividef(yf, kf * (kf + vf));
-      T += term;
-      n = k;
-      if (kf > kpk && term <= 1.4e-17f * (1.0f + T)) break;
-    }
-  }
   n = __reduce_max_sync(0xffffffffu, n);
   const double y = 0.25 * x * x;
   double P = 1.0;

@@ -63,10 +63,15 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
 // h rules 4 and 5 are the one-slot rules of kint_sum_one (22 g + 10 h
 // nodes, s0 = 8, for 2 <= v < 7; 12 + 20, s0 = 3, for 7 <= v <= 16.5), for
 // values only: their error map covers log K, not its x-derivative.
+// The x-derivative, a weighted mean of 1/(s + 2x) over the nodes, keeps the
+// 64-node g rule for v < 0.1 up to x = 0.6: there the 32-node rule leaves up
+// to 7e-15 relative error in the derivative (v = 0, x = 0.25), the 64-node
+// rule below 1e-16 (error map of the rules against the oracle's Bessel ratio).
 __device__ __forceinline__ int kint_rule(double v, double x, bool dx) {
   if (!dx && v >= 2.0 && v <= 16.5) return v < 7.0 ? (22 | (4 << 8)) : (12 | (5 << 8));
   if (v > 1.2 && v <= 5.0) return 24 | (3 << 8);
-  const int ng = (v >= 0.9 || x >= 0.25) ? 32 : ((v >= 0.4 || x >= 1e-3) ? 64 : 0);
+  const double x32 = (dx && v < 0.1) ? 0.6 : 0.25;
+  const int ng = (v >= 0.9 || x >= x32) ? 32 : ((v >= 0.4 || x >= 1e-3) ? 64 : 0);
   const int hr = (v <= 1.2) ? 0 : ((v <= 5.0) ? 1 : 2);
   return ng | (hr << 8);
 }
@@ -470,9 +475,13 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
 // pair e (DX = false) or d/dx log K (DX = true: the prefactor derivative
 // -v/x - 1 plus (2v - 1) <1/(s + 2x)>, the F-weighted mean over the nodes,
 // since dF/dx = F (2v - 1)/(s + 2x)).
-template <bool DX>
+// CLS >= 0 (values only): every pair of the batch is of rule class CLS
+// (kint_class), and only that class's code is compiled, so a kernel built
+// for one class holds the registers of its own rule only.
+template <bool DX, int CLS = -1>
 __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane,
                                                    const KintScalar* ks = nullptr) {
+  static_assert(CLS < 0 || !DX, "class-specialized batches are built for values only");
   const double beta_i = 16.0 * ix_rcp(2.0 * vi + 1.0);   // the reciprocal on the integer pipe
   const int rule_i = kint_rule(vi, xi, DX);
   // values: the g nodes' common factor as a log, beta (s0^(v+1/2) beta for
@@ -496,7 +505,7 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     unsigned grp = __ballot_sync(0xffffffffu, rule_i == rule) & rem;
     rem &= ~grp;
     const int ng = rule & 0xff, hr = rule >> 8;
-    if (!DX && ng != 0) {
+    if (!DX && CLS != 0 && ng != 0) {
       const int qb = hr >= 4 ? 58 : 56;
       for (; grp; grp &= grp - 1) {
         const int e = __ffs(grp) - 1;
@@ -506,9 +515,17 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
         const double gk = __shfl_sync(0xffffffffu, gk_i, e);
         double mm;
         uint64_t q;
-        if (hr >= 4) q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
-        else if (ng == 24) q = kint_sumq_g24h40(v, x, beta, gk, lane, mm, ks);
-        else q = kint_sumq_fixed(v, x, beta, gk, ng, hr, lane, mm, ks);
+        if constexpr (CLS == 1 || CLS == 2) {
+          q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
+        } else if constexpr (CLS == 3) {
+          q = kint_sumq_g24h40(v, x, beta, gk, lane, mm, ks);
+        } else if constexpr (CLS == 4 || CLS == 5) {
+          q = kint_sumq_fixed(v, x, beta, gk, ng, hr, lane, mm, ks);
+        } else if constexpr (CLS < 0) {
+          if (hr >= 4) q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
+          else if (ng == 24) q = kint_sumq_g24h40(v, x, beta, gk, lane, mm, ks);
+          else q = kint_sumq_fixed(v, x, beta, gk, ng, hr, lane, mm, ks);
+        }
         if (lane == e) {
           m_i = mm;
           q_i = q;
@@ -523,7 +540,7 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
       const double x = __shfl_sync(0xffffffffu, xi, e);
       const double beta = __shfl_sync(0xffffffffu, beta_i, e);
       double mm, s0, s1 = 0.0;
-      if (ng == 0) {
+      if (CLS == 0 || (CLS < 0 && ng == 0)) {
         kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
       } else if constexpr (DX) {                 // values take the fixed-point sums above
         if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1, ks);

@@ -45,6 +45,27 @@ namespace {
 #ifndef LB_KINT_CTAS_PER_SM
 #define LB_KINT_CTAS_PER_SM 4
 #endif
+// The class-specialized K-integral kernels (FP64 Gauss values, one per rule
+// class of kint_class: split, one-slot s0 = 8, one-slot s0 = 3, packed,
+// fixed 32 and 64 g nodes) each hold only their own rule's registers, so the
+// short rules run with more resident warps.
+#ifndef LB_KINT_CTAS_C0
+#define LB_KINT_CTAS_C0 4
+#endif
+#ifndef LB_KINT_CTAS_C12
+#define LB_KINT_CTAS_C12 6
+#endif
+#ifndef LB_KINT_CTAS_C3
+#define LB_KINT_CTAS_C3 5
+#endif
+#ifndef LB_KINT_CTAS_C45
+#define LB_KINT_CTAS_C45 5
+#endif
+constexpr int kKintCtasCls[6] = {LB_KINT_CTAS_C0, LB_KINT_CTAS_C12, LB_KINT_CTAS_C12,
+                                 LB_KINT_CTAS_C3, LB_KINT_CTAS_C45, LB_KINT_CTAS_C45};
+__host__ __device__ constexpr int kint_ctas_per_sm(int cls) {
+  return cls < 0 ? LB_KINT_CTAS_PER_SM : kKintCtasCls[cls];
+}
 
 // Tile kernel: classify, bin per region in shared memory, evaluate the
 // per-thread expressions (lb_tile.cuh); K fallback pairs go to a global queue
@@ -68,17 +89,17 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
   }
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t t0 = tile * LB_TILE;
-    tile_bin<KIND, DX, T>(S, v, v_stride, x, out, t0, n, mode, forced_region);
-    tile_eval<KIND, DX, T>(S, out, t0, so);
+    tile_bin<KIND, DX, T>(S, v, v_stride, x, t0, n, mode, forced_region);
+    tile_eval<KIND, DX, T>(S, out, t0, n, so);
     if (KIND == KIND_K) {
-      const int c = S.counts[R_FALLBACK];
+      const int c = S.rcount(R_FALLBACK), f0 = S.rbeg(R_FALLBACK);
       if (c > 0) {
         if (tid == 0) S.qbase = atomicAdd(qcount, (unsigned int)c);
         __syncthreads();
         const unsigned int b = S.qbase;
         unsigned cls = 0;                          // quadrature rule classes of the queued pairs
         for (int j = tid; j < c; j += LB_THREADS) {
-          const int li = S.lists[R_FALLBACK][j];
+          const int li = S.list[f0 + j];
           queue[b + j] = (uint32_t)(t0 + li);
           if constexpr (sizeof(T) == 8) {
             if (mode == MODE_TIGHT) cls |= 1u << kint_class(fabs((double)S.sv[li]), (double)S.sx[li], DX);
@@ -94,12 +115,17 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
   }
 }
 
-// K integral: one warp per queued pair, 32 pairs per warp batch.
-template <bool GAUSS, bool DX, typename T>
-__global__ void __launch_bounds__(LB_THREADS, LB_KINT_CTAS_PER_SM)
+// K integral: one warp per queued pair, 32 pairs per warp batch.  CLS = -1:
+// every queued pair; CLS = c (FP64 Gauss values): the pairs of rule class c
+// only, with that class's code alone compiled in (the kernel returns at once
+// when the queue holds none of them).
+template <bool GAUSS, bool DX, typename T, int CLS = -1>
+__global__ void __launch_bounds__(LB_THREADS, kint_ctas_per_sm(CLS))
 lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
                const unsigned int* __restrict__ qcount, const uint32_t* __restrict__ queue) {
   const unsigned int cnt = *qcount;
+  const unsigned present = (GAUSS && sizeof(T) == 8) ? qcount[1] : 0u;
+  if (CLS >= 0 && !(present & (1u << CLS))) return;     // the same for every thread of the grid
   const int lane = threadIdx.x & 31;
   const KintScalar* ks = nullptr;
   const KintScalar32* ks32 = nullptr;
@@ -132,17 +158,18 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
   // its rule classes evaluated one after another).  A phase re-reads the
   // queue and the pairs' (v, x), a few bytes per pair.  A pair's result
   // does not depend on its batch.  A queue of one class, and the other
-  // kernels, take the queue in order, 32 pairs at a time.
+  // kernels, take the queue in order, 32 pairs at a time.  A class kernel
+  // is one phase of this: the host launches the six, costliest first.
   __shared__ uint32_t ring[LB_THREADS / 32][512];
   uint32_t* my = ring[threadIdx.x >> 5];
-  const unsigned present = (GAUSS && sizeof(T) == 8) ? qcount[1] : 0u;
   const bool phased = __popc(present) > 1;
   const int P = phased && (int64_t)cnt >= nwarps * 256 ? 256 : 32;
-  const int nphase = phased ? 6 : 1;
+  const int nphase = (phased && CLS < 0) ? 6 : 1;
   const unsigned lt = (1u << lane) - 1u;
   unsigned head = 0, nb = 0;                       // ring: first entry, entries held (warp-uniform)
   for (int ph = 0; ph < nphase; ++ph) {
-    const int c = phased ? (ph == 0 ? 0 : 6 - ph) : -1;   // costliest class first; -1: every pair
+    // costliest class first; -1: every pair
+    const int c = !phased ? -1 : (CLS >= 0 ? CLS : (ph == 0 ? 0 : 6 - ph));
     if (phased && !(present & (1u << c))) continue;
     for (int64_t b = warp * P;; b += nwarps * P) {
       const bool last = b >= (int64_t)cnt;
@@ -168,7 +195,7 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
         const int64_t idx = (int64_t)my[(head + (lane < k ? lane : 0)) & 511u];
         const T vi = fabs(v[idx * v_stride]);
         const T xi = x[idx];
-        const T val = kint_warp_batch<DX, T>(vi, xi, k, lane, GAUSS, ks, ks32);
+        const T val = kint_warp_batch<DX, T, CLS>(vi, xi, k, lane, GAUSS, ks, ks32);
         if (lane < k) out[idx] = val;
         head += k;
         nb -= k;
@@ -362,6 +389,28 @@ lb_status validate(lb_dtype dtype, const void* v, int64_t v_stride, const void* 
   return LB_OK;
 }
 
+template <typename T, int CLS>
+lb_status launch_kint_class(int sms, cudaStream_t st, const T* v, int64_t v_stride, const T* x, T* out,
+                            const unsigned int* qcount, const uint32_t* queue) {
+  const int grid = sms * 2 * kint_ctas_per_sm(CLS);
+  return launch(PS_KINT, st, [&] {
+    lb_kint_kernel<true, false, T, CLS><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, qcount, queue);
+  });
+}
+
+// The six class kernels of the FP64 Gauss values, in the order of the phases.
+template <typename T>
+lb_status launch_kint_classes(int sms, cudaStream_t st, const T* v, int64_t v_stride, const T* x, T* out,
+                              const unsigned int* qcount, const uint32_t* queue) {
+  lb_status s = launch_kint_class<T, 0>(sms, st, v, v_stride, x, out, qcount, queue);
+  if (s == LB_OK) s = launch_kint_class<T, 5>(sms, st, v, v_stride, x, out, qcount, queue);
+  if (s == LB_OK) s = launch_kint_class<T, 4>(sms, st, v, v_stride, x, out, qcount, queue);
+  if (s == LB_OK) s = launch_kint_class<T, 3>(sms, st, v, v_stride, x, out, qcount, queue);
+  if (s == LB_OK) s = launch_kint_class<T, 2>(sms, st, v, v_stride, x, out, qcount, queue);
+  if (s == LB_OK) s = launch_kint_class<T, 1>(sms, st, v, v_stride, x, out, qcount, queue);
+  return s;
+}
+
 // Largest chunk handled with one queue: the queue holds 32-bit offsets.
 const int64_t kChunk = (int64_t)1 << 26;
 
@@ -408,13 +457,23 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
       lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount, queue);
     });
     if (status != LB_OK) break;
-    const int kgrid = sms * 8;
-    status = launch(PS_KINT, st, [&] {
-      if (mode == MODE_TIGHT)
-        lb_kint_kernel<true, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
-      else
-        lb_kint_kernel<false, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
-    });
+    bool done = false;
+    if constexpr (sizeof(T) == 8 && !DX) {
+      if (mode == MODE_TIGHT) {
+        // one kernel per rule class, costliest first (the phases of a mixed queue)
+        status = launch_kint_classes<T>(sms, st, vc, v_stride, xc, oc, qcount, queue);
+        done = true;
+      }
+    }
+    if (!done) {
+      const int kgrid = sms * 2 * LB_KINT_CTAS_PER_SM;
+      status = launch(PS_KINT, st, [&] {
+        if (mode == MODE_TIGHT)
+          lb_kint_kernel<true, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
+        else
+          lb_kint_kernel<false, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
+      });
+    }
   }
   if (!scratch) cudaFreeAsync(ws, st);
   return status;

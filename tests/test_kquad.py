@@ -113,3 +113,75 @@ def test_one_slot_tables():
         assert min(T["lb_kq_%s_s" % tag]) > s0
         w = sum(mp.exp(c) for c in T["lb_kq_%s_c" % tag])
         assert abs(w / mp.exp(-s0) - 1) < 1e-15
+
+
+def _g_fixed_dx(v, x, N):
+    """The g part of a fixed rule and of its x-derivative's weighted sum:
+    (beta sum_j F_j, beta sum_j F_j / (s_j + 2x))."""
+    beta = mp.mpf(16) / (2 * v + 1)
+    s0 = s1 = mp.mpf(0)
+    for lu, c in zip(T["lb_kq_g%d_logu" % N], T["lb_kq_g%d_c" % N]):
+        ub = mp.exp(beta * lu)
+        t = mp.exp(c + (v - mp.mpf(0.5)) * mp.log(2 * x + ub) - ub)
+        s0 += t
+        s1 += t / (ub + 2 * x)
+    return beta * s0, beta * s1
+
+
+def _h_dx(v, x, tag):
+    s0 = s1 = mp.mpf(0)
+    for s, y, c in zip(T["lb_kq_%s_s" % tag], T["lb_kq_%s_y" % tag], T["lb_kq_%s_c" % tag]):
+        t = mp.exp(c + (v - mp.mpf(0.5)) * (y + mp.log(s + 2 * x)))
+        s0 += t
+        s1 += t / (s + 2 * x)
+    return s0, s1
+
+
+# The x-derivative's rules (they keep the fixed and packed rules; no one-slot
+# rule): d/dx log K = -(v/x + 1) + (2v - 1) <1/(s + 2x)>, the mean weighted by
+# F over the nodes (dF/dx = F (2v - 1)/(s + 2x)), with the orders and
+# arguments each rule serves, including the small orders at 0.25 <= x < 0.6
+# that take 64 g nodes for the derivative.
+DX_RULES = {
+    "g32+hl32": ((32, "hl32"), [0.0, 0.05, 0.1, 0.5, 0.9, 1.0, 1.2], [0.6, 1.0, 3.0, 7.3, 25.0, 30.0]),
+    "g32+hl32 (v >= 0.1)": ((32, "hl32"), [0.1, 0.3, 0.5, 0.8, 0.89], [0.25, 0.3, 0.45]),
+    "g64+hl32": ((64, "hl32"), [0.0, 1e-3, 0.05, 0.099], [0.25, 0.3, 0.45, 0.59]),
+    "g64+hl32 (x < 0.25)": ((64, "hl32"), [0.4, 0.55, 0.89], [1e-3, 0.01, 0.05, 0.2]),
+    "g24+hl40": ((24, "hl40"), [1.21, 1.5, 2.5, 3.3, 5.0], [1e-300, 1e-6, 0.04, 1.0, 9.0, 25.0]),
+    "g32+hq32": ((32, "hq32"), [5.01, 8.5, 12.0, 16.0], [1e-300, 1e-8, 0.01, 1.0, 12.0, 25.0]),
+}
+
+
+@pytest.mark.parametrize("name", list(DX_RULES))
+def test_derivative_rule_error_map(name):
+    """Each derivative rule, summed from its double table entries in 30-digit
+    arithmetic, against the oracle's d/dx log K (the Bessel ratio of DLMF
+    10.29.2): relative error below 2e-16 (worst measured: 1.2e-16)."""
+    (N, tag), vs, xs = DX_RULES[name]
+    V, X = np.meshgrid(np.array(vs), np.array(xs), indexing="ij")
+    V, X = V.ravel(), X.ravel()
+    ref = oracle.dlog_k_dx(V, X)
+    with mp.workdps(30):
+        for v, x, r in zip(V, X, ref):
+            vm, xm = mp.mpf(v), mp.mpf(x)
+            a0, a1 = _g_fixed_dx(vm, xm, N)
+            b0, b1 = _h_dx(vm, xm, tag)
+            d = -(vm / xm + 1) + (2 * vm - 1) * (a1 + b1) / (a0 + b0)
+            err = float(abs(d - mp.mpf(r)) / abs(mp.mpf(r)))
+            assert err < 2e-16, (name, v, x, err)
+
+
+def test_derivative_needs_64_nodes_below_x_0_6():
+    """The reason for the derivative's boundary: at v = 0, x = 0.25 the 32-node
+    g rule leaves ~7e-15 in d/dx log K, the 64-node rule < 1e-16."""
+    v, x = 0.0, 0.25
+    ref = oracle.dlog_k_dx(np.array([v]), np.array([x]))[0]
+    with mp.workdps(30):
+        vm, xm = mp.mpf(v), mp.mpf(x)
+        errs = []
+        for N in (32, 64):
+            a0, a1 = _g_fixed_dx(vm, xm, N)
+            b0, b1 = _h_dx(vm, xm, "hl32")
+            d = -(vm / xm + 1) + (2 * vm - 1) * (a1 + b1) / (a0 + b0)
+            errs.append(float(abs(d - mp.mpf(ref)) / abs(mp.mpf(ref))))
+    assert errs[0] > 1e-15 and errs[1] < 1e-16
