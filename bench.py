@@ -27,6 +27,18 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "Gevals/s (log I_v and log K_v, FP64)"
+
+# DRAM bytes (read + write) per benchmark step of each kernel, from one ncu
+# capture of every launch of one full-size step (the launch list of
+# profiles/launches_paper_sweep_fp64.md, with dram__bytes_read.sum and
+# dram__bytes_write.sum); empty when the kernels changed since.
+NCU_DRAM_BYTES_PER_STEP = {}
+# Pipe utilisation of each kernel from ncu --set full on a small case of the
+# same workload (profiles/lb_tiles_kernel_sweep_small.md,
+# profiles/lb_kint_kernel_sweep_small.md): share of peak issue of the FP64
+# pipe, the ALU pipe and the XU (special-function) pipe; empty when stale.
+NCU_PIPES = {}
+NCU_PIPES_FP32 = {}
 UNIT = "Gevals/s"
 WORKLOAD = "paper-shaped sweep: v=2^0..2^10 x 20M x~U[1,100] per order, log I + log K, per-order + mixed-order calls"
 
@@ -173,8 +185,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--err-sample", type=int, default=4000, help="oracle-checked outputs per call type")
-    ap.add_argument("--serve-requests", type=int, default=4000,
+    ap.add_argument("--serve-requests", type=int, default=100_000,
                     help="requests in the serving measurement (0 = skip)")
+    ap.add_argument("--serve-per-call-requests", type=int, default=5000,
+                    help="requests of the one-call-per-request arm at the offered loads")
     ap.add_argument("--robust-n", type=int, default=64 << 20,
                     help="pairs of the robustness sweep measurement (0 = skip)")
     ap.add_argument("--no-paper-tables", action="store_true",
@@ -192,7 +206,8 @@ def main():
     import torch
     import paper_2409_08729_gb300 as lb
     from paper_2409_08729_gb300 import _binding as B
-    from benchmarks import workmodel as WM
+    from benchmarks import optable as OT
+    from benchmarks import work as WK
     from paper_2409_08729_gb300.workloads import SWEEP_ORDERS, sweep_device
     lb.build_library()
 
@@ -225,9 +240,9 @@ def main():
 
     evals_per_step = 4 * n_all
 
-    # FP64 roofline of this GPU, measured live
+    # FP64 rates of this GPU, measured live (the DFMA rate checks the peak
+    # derived from unit counts and clock)
     rates = B.measure_fp64(sp)
-    slot_costs = WM.set_costs(rates)
 
     for _ in range(args.warmup):
         step(x_all, v_mixed, outs)
@@ -354,11 +369,14 @@ def main():
         torch.cuda.synchronize()
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
+        B.profile_enable(True)
         g0.record(stream)
         for _ in range(args.steps):
             step32()
         g1.record(stream)
         torch.cuda.synchronize()
+        prof32 = B.profile_read()
+        B.profile_enable(False)
         ms32 = max_over_ranks(g0.elapsed_time(g1), pg, dev)
         fp32 = {"value": job_gevals(evals_per_step, args.steps, world, ms32), "unit": UNIT,
                 "ms_per_step": ms32 / args.steps, "dtype": "f32 inputs/outputs, FP32-pipe evaluation"}
@@ -375,67 +393,79 @@ def main():
             fp32["max_rel_err_mixed_calls"] = e_max
         del x32, v32, o32
 
-    # ---- roofline of the dominant kernel (FP64 pipe) ----
-    regions_k = lb.classify("k", v_mixed, x_all).cpu().numpy()
-    regions_i = lb.classify("i", v_mixed, x_all).cpu().numpy()
-    vm_h = v_mixed.cpu().numpy()
-    x_h = x_all.cpu().numpy()
-    per_order_k = np.repeat(np.asarray(SWEEP_ORDERS), n1)
-    peak_flops = 2.0 * rates["dfma"]
-    dominant = max(prof.items(), key=lambda kv: kv[1][2])
-    name, (nl, ntimed, kms) = dominant
-    roof = None
-    # algorithmic work of each kernel over the timed region (one step, then x steps)
-    per_order_t = orders.repeat_interleave(n1)
-    fb_mix = regions_k == 2
-    fb_per = lb.classify("k", per_order_t, x_all).cpu().numpy() == 2
-    ri_per = lb.classify("i", per_order_t, x_all).cpu().numpy()
-    rk_per = lb.classify("k", per_order_t, x_all).cpu().numpy()
-    del per_order_t
-    kint_slots = (WM.kint_slots(vm_h[fb_mix], x_h[fb_mix]).sum()
-                  + WM.kint_slots(per_order_k[fb_per], x_h[fb_per], scalar=True).sum())
-    rng_w = np.random.default_rng(0)
-
-    def sampled_sum(fn, sel_idx, vv):
-        if sel_idx.size == 0:
-            return 0.0
-        sub = sel_idx[rng_w.integers(0, sel_idx.size, min(sel_idx.size, 1_000_000))]
-        return float(np.mean(fn(vv[sub], x_h[sub]))) * sel_idx.size
-
-    tiles_slots = 0.0
-    # per-order calls pass one order for all pairs (the scalar-order path)
-    for kind_regs in ((regions_i, vm_h, True, False), (ri_per, per_order_k, True, True),
-                      (regions_k, vm_h, False, False), (rk_per, per_order_k, False, True)):
-        regs, vv, is_i, scalar = kind_regs
-        for rid in (0, 1, 2, 4, 5, 6, 7):
-            if rid == 2 and not is_i:
+    # ---- rooflines: algorithmic work of one step from the fixed operation
+    # table (benchmarks/optable.py), per kernel, over the CUDA-event time of
+    # the kernel's launches in the timed region ----
+    wk = {}
+    for kind in ("i", "k"):
+        for k in range(nv):
+            WK.merge(wk, WK.call_work(kind, orders[k:k + 1], x_all[k * n1:(k + 1) * n1], seed=k))
+        WK.merge(wk, WK.call_work(kind, v_mixed, x_all, seed=100))
+    kern_ops = {"lb_tiles_kernel": WK.ops_of(wk, "tiles"), "lb_kint_kernel": WK.ops_of(wk, "kint")}
+    fb_pairs = sum(c for c, _ in wk["kint"].values())
+    # algorithmic bytes per step: per pair x (and v when one per pair) read
+    # and the result written (8 B each); K-integral pairs: the tile kernel
+    # writes a 4 B queue entry, the K-integral kernel reads the entry, v and
+    # x and writes the result
+    alg_bytes = {"lb_tiles_kernel": 2 * (nv * n1 * 16 + n_all * 24) - fb_pairs * 4,
+                 "lb_kint_kernel": fb_pairs * 4 + fb_pairs * 20}
+    kernels = {}
+    for kname, ops in kern_ops.items():
+        nl, ntimed, kms = prof.get(kname, (0, 0, 0.0))
+        if not ntimed or kms <= 0:
+            continue
+        ach = ops * args.steps / (kms / 1e3)
+        traffic = NCU_DRAM_BYTES_PER_STEP.get(kname)
+        kernels[kname] = {"launches": ntimed, "ms": kms, "avg_launch_ms": kms / ntimed,
+                          "ops_per_step": ops, "achieved": ach / 1e9, "frac": ach / OT.PEAK_FP64_OPS,
+                          "algorithmic_bytes_per_launch": alg_bytes[kname] * args.steps / ntimed,
+                          "traffic": traffic[0] * args.steps / ntimed if traffic else None,
+                          "ncu": NCU_PIPES.get(kname)}
+    name = max(kernels, key=lambda k: kernels[k]["ms"])
+    kd = kernels[name]
+    roof = {"bound": "alu", "kernel": name, "achieved": kd["achieved"], "peak": OT.PEAK_FP64_OPS / 1e9,
+            "unit": "G FP64 op/s", "frac": kd["frac"], "traffic": kd["traffic"],
+            "algorithmic_bytes": kd["algorithmic_bytes_per_launch"], "launches": kd["launches"],
+            "avg_launch_ms": kd["avg_launch_ms"],
+            "work": "FP64 operations of the method (benchmarks/optable.py) at per-pair term and node counts; "
+                    "library calls (log, exp, rcp, rsqrt, lgamma) not priced",
+            "peak_source": "152 SMs x 2 FP64 op/clk x 2.07 GHz; live DFMA microbenchmark %.1f G/s"
+                           % (rates["dfma"] / 1e9),
+            "ncu": kd["ncu"]}
+    work_by_region = {kern: {r: {"pairs": c, "ops_per_pair": m} for r, (c, m) in regs.items()}
+                      for kern, regs in wk.items()}
+    if fp32 is not None:
+        wk32 = {}
+        x32 = x_all.float()
+        v32 = v_mixed.float()
+        ord32 = orders.float()
+        for kind in ("i", "k"):
+            for k in range(nv):
+                WK.merge(wk32, WK.call_work(kind, ord32[k:k + 1], x32[k * n1:(k + 1) * n1], fp32=True, seed=k))
+            WK.merge(wk32, WK.call_work(kind, v32, x32, fp32=True, seed=100))
+        del x32, v32
+        k32 = {}
+        for kname, kern in (("lb_tiles_kernel", "tiles"), ("lb_kint_kernel", "kint")):
+            nl, ntimed, kms = prof32.get(kname, (0, 0, 0.0))
+            if not ntimed or kms <= 0:
                 continue
-            sel = np.flatnonzero(regs == rid)
-            tiles_slots += sampled_sum(lambda a, b, r=rid, sc=scalar: WM.region_slots(r, a, b, sc), sel, vv)
-    work_slots = {"lb_kint_kernel": kint_slots, "lb_tiles_kernel": tiles_slots}
-    # DRAM traffic of the K-integral kernel: 37 B per queued pair (one ncu
-    # capture, profiles/lb_kint_kernel_sweep_small.md), scaled to the pairs of
-    # an average launch; it grows in proportion (per-pair gathers only).
-    kint_pairs_per_launch = (fb_mix.sum() + fb_per.sum()) * args.steps / max(prof["lb_kint_kernel"][1], 1)
-    # DRAM traffic of the tiles kernel, from one ncu capture at 1M arguments
-    # per order (profiles/lb_tiles_kernel_sweep_small.md): 9.1 B per pair for
-    # a one-order call (x read; the results were still in L2 when it ended)
-    # and 16.3 B read + 5.2 B written per pair for a mixed-order call. Reads
-    # grow in proportion; the writes are a lower bound at full size.
-    tiles_bytes = 2 * args.steps * n_all * (9.1 + 16.3 + 5.2)
-    traffic = {"lb_kint_kernel": 37.0 * kint_pairs_per_launch,
-               "lb_tiles_kernel": tiles_bytes / max(prof["lb_tiles_kernel"][1], 1)}
-    if name in work_slots:
-        work = 2.0 * work_slots[name] * args.steps
-        roof = {"bound": "alu", "kernel": name, "achieved": work / (kms / 1e3) / 1e9,
-                "peak": peak_flops / 1e9, "unit": "GFLOP/s", "frac": (work / (kms / 1e3)) / peak_flops,
-                "traffic": traffic.get(name), "launches": ntimed, "avg_launch_ms": kms / max(ntimed, 1),
-                "peak_source": "FP64 DFMA rate measured live by logbessel_measure_fp64 (x2 flops/FMA)"}
-    other = {k: {"achieved_gflops": 2.0 * w * args.steps / (prof[k][2] / 1e3) / 1e9 if prof.get(k, (0, 0, 0))[2] else None}
-             for k, w in work_slots.items()}
+            ops = WK.ops_of(wk32, kern)
+            ach = ops * args.steps / (kms / 1e3)
+            k32[kname] = {"launches": ntimed, "ms": kms, "ops_per_step": ops, "achieved": ach / 1e9,
+                          "frac_fp32_pipe": ach / OT.PEAK_FP32_OPS, "ncu": NCU_PIPES_FP32.get(kname)}
+        n32 = max(k32, key=lambda k: k32[k]["ms"])
+        fp32["roofline"] = {"bound": "alu", "kernel": n32, "achieved": k32[n32]["achieved"],
+                            "peak": OT.PEAK_FP32_OPS / 1e9, "unit": "G FP32 op/s",
+                            "frac": k32[n32]["frac_fp32_pipe"], "traffic": None,
+                            "peak_source": "152 SMs x 128 FP32 op/clk x 2.07 GHz",
+                            "fp64_pipe": "no FP64 operations on this path (FP32 everywhere); ncu: see ncu"}
+        fp32["kernels"] = k32
+        fp32["work_by_region"] = {kern: {r: {"pairs": c, "ops_per_pair": m} for r, (c, m) in regs.items()}
+                                  for kern, regs in wk32.items()}
     mix = {}
-    for nm, rid in (("mu20", 0), ("u13", 1), ("fallback", 2), ("u4", 5), ("u6", 6), ("u9", 7)):
-        mix[nm] = {"i": float(np.mean(regions_i == rid)), "k": float(np.mean(regions_k == rid))}
+    for nm, (c, _) in wk["tiles"].items():
+        mix[nm] = c / (4 * n_all)
+    mix["k_integral"] = fb_pairs / (4 * n_all)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -444,9 +474,8 @@ def main():
                        "mode": args.mode, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (>=160 MB per call), no flush"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clocks,
-            "kernels": {k: {"launches": v[1], "ms": v[2], **other.get(k, {})} for k, v in prof.items()},
-            "region_mix_mixed_call": mix,
-            "fp64_rates": {k: v / 1e9 for k, v in rates.items()}, "slot_costs": slot_costs}
+            "kernels": kernels, "work_by_region": work_by_region, "region_mix_step": mix,
+            "fp64_rates": {k: v / 1e9 for k, v in rates.items()}}
     line["max_rel_err"] = acc
     line["fp32_mixed"] = fp32
     del outs
@@ -463,7 +492,8 @@ def main():
         torch.cuda.empty_cache()
     if rank == 0 and args.serve_requests > 0:
         from benchmarks import servebench
-        line["serving"] = servebench.run(n_req=args.serve_requests, seed=0, device=str(dev))
+        line["serving"] = servebench.run(n_req=args.serve_requests, seed=0, device=str(dev),
+                                         load=[0.5, 0.8, 0.95], per_call_requests=args.serve_per_call_requests)
     if rank == 0:
         r, threads, n = time_oracle(args.cpu_per_v)
         line["cpu_baseline"] = {"value": r / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
