@@ -185,6 +185,13 @@ __device__ __forceinline__ int series_terms(float v, float x) {
   return n;
 }
 
+// 1/k and (2k-1)^2/k for k = 1..20, the constants of the term ratios of
+// mu_K, for a rolled loop over the warp's own number of terms (entry 0
+// unused).  A fully unrolled loop with the terms above n switched off by a
+// predicate would still issue every term's FP64 instructions.
+static __constant__ double kMuInvK[21] = {0.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0, 1.0 / 10.0, 1.0 / 11.0, 1.0 / 12.0, 1.0 / 13.0, 1.0 / 14.0, 1.0 / 15.0, 1.0 / 16.0, 1.0 / 17.0, 1.0 / 18.0, 1.0 / 19.0, 1.0 / 20.0};
+static __constant__ double kMuOddK[21] = {0.0, 1.0 / 1.0, 9.0 / 2.0, 25.0 / 3.0, 49.0 / 4.0, 81.0 / 5.0, 121.0 / 6.0, 169.0 / 7.0, 225.0 / 8.0, 289.0 / 9.0, 361.0 / 10.0, 441.0 / 11.0, 529.0 / 12.0, 625.0 / 13.0, 729.0 / 14.0, 841.0 / 15.0, 961.0 / 16.0, 1089.0 / 17.0, 1225.0 / 18.0, 1369.0 / 19.0, 1521.0 / 20.0};
+
 // mu_K with the lane's term count n given (at most K); all 32 lanes of the
 // warp call it together.
 template <int KIND, int K>
@@ -194,15 +201,12 @@ __device__ __forceinline__ double mu_expr_n(double v, double x, int n) {
   const double rx = ix_rcp_call(8.0 * x);                             // 1/(8x) on the integer pipe
   const double inv8x = (KIND == KIND_I) ? -rx : rx;                   // the sign s folded in
   double P = 1.0;
-  // Unrolled, so 1/k and (2k-1)^2/k are constants and each term costs three
-  // FP64 operations: a = mu/k - (2k-1)^2/k, P = 1 + (a s/(8x)) P.  Terms
-  // above n are skipped by a warp-uniform predicate.
-#pragma unroll
-  for (int k = K; k >= 1; --k) {
-    if (k <= n) {
-      const double a = fma(mu, 1.0 / (double)k, -(double)((2 * k - 1) * (2 * k - 1)) / (double)k);
-      P = fma(a * inv8x, P, 1.0);
-    }
+  // Three FP64 operations per term: a = mu/k - (2k-1)^2/k, P = 1 + (a s/(8x)) P,
+  // for the warp's n terms only.
+#pragma unroll 1
+  for (int k = n; k >= 1; --k) {
+    const double a = fma(mu, kMuInvK[k], -kMuOddK[k]);
+    P = fma(a * inv8x, P, 1.0);
   }
   // log(S / sqrt(2 pi x)) = log(S^2 / (2 pi x)) / 2 and
   // log(S sqrt(pi / (2x))) = log(S^2 pi / (2x)) / 2, with 1/x = 8 |inv8x|:
@@ -408,13 +412,11 @@ __device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
 
 template <int KIND>
 __device__ __forceinline__ double mu_expr_so(const ScalarOrder& so, double x, int n) {
-  constexpr int K = 20;
   n = __reduce_max_sync(0xffffffffu, n);
   const double w = ix_rcp_call(8.0 * x);
   double P = 0.0;
-#pragma unroll
-  for (int k = K; k >= 0; --k)
-    if (k <= n) P = fma(P, w, so.mu[k]);
+#pragma unroll 1
+  for (int k = n; k >= 0; --k) P = fma(P, w, so.mu[k]);   // the warp's n terms only
   const double S2 = P * P;
   if (KIND == KIND_I) return fma(0.5, ix_log_call(S2 * w * (8.0 / kTwoPi)), x);
   return fma(0.5, ix_log_call(S2 * w * (4.0 * kPi)), -x);

@@ -63,15 +63,18 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
 // h rules 4 and 5 are the one-slot rules of kint_sum_one (22 g + 10 h
 // nodes, s0 = 8, for 2 <= v < 7; 12 + 20, s0 = 3, for 7 <= v <= 16.5), for
 // values only: their error map covers log K, not its x-derivative.
-// The x-derivative, a weighted mean of 1/(s + 2x) over the nodes, keeps the
-// 64-node g rule for v < 0.1 up to x = 0.6: there the 32-node rule leaves up
-// to 7e-15 relative error in the derivative (v = 0, x = 0.25), the 64-node
-// rule below 1e-16 (error map of the rules against the oracle's Bessel ratio).
+// The x-derivative, a weighted mean of 1/(s + 2x) over the nodes, moves both
+// boundaries up for v < 0.1: 64 g nodes up to x = 0.6 and the split rule up
+// to x = 5e-3.  There the 32-node rule leaves up to 7e-15 relative error in
+// the derivative (v = 0, x = 0.25) and the 64-node rule 8e-15 (v = 0,
+// x = 1e-3); the rules taken instead stay below 1.2e-16 (error map of the
+// derivative rules against the oracle's Bessel ratio).
 __device__ __forceinline__ int kint_rule(double v, double x, bool dx) {
   if (!dx && v >= 2.0 && v <= 16.5) return v < 7.0 ? (22 | (4 << 8)) : (12 | (5 << 8));
   if (v > 1.2 && v <= 5.0) return 24 | (3 << 8);
-  const double x32 = (dx && v < 0.1) ? 0.6 : 0.25;
-  const int ng = (v >= 0.9 || x >= x32) ? 32 : ((v >= 0.4 || x >= 1e-3) ? 64 : 0);
+  const bool dsmall = dx && v < 0.1;
+  const double x32 = dsmall ? 0.6 : 0.25, xsplit = dsmall ? 5e-3 : 1e-3;
+  const int ng = (v >= 0.9 || x >= x32) ? 32 : ((v >= 0.4 || x >= xsplit) ? 64 : 0);
   const int hr = (v <= 1.2) ? 0 : ((v <= 5.0) ? 1 : 2);
   return ng | (hr << 8);
 }
@@ -513,8 +516,8 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
         const double x = __shfl_sync(0xffffffffu, xi, e);
         const double beta = __shfl_sync(0xffffffffu, beta_i, e);
         const double gk = __shfl_sync(0xffffffffu, gk_i, e);
-        double mm;
-        uint64_t q;
+        double mm = 0.0;
+        uint64_t q = 0;
         if constexpr (CLS == 1 || CLS == 2) {
           q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
         } else if constexpr (CLS == 3) {

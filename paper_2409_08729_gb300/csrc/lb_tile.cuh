@@ -29,11 +29,14 @@
 
 namespace lb {
 
-// List keys.  mu_20 takes one key per term count n = 1..20 and the power
-// series one per band of six counts (1-6, ..., 85-90), so that sorting by key
-// sorts each region by the number of terms its lanes sum (FP64 values; the
-// other forms use the first key of the region).  Keys of a region are
-// adjacent; regions come in the order of their list ranges.
+// List keys.  mu_20 (FP64 values) takes one key per term count n = 1..20,
+// found while binning (an unrolled single-precision pass); the power series
+// one key per band of x, log-spaced, 3 log2(1 + x) (its term count grows with
+// x: rank correlation 0.98), because its exact count is a loop of up to 90
+// steps that is cheaper once per 32-pair chunk than once per item round.  So
+// each region's pairs come ordered by the number of terms their lanes sum.
+// Keys of a region are adjacent; regions come in the order of their list
+// ranges.
 enum TileKey {
   KEY_MU20 = 0,                  // .. KEY_MU20 + 19
   KEY_U13 = 20,
@@ -59,7 +62,7 @@ struct TileShared {
   T sx[LB_TILE];
   T sres[LB_TILE];                                 // results, stored coalesced at the end of the tile
   uint16_t list[LB_TILE];                          // tile offsets of the pairs to evaluate, sorted by key
-  uint8_t nt[LB_TILE];                             // estimated term count (mu_20, series; FP64 values)
+  uint8_t nt[LB_TILE];                             // estimated term count (mu_20; FP64 values)
   uint8_t keep[LB_TILE];                           // 1: sres holds this pair's result
   uint16_t wcount[LB_ITEMS][LB_THREADS / 32][NKEYS];   // pairs per (item round, warp, key), then offsets
   int kbeg[NKEYS + 1];                             // start of each key's range in list
@@ -122,8 +125,8 @@ __device__ __forceinline__ T tile_expr(int r, T v, T x, int n) {
   }
 }
 
-// List key of a classified pair, and its term count in *n (FP64 values of
-// mu_20 and of the power series; 0 otherwise).
+// List key of a classified pair, and the term count of mu_20 in *n (FP64
+// values; 0 otherwise).
 template <int KIND, bool DX, typename T>
 __device__ __forceinline__ int tile_key(int r, T v, T x, int* n) {
   *n = 0;
@@ -132,11 +135,9 @@ __device__ __forceinline__ int tile_key(int r, T v, T x, int* n) {
       *n = mu_terms<20>((float)v, (float)x);
       return KEY_MU20 + *n - 1;
     }
-    if (KIND == KIND_I && r == R_FALLBACK) {
-      *n = series_terms((float)v, (float)x);
-      return KEY_FB + (*n - 1) / 6;
-    }
   }
+  if (KIND == KIND_I && r == R_FALLBACK)
+    return KEY_FB + min(14, (int)(3.0f * __log2f(1.0f + (float)x)));
   return region_key_first(r);
 }
 
@@ -296,7 +297,9 @@ __device__ __forceinline__ void tile_eval_region(TileShared<T>& S, int lane, con
     const int j0 = id << 5, j = j0 + lane;
     const bool ok = j < c;
     const int li = S.list[b0 + (ok ? j : j0)];
-    const int nterm = S.nt[li];
+    int nterm = S.nt[li];
+    if constexpr (sizeof(T) == 8 && !DX && KIND == KIND_I && R == R_FALLBACK)
+      nterm = series_terms((float)(so ? so->v : (double)S.sv[li]), (float)S.sx[li]);
     T val;
     if constexpr (sizeof(T) == 8 && !DX) {
       if (so) val = tile_expr_so<KIND>(R, *so, S.sx[li], nterm);

@@ -48,18 +48,20 @@ namespace {
 // The class-specialized K-integral kernels (FP64 Gauss values, one per rule
 // class of kint_class: split, one-slot s0 = 8, one-slot s0 = 3, packed,
 // fixed 32 and 64 g nodes) each hold only their own rule's registers, so the
-// short rules run with more resident warps.
+// short rules run with more resident warps (budgets measured on the sweep and
+// the robustness sweep: 4, 8, 8, 6, 6, 6 CTAs per SM beat 4 everywhere by
+// 1-2 %; the split rule keeps 4).
 #ifndef LB_KINT_CTAS_C0
 #define LB_KINT_CTAS_C0 4
 #endif
 #ifndef LB_KINT_CTAS_C12
-#define LB_KINT_CTAS_C12 6
+#define LB_KINT_CTAS_C12 8
 #endif
 #ifndef LB_KINT_CTAS_C3
-#define LB_KINT_CTAS_C3 5
+#define LB_KINT_CTAS_C3 6
 #endif
 #ifndef LB_KINT_CTAS_C45
-#define LB_KINT_CTAS_C45 5
+#define LB_KINT_CTAS_C45 6
 #endif
 constexpr int kKintCtasCls[6] = {LB_KINT_CTAS_C0, LB_KINT_CTAS_C12, LB_KINT_CTAS_C12,
                                  LB_KINT_CTAS_C3, LB_KINT_CTAS_C45, LB_KINT_CTAS_C45};

@@ -10,10 +10,11 @@ import paper_2409_08729_gb300 as lb
 from paper_2409_08729_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
-# Relative tolerance of the FP64 derivative (no dedicated bound in the paper):
-# the derivative of each expression carries the rounding of its terms, a few
-# times that of the value.
-TOL_DX = 2e-14
+# Relative tolerance of the FP64 derivative, the gate of the values (the paper
+# gives no bound for derivatives).  The derivative rules of the K integral are
+# within 1.2e-16 of the oracle's Bessel ratio (error map in test_kquad.py);
+# the worst measured end to end on these sets is 2.1e-15.
+TOL_DX = 4e-15
 
 
 def _dx(kind, v, x, dev, scalar_v=False):

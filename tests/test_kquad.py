@@ -145,7 +145,7 @@ def _h_dx(v, x, tag):
 DX_RULES = {
     "g32+hl32": ((32, "hl32"), [0.0, 0.05, 0.1, 0.5, 0.9, 1.0, 1.2], [0.6, 1.0, 3.0, 7.3, 25.0, 30.0]),
     "g32+hl32 (v >= 0.1)": ((32, "hl32"), [0.1, 0.3, 0.5, 0.8, 0.89], [0.25, 0.3, 0.45]),
-    "g64+hl32": ((64, "hl32"), [0.0, 1e-3, 0.05, 0.099], [0.25, 0.3, 0.45, 0.59]),
+    "g64+hl32": ((64, "hl32"), [0.0, 1e-3, 0.05, 0.099], [5e-3, 0.01, 0.1, 0.25, 0.3, 0.45, 0.59]),
     "g64+hl32 (x < 0.25)": ((64, "hl32"), [0.4, 0.55, 0.89], [1e-3, 0.01, 0.05, 0.2]),
     "g24+hl40": ((24, "hl40"), [1.21, 1.5, 2.5, 3.3, 5.0], [1e-300, 1e-6, 0.04, 1.0, 9.0, 25.0]),
     "g32+hq32": ((32, "hq32"), [5.01, 8.5, 12.0, 16.0], [1e-300, 1e-8, 0.01, 1.0, 12.0, 25.0]),
@@ -185,3 +185,46 @@ def test_derivative_needs_64_nodes_below_x_0_6():
             d = -(vm / xm + 1) + (2 * vm - 1) * (a1 + b1) / (a0 + b0)
             errs.append(float(abs(d - mp.mpf(ref)) / abs(mp.mpf(ref))))
     assert errs[0] > 1e-15 and errs[1] < 1e-16
+
+
+def _split_dx_above_1e3(v, x):
+    """The split g rule for 1e-3 <= x < 5e-3 (y1 = log(128 x) > -4, so of its
+    log-s panels only [y1, 0] is non-empty): 64 nodes on [0, s1], s = s1 u^beta,
+    16 Gauss-Legendre nodes in y = log s on [y1, 0], the 32 h nodes; the
+    derivative's weighted sums as in _g_fixed_dx."""
+    beta = mp.mpf(16) / (2 * v + 1)
+    s1 = 128 * x
+    y1 = mp.log(s1)
+    s0 = s1w = mp.mpf(0)
+    for lu, c in zip(T["lb_kq_g64_logu"], T["lb_kq_g64_c"]):
+        r = mp.exp(beta * lu)
+        s = s1 * r
+        t = beta * mp.exp(2 * v * y1 + c + (v - mp.mpf(0.5)) * mp.log(r + mp.mpf(1) / 64) - s)
+        s0 += t
+        s1w += t / (s + 2 * x)
+    for tt, lw in zip(T["lb_kq_gl16_t"], T["lb_kq_gl16_logw"]):
+        y = y1 * (1 - tt)
+        s = mp.exp(y)
+        t = mp.exp(lw + mp.log(-y1) + (v + mp.mpf(0.5)) * y + (v - mp.mpf(0.5)) * mp.log(s + 2 * x) - s)
+        s0 += t
+        s1w += t / (s + 2 * x)
+    h0, h1 = _h_dx(v, x, "hl32")
+    return -(v / x + 1) + (2 * v - 1) * (s1w + h1) / (s0 + h0)
+
+
+def test_derivative_split_rule_up_to_5e_3():
+    """For v < 0.1 the derivative takes the split rule up to x = 5e-3, where
+    the 64-node rule leaves 8e-15 (v = 0, x = 1e-3): the split rule's error
+    there is below 2e-16."""
+    with mp.workdps(30):
+        for v in (0.0, 1e-4, 0.01, 0.05, 0.099):
+            for x in (1e-3, 1.5e-3, 2e-3, 3e-3, 4.9e-3):
+                ref = oracle.dlog_k_dx(np.array([v]), np.array([x]))[0]
+                d = _split_dx_above_1e3(mp.mpf(v), mp.mpf(x))
+                err = float(abs(d - mp.mpf(ref)) / abs(mp.mpf(ref)))
+                assert err < 2e-16, (v, x, err)
+        a0, a1 = _g_fixed_dx(mp.mpf(0), mp.mpf(1e-3), 64)
+        b0, b1 = _h_dx(mp.mpf(0), mp.mpf(1e-3), "hl32")
+        d64 = -(mp.mpf(1e-3) ** -1 * 0 + 1) - (a1 + b1) / (a0 + b0)
+        ref = oracle.dlog_k_dx(np.array([0.0]), np.array([1e-3]))[0]
+        assert float(abs(d64 - mp.mpf(ref)) / abs(mp.mpf(ref))) > 1e-15
