@@ -72,7 +72,7 @@ def _latency_run(srv, n_req, arr, submit, out_slots):
         if i >= out_slots:
             srv.wait(tickets[i - out_slots], timeout=300)
         tickets[i] = submit(i)
-    for t in tickets[-out_slots:]:
+    for t in tickets[-min(out_slots, n_req):]:
         srv.wait(t, timeout=300)
     lat = np.empty(n_req)
     t_first, t_last = np.inf, 0.0
@@ -91,7 +91,7 @@ def _closed_loop(srv, n_req, submit, out_slots):
         if i >= out_slots:
             srv.wait(tickets[i - out_slots], timeout=300)
         tickets.append(submit(i))
-    for t in tickets[-out_slots:]:
+    for t in tickets[-min(out_slots, n_req):]:
         srv.wait(t, timeout=300)
     dt = time.perf_counter() - t0
     for t in tickets:
@@ -119,8 +119,14 @@ def _run(n_req, seed, max_n, loads, device, pool_n, out_slots, per_call_requests
     offs = rng.integers(0, pool_n - max_n, n_req)
     out64 = torch.empty((out_slots, max_n), dtype=torch.float64).pin_memory()
     out32 = torch.empty((out_slots, max_n), dtype=torch.float32).pin_memory()
-    dout64 = torch.empty((out_slots, max_n), dtype=torch.float64, device=dev)
-    dout32 = torch.empty((out_slots, max_n), dtype=torch.float32, device=dev)
+    # device requests write to regions of their own (nothing is copied back,
+    # so the client never waits for a region to be free)
+    tot64, tot32 = int(sizes[~f32].sum()), int(sizes[f32].sum())
+    dout64 = torch.empty(max(tot64, max_n), dtype=torch.float64, device=dev)
+    dout32 = torch.empty(max(tot32, max_n), dtype=torch.float32, device=dev)
+    dpos = np.zeros(n_req, dtype=np.int64)
+    dpos[~f32] = np.concatenate([[0], np.cumsum(sizes[~f32])[:-1]]) if tot64 else 0
+    dpos[f32] = np.concatenate([[0], np.cumsum(sizes[f32])[:-1]]) if tot32 else 0
 
     def host_args(i):
         o, n = int(offs[i]), int(sizes[i])
@@ -129,23 +135,23 @@ def _run(n_req, seed, max_n, loads, device, pool_n, out_slots, per_call_requests
         return pv64[o:o + n], px64[o:o + n], out64[i % out_slots, :n]
 
     def dev_args(i):
-        o, n = int(offs[i]), int(sizes[i])
+        o, n, p = int(offs[i]), int(sizes[i]), int(dpos[i])
         if f32[i]:
-            return dv32[o:o + n], dx32[o:o + n], dout32[i % out_slots, :n]
-        return dv64[o:o + n], dx64[o:o + n], dout64[i % out_slots, :n]
+            return dv32[o:o + n], dx32[o:o + n], dout32[p:p + n]
+        return dv64[o:o + n], dx64[o:o + n], dout64[p:p + n]
 
     # raw pointers of every request, so the submitting loop does not inspect tensors
-    def ptrs(bufs):
+    def ptrs(bufs, out_pos):
         v64, x64, v32, x32, o64, o32 = (b.data_ptr() for b in bufs)
         es = np.where(f32, 4, 8)
         vb = np.where(f32, v32, v64) + offs * es
         xb = np.where(f32, x32, x64) + offs * es
-        ob = np.where(f32, o32, o64) + (np.arange(n_req) % out_slots) * max_n * es
+        ob = np.where(f32, o32, o64) + out_pos * es
         return [(("i", "k")[kinds[i]], B.LB_F32 if f32[i] else B.LB_F64, int(vb[i]), int(xb[i]), int(ob[i]),
                  int(sizes[i])) for i in range(n_req)]
 
-    host_ptrs = ptrs((pv64, px64, pv32, px32, out64, out32))
-    dev_ptrs = ptrs((dv64, dx64, dv32, dx32, dout64, dout32))
+    host_ptrs = ptrs((pv64, px64, pv32, px32, out64, out32), (np.arange(n_req) % out_slots) * max_n)
+    dev_ptrs = ptrs((dv64, dx64, dv32, dx32, dout64, dout32), dpos)
 
     total = int(sizes.sum())
     res = {"requests": n_req, "pairs": total,
@@ -165,20 +171,23 @@ def _run(n_req, seed, max_n, loads, device, pool_n, out_slots, per_call_requests
             srv.wait(sub_host(i), timeout=120)
             srv.wait(sub_dev(i), timeout=120)
         cap = {}
-        for arm, sub in (("batched", sub_host), ("batched_device", sub_dev)):
-            cap[arm] = total / _closed_loop(srv, n_req, sub, out_slots)
+        # host requests: output rows are reused, so the client waits for the
+        # request that last used a row; device requests: everything submitted
+        # at once, then waited for
+        for arm, sub, slots_ in (("batched", sub_host, out_slots), ("batched_device", sub_dev, n_req + 1)):
+            cap[arm] = total / _closed_loop(srv, n_req, sub, slots_)
             res[arm + "_capacity_gevals"] = cap[arm] / 1e9
         res["capacity_gevals"] = res["batched_capacity_gevals"]
         arrivals = []
         for load in loads:
             rate = load * cap["batched"] / (total / n_req)            # requests per second
             arrivals.append(np.cumsum(rng.exponential(1.0 / rate, n_req)))
-        for arm, sub in (("batched", sub_host), ("batched_device", sub_dev)):
+        for arm, sub, slots_ in (("batched", sub_host, out_slots), ("batched_device", sub_dev, n_req + 1)):
             res[arm + "_by_load"] = []
             for load in loads:
                 # the same arrival pattern, scaled to this arm's own capacity
                 arr = arrivals[loads.index(load)] * cap["batched"] / cap[arm]
-                lat, t_first, t_last, relaunches = _latency_run(srv, n_req, arr, sub, out_slots)
+                lat, t_first, t_last, relaunches = _latency_run(srv, n_req, arr, sub, slots_)
                 res[arm + "_by_load"].append({
                     "offered_load": load, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                     "p99_ms": 1e3 * float(np.percentile(lat, 99)), "gevals": total / (t_last - t_first) / 1e9,
@@ -210,7 +219,8 @@ def _run(n_req, seed, max_n, loads, device, pool_n, out_slots, per_call_requests
         for kind in (0, 1):
             for is32 in (False, True):
                 v, x = (dv32, dx32) if is32 else (dv64, dx64)
-                o = dout32.view(-1)[:pool_n] if is32 else dout64.view(-1)[:pool_n]
+                o = (dout32 if is32 else dout64)[:pool_n] if (dout32 if is32 else dout64).numel() >= pool_n else \
+                    torch.empty(pool_n, dtype=torch.float32 if is32 else torch.float64, device=dev)
                 fn = L.logbessel_i if kind == 0 else L.logbessel_k
 
                 def call():
