@@ -336,6 +336,21 @@ lb_status lb_server_destroy(lb_server* server);
 /* Message describing the last server failure on the calling thread. */
 const char* lb_server_last_error(void);
 
+/*
+ * Index checks (the checked build, compiled with LB_CHECKS into
+ * liblogbessel_checks.so).  There, every index into a tile's shared list,
+ * into the K-integral queue, and every pair offset read back from the queue
+ * is checked against its bound before use; a failed check sets a bit of a
+ * device status word (1 list write, 2 list read, 4 queue write, 8 queue
+ * count above the capacity, 16 pair offset beyond the chunk, 32 rule class
+ * out of range) and the access is skipped, so an index error is recorded
+ * instead of faulting.  Results are identical to the release build's when
+ * no check fails.  logbessel_check_status stores the word in *bits (host
+ * pointer) and clears it when clear != 0; it synchronizes the device.
+ * Release builds: *bits = 0 and LB_ENOTSUP.  The paper has no counterpart.
+ */
+lb_status logbessel_check_status(unsigned int* bits, int clear);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* logbessel_last_error(void);
 

@@ -29,6 +29,21 @@
 
 namespace lb {
 
+// Checked build (-DLB_CHECKS, liblogbessel_checks.so): every index into the
+// tile's shared list, into the K-integral queue, and every pair offset read
+// back from the queue is checked against its bound before use; a failed
+// check sets a bit of lb_check_status (1 list write, 2 list read, 4 queue
+// write, 8 queue count above the capacity, 16 pair offset beyond the chunk,
+// 32 rule class out of range) and the access is skipped or clamped.  It
+// stands in for a memory checker: the kernels record where an index left
+// its buffer instead of faulting.  Release builds compile the checks out.
+#ifdef LB_CHECKS
+static __device__ unsigned int lb_check_status;
+#define LB_CHECK(cond, bit) ((cond) || (atomicOr(&lb_check_status, (unsigned)(bit)), false))
+#else
+#define LB_CHECK(cond, bit) true
+#endif
+
 // List keys.  mu_20 (FP64 values) takes one key per term count n = 1..20,
 // found while binning (an unrolled single-precision pass); the power series
 // one key per band of x, log-spaced, 3 log2(1 + x) (its term count grows with
@@ -260,8 +275,10 @@ __device__ __forceinline__ void tile_bin(TileShared<T>& S, const T* __restrict__
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < LB_ITEMS; ++it)
-    if (key[it] < NKEYS)
-      S.list[S.kbeg[key[it]] + S.wcount[it][warp][key[it]] + rank[it]] = (uint16_t)tile_offset(it, tid);
+    if (key[it] < NKEYS) {
+      const int pos = S.kbeg[key[it]] + S.wcount[it][warp][key[it]] + rank[it];
+      if (LB_CHECK(pos >= 0 && pos < LB_TILE, 1u)) S.list[pos] = (uint16_t)tile_offset(it, tid);
+    }
   __syncthreads();
 }
 
@@ -295,8 +312,13 @@ __device__ __forceinline__ void tile_eval_region(TileShared<T>& S, int lane, con
     id = __shfl_sync(0xffffffffu, id, 0);
     if (id >= nch) break;
     const int j0 = id << 5, j = j0 + lane;
-    const bool ok = j < c;
-    const int li = S.list[b0 + (ok ? j : j0)];
+    bool ok = j < c;
+    int jl = b0 + (ok ? j : j0);
+    if (!LB_CHECK(jl >= 0 && jl < LB_TILE, 2u)) {
+      jl = 0;                                      // clamped: the warp still runs the expression together
+      ok = false;
+    }
+    const int li = S.list[jl];
     int nterm = S.nt[li];
     if constexpr (sizeof(T) == 8 && !DX && KIND == KIND_I && R == R_FALLBACK)
       nterm = series_terms((float)(so ? so->v : (double)S.sv[li]), (float)S.sx[li]);

@@ -69,6 +69,13 @@ __host__ __device__ constexpr int kint_ctas_per_sm(int cls) {
   return cls < 0 ? LB_KINT_CTAS_PER_SM : kKintCtasCls[cls];
 }
 
+// K-integral queue entries: the pair's offset within its chunk (chunks hold
+// at most 2^26 pairs) in the low 26 bits, the quadrature rule class of the
+// FP64 Gauss rules (kint_class; 0 otherwise) above them, so that a kernel
+// that takes one class finds its pairs by reading the queue alone.
+constexpr int kQueueOffsetBits = 26;
+constexpr uint32_t kQueueOffsetMask = (1u << kQueueOffsetBits) - 1u;
+
 // Tile kernel: classify, bin per region in shared memory, evaluate the
 // per-thread expressions (lb_tile.cuh); K fallback pairs go to a global queue
 // for lb_kint_kernel.  T = double (FP64) or float (FP32-mixed).
@@ -76,7 +83,7 @@ template <int KIND, bool DX, typename T>
 __global__ void __launch_bounds__(LB_THREADS, LB_TILES_CTAS_PER_SM)
 lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
                 int64_t n, int mode, int forced_region, unsigned int* __restrict__ qcount,
-                uint32_t* __restrict__ queue) {
+                uint32_t* __restrict__ queue, int64_t qcap) {
   __shared__ TileShared<T> S;
   const int tid = threadIdx.x;
   const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
@@ -102,10 +109,15 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
         unsigned cls = 0;                          // quadrature rule classes of the queued pairs
         for (int j = tid; j < c; j += LB_THREADS) {
           const int li = S.list[f0 + j];
-          queue[b + j] = (uint32_t)(t0 + li);
+          uint32_t cl = 0;
           if constexpr (sizeof(T) == 8) {
-            if (mode == MODE_TIGHT) cls |= 1u << kint_class(fabs((double)S.sv[li]), (double)S.sx[li], DX);
+            if (mode == MODE_TIGHT) {
+              cl = (uint32_t)kint_class(fabs((double)S.sv[li]), (double)S.sx[li], DX);
+              cls |= 1u << cl;
+            }
           }
+          // the pair's offset in the chunk (< 2^26) and its rule class above it
+          if (LB_CHECK(b + j < qcap, 4u)) queue[b + j] = (uint32_t)(t0 + li) | (cl << kQueueOffsetBits);
         }
         if constexpr (sizeof(T) == 8) {
           cls = __reduce_or_sync(0xffffffffu, cls);
@@ -124,8 +136,10 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
 template <bool GAUSS, bool DX, typename T, int CLS = -1>
 __global__ void __launch_bounds__(LB_THREADS, kint_ctas_per_sm(CLS))
 lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
-               const unsigned int* __restrict__ qcount, const uint32_t* __restrict__ queue) {
-  const unsigned int cnt = *qcount;
+               const unsigned int* __restrict__ qcount, const uint32_t* __restrict__ queue, int64_t n,
+               int64_t qcap) {
+  unsigned int cnt = *qcount;
+  if (!LB_CHECK(cnt <= qcap, 8u)) cnt = (unsigned int)qcap;
   const unsigned present = (GAUSS && sizeof(T) == 8) ? qcount[1] : 0u;
   if (CLS >= 0 && !(present & (1u << CLS))) return;     // the same for every thread of the grid
   const int lane = threadIdx.x & 31;
@@ -158,7 +172,7 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
   // every warp switching between up to six code paths, the instruction
   // cache thrashed (the K call of the robustness sweep took 2.2x the time of
   // its rule classes evaluated one after another).  A phase re-reads the
-  // queue and the pairs' (v, x), a few bytes per pair.  A pair's result
+  // queue only, 4 bytes per pair: each entry carries its pair's class.  A pair's result
   // does not depend on its batch.  A queue of one class, and the other
   // kernels, take the queue in order, 32 pairs at a time.  A class kernel
   // is one phase of this: the host launches the six, costliest first.
@@ -182,10 +196,12 @@ lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ 
           uint32_t id = 0;
           int cl = -1;
           if (t < m) {
-            id = queue[b + t];
-            if (c >= 0) cl = kint_class((double)fabs(v[(int64_t)id * v_stride]), (double)x[id], DX);
+            const uint32_t e = queue[b + t];       // offset and rule class: no gather of v and x to scan
+            id = e & kQueueOffsetMask;
+            cl = (int)(e >> kQueueOffsetBits);
+            if (!LB_CHECK(cl <= 5, 32u)) cl = 0;
           }
-          const bool take = t < m && cl == c;
+          const bool take = t < m && (c < 0 || cl == c) && LB_CHECK((int64_t)id < n, 16u);
           const unsigned mk = __ballot_sync(0xffffffffu, take);
           if (take) my[(head + nb + __popc(mk & lt)) & 511u] = id;   // nb <= 31 + 256 < 512: no overrun
           nb += __popc(mk);
@@ -393,28 +409,28 @@ lb_status validate(lb_dtype dtype, const void* v, int64_t v_stride, const void* 
 
 template <typename T, int CLS>
 lb_status launch_kint_class(int sms, cudaStream_t st, const T* v, int64_t v_stride, const T* x, T* out,
-                            const unsigned int* qcount, const uint32_t* queue) {
+                            const unsigned int* qcount, const uint32_t* queue, int64_t n, int64_t qcap) {
   const int grid = sms * 2 * kint_ctas_per_sm(CLS);
   return launch(PS_KINT, st, [&] {
-    lb_kint_kernel<true, false, T, CLS><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, qcount, queue);
+    lb_kint_kernel<true, false, T, CLS><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, qcount, queue, n, qcap);
   });
 }
 
 // The six class kernels of the FP64 Gauss values, in the order of the phases.
 template <typename T>
 lb_status launch_kint_classes(int sms, cudaStream_t st, const T* v, int64_t v_stride, const T* x, T* out,
-                              const unsigned int* qcount, const uint32_t* queue) {
-  lb_status s = launch_kint_class<T, 0>(sms, st, v, v_stride, x, out, qcount, queue);
-  if (s == LB_OK) s = launch_kint_class<T, 5>(sms, st, v, v_stride, x, out, qcount, queue);
-  if (s == LB_OK) s = launch_kint_class<T, 4>(sms, st, v, v_stride, x, out, qcount, queue);
-  if (s == LB_OK) s = launch_kint_class<T, 3>(sms, st, v, v_stride, x, out, qcount, queue);
-  if (s == LB_OK) s = launch_kint_class<T, 2>(sms, st, v, v_stride, x, out, qcount, queue);
-  if (s == LB_OK) s = launch_kint_class<T, 1>(sms, st, v, v_stride, x, out, qcount, queue);
+                              const unsigned int* qcount, const uint32_t* queue, int64_t n, int64_t qcap) {
+  lb_status s = launch_kint_class<T, 0>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<T, 5>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<T, 4>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<T, 3>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<T, 2>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<T, 1>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
   return s;
 }
 
-// Largest chunk handled with one queue: the queue holds 32-bit offsets.
-const int64_t kChunk = (int64_t)1 << 26;
+// Largest chunk handled with one queue: the queue entries hold 26-bit offsets.
+const int64_t kChunk = (int64_t)1 << kQueueOffsetBits;
 
 // Enqueue the evaluation of n pairs.  The K fallback goes through a queue
 // of 32-bit pair offsets in scratch memory (qcount: the counter and the
@@ -430,14 +446,15 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
     const int grid = (int)(ntiles_all < (int64_t)sms * LB_TILES_CTAS_PER_SM ? ntiles_all : (int64_t)sms * LB_TILES_CTAS_PER_SM);
     return launch(PS_TILES, st, [&] {
       lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region,
-                                                                 nullptr, nullptr);
+                                                                 nullptr, nullptr, 0);
     });
   }
   if (sizeof(T) == 4 && mode != MODE_TIGHT)
     return fail(LB_ENOTSUP, "%sthe FP32 K integral is implemented for LB_TIGHT only", "", 0);
+  // queue entries a pass can write: every workspace holds at least this many
+  const int64_t cap = n < chunk ? n : chunk;
   void* ws = scratch;
   if (!ws) {
-    const int64_t cap = n < chunk ? n : chunk;
     const size_t bytes = 256 + (size_t)cap * sizeof(uint32_t);
     if (cudaMallocAsync(&ws, bytes, st) != cudaSuccess) {
       cudaGetLastError();
@@ -456,14 +473,15 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
     const int64_t ntiles = (cn + LB_TILE - 1) / LB_TILE;
     const int grid = (int)(ntiles < (int64_t)sms * LB_TILES_CTAS_PER_SM ? ntiles : (int64_t)sms * LB_TILES_CTAS_PER_SM);
     status = launch(PS_TILES, st, [&] {
-      lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount, queue);
+      lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount,
+                                                                 queue, cap);
     });
     if (status != LB_OK) break;
     bool done = false;
     if constexpr (sizeof(T) == 8 && !DX) {
       if (mode == MODE_TIGHT) {
         // one kernel per rule class, costliest first (the phases of a mixed queue)
-        status = launch_kint_classes<T>(sms, st, vc, v_stride, xc, oc, qcount, queue);
+        status = launch_kint_classes<T>(sms, st, vc, v_stride, xc, oc, qcount, queue, cn, cap);
         done = true;
       }
     }
@@ -471,9 +489,9 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
       const int kgrid = sms * 2 * LB_KINT_CTAS_PER_SM;
       status = launch(PS_KINT, st, [&] {
         if (mode == MODE_TIGHT)
-          lb_kint_kernel<true, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
+          lb_kint_kernel<true, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue, cn, cap);
         else
-          lb_kint_kernel<false, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue);
+          lb_kint_kernel<false, DX, T><<<kgrid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, qcount, queue, cn, cap);
       });
     }
   }
@@ -867,6 +885,24 @@ lb_status logbessel_host_release(void) {
     host_pipe_destroy(P);
   }
   return LB_OK;
+}
+
+lb_status logbessel_check_status(unsigned int* bits, int clear) {
+  if (!bits) return fail(LB_EINVAL, "%sNULL bits", "", 0);
+  *bits = 0;
+#ifdef LB_CHECKS
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, lb_check_status, sizeof v) != cudaSuccess) return check_launch("logbessel_check_status");
+  if (clear) {
+    const unsigned int z = 0;
+    if (cudaMemcpyToSymbol(lb_check_status, &z, sizeof z) != cudaSuccess) return check_launch("logbessel_check_status");
+  }
+  *bits = v;
+  return LB_OK;
+#else
+  (void)clear;
+  return fail(LB_ENOTSUP, "%sthis build has no index checks (build with LB_CHECKS)", "", 0);
+#endif
 }
 
 const char* logbessel_last_error(void) { return g_last_error.c_str(); }
