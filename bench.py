@@ -32,13 +32,26 @@ METRIC = "Gevals/s (log I_v and log K_v, FP64)"
 # capture of every launch of one full-size step (the launch list of
 # profiles/launches_paper_sweep_fp64.md, with dram__bytes_read.sum and
 # dram__bytes_write.sum); empty when the kernels changed since.
-NCU_DRAM_BYTES_PER_STEP = {}
+NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.785e9, 27), "lb_kint_kernel": (11.232e9, 90)}
 # Pipe utilisation of each kernel from ncu --set full on a small case of the
 # same workload (profiles/lb_tiles_kernel_sweep_small.md,
-# profiles/lb_kint_kernel_sweep_small.md): share of peak issue of the FP64
-# pipe, the ALU pipe and the XU (special-function) pipe; empty when stale.
-NCU_PIPES = {}
-NCU_PIPES_FP32 = {}
+# profiles/lb_kint_kernel_sweep_small.md, profiles/fp32_mixed_sweep_small.md):
+# share of peak issue of the FP64 pipe, the ALU pipe, the FP32 (FMA) pipe and
+# the XU (special-function) pipe while active, and the share of cycles that
+# issue; empty when stale.
+NCU_PIPES = {
+    "lb_tiles_kernel": {"fp64": 0.830, "alu": 0.201, "fma": 0.067, "xu": 0.013, "issue_active": 0.274,
+                        "launch": "log I, mixed orders, 11M pairs"},
+    "lb_kint_kernel": {"fp64": 0.625, "alu": 0.659, "fma": 0.188, "xu": 0.017, "issue_active": 0.680,
+                       "launch": "one-slot class kernel of a mixed-order log K call (class 4: fp64 0.492, "
+                                 "alu 0.641, issue 0.630)"},
+}
+NCU_PIPES_FP32 = {
+    "lb_tiles_kernel": {"fp64": 0.0, "alu": 0.426, "fma": 0.253, "xu": 0.119, "issue_active": 0.763,
+                        "launch": "log I, mixed orders, 11M pairs"},
+    "lb_kint_kernel": {"fp64": 0.0, "alu": 0.563, "fma": 0.347, "xu": 0.077, "issue_active": 0.840,
+                       "launch": "log K integral, mixed orders"},
+}
 UNIT = "Gevals/s"
 WORKLOAD = "paper-shaped sweep: v=2^0..2^10 x 20M x~U[1,100] per order, log I + log K, per-order + mixed-order calls"
 
@@ -458,7 +471,11 @@ def main():
                             "peak": OT.PEAK_FP32_OPS / 1e9, "unit": "G FP32 op/s",
                             "frac": k32[n32]["frac_fp32_pipe"], "traffic": None,
                             "peak_source": "152 SMs x 128 FP32 op/clk x 2.07 GHz",
-                            "fp64_pipe": "no FP64 operations on this path (FP32 everywhere); ncu: see ncu"}
+                            "fp64_pipe": "no FP64 operations on this path (FP32 everywhere)",
+                            "bound_by": "instruction issue (ncu issue active %.2f; FP32 pipe %.2f)"
+                                        % (NCU_PIPES_FP32[n32]["issue_active"], NCU_PIPES_FP32[n32]["fma"])
+                                        if n32 in NCU_PIPES_FP32 else None,
+                            "ncu": NCU_PIPES_FP32.get(n32)}
         fp32["kernels"] = k32
         fp32["work_by_region"] = {kern: {r: {"pairs": c, "ops_per_pair": m} for r, (c, m) in regs.items()}
                                   for kern, regs in wk32.items()}
