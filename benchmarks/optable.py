@@ -129,10 +129,9 @@ def region_ops(region, v, x, shared=False, fp32=False):
 
 
 def kint_ops(v, x, shared=False, fp32=False):
-    """Operations per pair of the K integral (Gauss rules; the FP32 form has
-    no one-slot rules and computes its node positions per pair)."""
-    ng, nh = kint_nodes(v, x, one_slot=not fp32)
-    shared = shared and not fp32
+    """Operations per pair of the K integral (Gauss rules; the FP32 form takes
+    the same rules, in single precision)."""
+    ng, nh = kint_nodes(v, x)
     return ng * (7 if shared else 8) + nh * 6 + (10 if shared else 11)
 
 

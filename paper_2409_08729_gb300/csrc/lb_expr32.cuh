@@ -119,14 +119,17 @@ __device__ __forceinline__ float series_log_i32(float v, float x) {
 }
 
 // K integral, Gauss rules of lb_kint.cuh evaluated in single precision
-// (float copies of the tables), including the split g rule for v < 0.4,
-// x < 1e-3 (see kint_sums_split: the nodes anchored at s1 = 128 x carry their
-// terms less C = 2 v log s1 and are shifted by m - C).  Warp-cooperative; all
-// lanes pass the same pair.
-// One order for every pair of a call: u_j^beta of the three u rules once per
-// block (as KintScalar; same operations, same results).
+// (float copies of the tables): the one-slot rules for 2 <= v <= 16.5, the
+// packed rule for 1.2 < v <= 5 below that, the fixed rules, and the split g
+// rule for v < 0.4, x < 1e-3 (see kint_sums_split: the nodes anchored at
+// s1 = 128 x carry their terms less C = 2 v log s1 and are shifted by
+// m - C).  Warp-cooperative; all lanes pass the same pair.
+// One order for every pair of a call: u_j^beta of the three u rules and the
+// one-slot rule's s0 u_j^beta once per block (as KintScalar; same operations,
+// same results).
 struct KintScalar32 {
   float ub24[24], ub32[32], ub64[64];
+  float sg[22];                                    // s0 u_j^beta of the one-slot rule of v (if any)
 };
 
 __device__ __forceinline__ void kint_scalar_setup32(KintScalar32& ks, float v) {
@@ -135,6 +138,11 @@ __device__ __forceinline__ void kint_scalar_setup32(KintScalar32& ks, float v) {
   if (tid < 24) ks.ub24[tid] = expf(beta * __ldg(lb_kqf_g24_logu + tid));
   else if (tid < 56) ks.ub32[tid - 24] = expf(beta * __ldg(lb_kqf_g32_logu + tid - 24));
   else if (tid < 120) ks.ub64[tid - 56] = expf(beta * __ldg(lb_kqf_g64_logu + tid - 56));
+  else if (tid >= 128 && tid < 150 && v >= 2.0f && v <= 16.5f) {
+    const int j = tid - 128;
+    if (v < 7.0f) ks.sg[j] = expf(fmaf(beta, __ldg(lb_kqf_g22_logu + j), (float)LB_KQ_LOG8));
+    else if (j < 12) ks.sg[j] = expf(fmaf(beta, __ldg(lb_kqf_g12_logu + j), (float)LB_KQ_LOG3));
+  }
   __syncthreads();
 }
 
@@ -155,6 +163,33 @@ __device__ __forceinline__ float warp_max32(float a) {
 __device__ __forceinline__ float kint_gauss32(float v, float x, float beta, float logbeta, int lane,
                                               const KintScalar32* ks = nullptr) {
   const float vm = v - 0.5f, vp = v + 0.5f, tx = 2.0f * x;
+  if (v >= 2.0f && v <= 16.5f) {
+    // the one-slot rules of the FP64 path (kint_sum_one): int_0^inf F split at
+    // s0 = 8 (22 g + 10 h nodes, v < 7) or s0 = 3 (12 + 20), [0, s0] with
+    // s = s0 u^beta, [s0, inf) by Gauss-Laguerre in s - s0: one lane slot
+    // instead of two
+    const bool r4 = v < 7.0f;
+    const int ng = r4 ? 22 : 12;
+    const float ls0 = r4 ? (float)LB_KQ_LOG8 : (float)LB_KQ_LOG3;
+    const bool isg = lane < ng;
+    float s, y, c;
+    if (isg) {
+      s = ks ? ks->sg[lane] : expf(fmaf(beta, __ldg((r4 ? lb_kqf_g22_logu : lb_kqf_g12_logu) + lane), ls0));
+      y = 0.0f;
+      c = __ldg((r4 ? lb_kqf_g22_c : lb_kqf_g12_c) + lane) + fmaf(vp, ls0, logbeta);
+    } else {
+      const int j = lane - ng;
+      s = __ldg((r4 ? lb_kqf_hq10o8_s : lb_kqf_hq20o3_s) + j);
+      y = __ldg((r4 ? lb_kqf_hq10o8_y : lb_kqf_hq20o3_y) + j);
+      c = __ldg((r4 ? lb_kqf_hq10o8_c : lb_kqf_hq20o3_c) + j);
+    }
+    const float L = fmaf(vm, logf(tx + s) + y, c) - (isg ? s : 0.0f);
+    const float m = warp_max32(L);
+    float sum = __expf(L - m);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    return m + logf(sum);
+  }
   if (v > 1.2f && v <= 5.0f) {
     // 24 g + 40 h nodes in two lane slots (as kint_sums_g24h40)
     const bool isg = lane < 24;
