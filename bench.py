@@ -49,6 +49,8 @@ NCU_PIPES = {
 NCU_PIPES_FP32 = {
     "lb_tiles_kernel": {"fp64": 0.0, "alu": 0.426, "fma": 0.253, "xu": 0.119, "issue_active": 0.763,
                         "launch": "log I, mixed orders, 11M pairs"},
+    "lb_kint_kernel": {"fp64": 0.0, "alu": 0.529, "fma": 0.320, "xu": 0.055, "issue_active": 0.813,
+                       "launch": "log K integral, mixed orders"},
 }
 UNIT = "Gevals/s"
 WORKLOAD = "paper-shaped sweep: v=2^0..2^10 x 20M x~U[1,100] per order, log I + log K, per-order + mixed-order calls"

@@ -23,8 +23,12 @@
 #include "lb_expr32.cuh"
 #include "lb_kint.cuh"
 
+#ifndef LB_THREADS
 #define LB_THREADS 256
+#endif
+#ifndef LB_ITEMS
 #define LB_ITEMS 4
+#endif
 #define LB_TILE (LB_THREADS * LB_ITEMS)
 
 namespace lb {
@@ -74,8 +78,10 @@ __host__ __device__ constexpr int region_key_end(int r) {
 template <typename T>
 struct TileShared {
   T sv[LB_TILE];
-  T sx[LB_TILE];
-  T sres[LB_TILE];                                 // results, stored coalesced at the end of the tile
+  union {                                          // a pair's result replaces its argument
+    T sx[LB_TILE];
+    T sres[LB_TILE];                               // results, stored coalesced at the end of the tile
+  };
   uint16_t list[LB_TILE];                          // tile offsets of the pairs to evaluate, sorted by key
   uint8_t nt[LB_TILE];                             // estimated term count (mu_20; FP64 values)
   uint8_t keep[LB_TILE];                           // 1: sres holds this pair's result
@@ -329,6 +335,7 @@ __device__ __forceinline__ void tile_eval_region(TileShared<T>& S, int lane, con
     } else {
       val = tile_expr<KIND, DX, T>(R, S.sv[li], S.sx[li], nterm);
     }
+    __syncwarp();                                  // every lane has read its arguments (sres is sx)
     if (ok) S.sres[li] = val;
   }
 }
