@@ -32,7 +32,7 @@ METRIC = "Gevals/s (log I_v and log K_v, FP64)"
 # capture of every launch of one full-size step (the launch list of
 # profiles/launches_paper_sweep_fp64.md, with dram__bytes_read.sum and
 # dram__bytes_write.sum); empty when the kernels changed since.
-NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.785e9, 27), "lb_kint_kernel": (11.232e9, 90)}
+NCU_DRAM_BYTES_PER_STEP = {"lb_kint_kernel": (11.232e9, 90)}
 # Pipe utilisation of each kernel from ncu --set full on a small case of the
 # same workload (profiles/lb_tiles_kernel_sweep_small.md,
 # profiles/lb_kint_kernel_sweep_small.md, profiles/fp32_mixed_sweep_small.md):
@@ -40,7 +40,7 @@ NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.785e9, 27), "lb_kint_kernel": 
 # the XU (special-function) pipe while active, and the share of cycles that
 # issue; empty when stale.
 NCU_PIPES = {
-    "lb_tiles_kernel": {"fp64": 0.830, "alu": 0.201, "fma": 0.067, "xu": 0.013, "issue_active": 0.274,
+    "lb_tiles_kernel": {"fp64": 0.723, "alu": 0.378, "fma": 0.153, "xu": 0.019, "issue_active": 0.450,
                         "launch": "log I, mixed orders, 11M pairs"},
     "lb_kint_kernel": {"fp64": 0.625, "alu": 0.659, "fma": 0.188, "xu": 0.017, "issue_active": 0.680,
                        "launch": "one-slot class kernel of a mixed-order log K call (class 4: fp64 0.492, "
@@ -441,7 +441,9 @@ def main():
             "algorithmic_bytes": kd["algorithmic_bytes_per_launch"], "launches": kd["launches"],
             "avg_launch_ms": kd["avg_launch_ms"],
             "work": "FP64 operations of the method (benchmarks/optable.py) at per-pair term and node counts; "
-                    "library calls (log, exp, rcp, rsqrt, lgamma) not priced",
+                    "library calls (log, exp, rcp, rsqrt, lgamma) not priced; the high-order terms of the "
+                    "mu_20 and U_K sums execute as double-float FP32 instructions, so the rate counts the "
+                    "method's operations, not the FP64 instructions issued",
             "peak_source": "152 SMs x 2 FP64 op/clk x 2.07 GHz; live DFMA microbenchmark %.1f G/s"
                            % (rates["dfma"] / 1e9),
             "ncu": kd["ncu"]}

@@ -99,6 +99,18 @@ def _closed_loop(srv, n_req, submit, out_slots):
     return dt
 
 
+def _device_shares(d0, d1, ctas, wall):
+    """The persistent kernel's CTA time over a run: the share spent running
+    items (per item family too) and claiming or waiting for them."""
+    span = ctas * wall * 1e9
+    busy = {f: d1["busy_ns"][f] - d0["busy_ns"][f] for f in d1["busy_ns"]}
+    items = {f: d1["items"][f] - d0["items"][f] for f in d1["items"]}
+    return {"ctas": ctas, "busy_share": sum(busy.values()) / span,
+            "claim_wait_share": (d1["claim_ns"] - d0["claim_ns"]) / span,
+            "busy_share_by_family": {f: b / span for f, b in busy.items() if items[f]},
+            "items_by_family": {f: n for f, n in items.items() if n}}
+
+
 def _time_cuda(fn, stream):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -174,9 +186,14 @@ def _run(n_req, seed, max_n, loads, device, pool_n, out_slots, per_call_requests
         # host requests: output rows are reused, so the client waits for the
         # request that last used a row; device requests: everything submitted
         # at once, then waited for
+        ctas = torch.cuda.get_device_properties(dev).multi_processor_count * 4
         for arm, sub, slots_ in (("batched", sub_host, out_slots), ("batched_device", sub_dev, n_req + 1)):
-            cap[arm] = total / _closed_loop(srv, n_req, sub, slots_)
+            d0 = srv.device_stats()
+            wall = _closed_loop(srv, n_req, sub, slots_)
+            d1 = srv.device_stats()
+            cap[arm] = total / wall
             res[arm + "_capacity_gevals"] = cap[arm] / 1e9
+            res[arm + "_time_shares"] = _device_shares(d0, d1, ctas, wall)
         res["capacity_gevals"] = res["batched_capacity_gevals"]
         arrivals = []
         for load in loads:

@@ -105,11 +105,12 @@ lb_status logbessel_k(lb_dtype dtype, const void* v, int64_t v_stride, const voi
  * caller and allocate nothing.
  *
  * logbessel_workspace_bytes(n): the bytes that evaluate n pairs in one pass,
- * 256 + 4 min(n, 2^26) (0 for n < 0).
+ * 256 + 4 min(m, 2^26) with m = n rounded up to a multiple of 2048 (the
+ * tile of the per-call kernels), at least 8448 (0 for n < 0).
  * logbessel_k_ws / logbessel_k_dx_ws: as logbessel_k / logbessel_k_dx, with
  * `workspace` a device pointer (256-byte aligned) to `ws_bytes` bytes, at
- * least 4352 (1024 pairs per pass); n pairs are processed in passes of
- * (ws_bytes - 256) / 4 pairs rounded down to a multiple of 1024 (at most
+ * least 8448 (2048 pairs per pass); n pairs are processed in passes of
+ * (ws_bytes - 256) / 4 pairs rounded down to a multiple of 2048 (at most
  * 2^26), with results identical to one pass.  The workspace is used in
  * stream order on cuda_stream: other work must not use it until the call's
  * work has finished.  LB_EINVAL (nothing enqueued) for a NULL, misaligned
@@ -332,6 +333,23 @@ lb_status lb_server_ticket_info(lb_server* server, long long ticket, int* done, 
 lb_status lb_server_release(lb_server* server, long long ticket);
 lb_status lb_server_stats(lb_server* server, long long* completed, long long* evals,
                           long long* kernel_launches, long long* in_flight);
+/*
+ * Device time accounts of the persistent kernel, cumulative since
+ * lb_server_create (take differences between two reads).  claim_ns: the
+ * summed time its CTAs spent claiming a work item, waiting for one included
+ * (a CTA with nothing to do counts here until it exits).  busy_ns[f] and
+ * items[f], f < LB_SERVER_FAMILIES: the summed time CTAs spent running the
+ * items of family f, and how many ran; the families are 0 FP64 log I tiles,
+ * 1 FP64 log K tiles, 2 FP32 log I tiles, 3 FP32 log K tiles, 4 + c the
+ * windows of the FP64 K-integral queue of rule class c (c < 6; the paper
+ * modes' single queue counts as class 0), 10 FP32 K-integral windows.  Times
+ * are ns of the device's global timer.  The counters are read by a copy on a
+ * stream of the server's own while the kernel runs; the call blocks until
+ * that copy is done.  Any pointer may be NULL.  LB_ECUDA if the copy fails.
+ */
+#define LB_SERVER_FAMILIES 11
+lb_status lb_server_device_stats(lb_server* server, long long* claim_ns, long long* busy_ns,
+                                 long long* items);
 lb_status lb_server_destroy(lb_server* server);
 /* Message describing the last server failure on the calling thread. */
 const char* lb_server_last_error(void);

@@ -14,6 +14,8 @@ import os
 import sys
 from fractions import Fraction
 
+import numpy as np
+
 KMAX = 13
 
 
@@ -67,6 +69,45 @@ def _horner(cs, fn_name):
     return lines
 
 
+def f32_split(c):
+    """c (a Fraction) as a pair of floats hi + lo: hi = c rounded to single
+    precision, lo = the remainder rounded to single precision (exact
+    Fraction arithmetic, one rounding each)."""
+    import struct
+
+    def to_f32(q):
+        # nearest float to the rational q: round through a double, then fix
+        # the rare double-rounding case by comparing the two neighbours
+        f = struct.unpack("f", struct.pack("f", float(q)))[0]
+        best, err = f, abs(Fraction(f) - q)
+        for g in (np.nextafter(np.float32(f), np.float32(np.inf)), np.nextafter(np.float32(f), np.float32(-np.inf))):
+            e = abs(Fraction(float(g)) - q)
+            if e < err:
+                best, err = float(g), e
+        return best
+
+    hi = to_f32(c)
+    lo = to_f32(c - Fraction(hi))
+    return hi, lo
+
+
+def _f32_lit(f):
+    """A float as an exact C hexadecimal literal with the f suffix."""
+    if f == 0.0:
+        return "0.0f"
+    return float(f).hex() + "f"
+
+
+def _horner_df(cs, fn_name):
+    pairs = [f32_split(c) for c in cs]
+    lines = ["__host__ __device__ __forceinline__ lb::dfloat %s(lb::dfloat p) {" % fn_name,
+             "  lb::dfloat r = lb::df_make(%s, %s);" % (_f32_lit(pairs[-1][0]), _f32_lit(pairs[-1][1]))]
+    for j in range(len(pairs) - 2, -1, -1):
+        lines.append("  r = lb::df_mul_add(r, p, lb::df_make(%s, %s));" % (_f32_lit(pairs[j][0]), _f32_lit(pairs[j][1])))
+    lines += ["  return r;", "}", ""]
+    return lines
+
+
 def render_header(polys):
     lines = [
         "// Generated by gen_debye.py -- do not edit.",
@@ -94,6 +135,11 @@ def render_header(polys):
     lines.append("")
     for k in range(1, KMAX + 1):
         lines += _horner(q_coeffs(k, polys), "lb_debye_Q%d" % k)
+    lines.append("// P_k(p) in double-float (lb_df.cuh), k = 2..13: each coefficient as the")
+    lines.append("// pair hi + lo of floats nearest to it (exact hexadecimal literals).")
+    lines.append("")
+    for k in range(2, KMAX + 1):
+        lines += _horner_df(p_coeffs(k, polys), "lb_debye_P%d_df" % k)
     return "\n".join(lines) + "\n"
 
 

@@ -18,6 +18,7 @@ template <typename T> __host__ __device__ __forceinline__ T lb_fma(T a, T b, T c
 template <> __host__ __device__ __forceinline__ double lb_fma<double>(double a, double b, double c) { return fma(a, b, c); }
 template <> __host__ __device__ __forceinline__ float lb_fma<float>(float a, float b, float c) { return fmaf(a, b, c); }
 
+#include "lb_df.cuh"
 #include "debye_uk.h"
 #include "lb_fastmath.cuh"
 #include "lb_intmath.cuh"
@@ -185,26 +186,68 @@ __device__ __forceinline__ int series_terms(float v, float x) {
   return n;
 }
 
+// Leading terms of mu_K kept in FP64: the smallest k at which the running
+// product of the term ratios (the k-th term against the leading 1) falls
+// below 1e-3, by the single-precision pass of mu_terms; K when none does.
+// The terms past it hold less than 1e-3 of the sum and are summed in
+// double-float (relative error a few 2^-48, below 1e-17 of the sum).
+template <int K>
+__device__ __forceinline__ int mu_head(float v, float x) {
+  int m = K;
+  const float muf = 4.0f * v * v, inv8xf = __fdividef(1.0f, 8.0f * x);
+  float t = 1.0f;
+  bool found = false;
+#pragma unroll
+  for (int k = 1; k <= K; ++k) {
+    t *= (muf - (float)((2 * k - 1) * (2 * k - 1))) * (inv8xf * (1.0f / (float)k));
+    const bool hit = !found && fabsf(t) < 1e-3f;
+    m = hit ? k : m;
+    found = found || hit;
+  }
+  return m;
+}
+
 // 1/k and (2k-1)^2/k for k = 1..20, the constants of the term ratios of
 // mu_K, for a rolled loop over the warp's own number of terms (entry 0
 // unused).  A fully unrolled loop with the terms above n switched off by a
 // predicate would still issue every term's FP64 instructions.
 static __constant__ double kMuInvK[21] = {0.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0, 1.0 / 10.0, 1.0 / 11.0, 1.0 / 12.0, 1.0 / 13.0, 1.0 / 14.0, 1.0 / 15.0, 1.0 / 16.0, 1.0 / 17.0, 1.0 / 18.0, 1.0 / 19.0, 1.0 / 20.0};
 static __constant__ double kMuOddK[21] = {0.0, 1.0 / 1.0, 9.0 / 2.0, 25.0 / 3.0, 49.0 / 4.0, 81.0 / 5.0, 121.0 / 6.0, 169.0 / 7.0, 225.0 / 8.0, 289.0 / 9.0, 361.0 / 10.0, 441.0 / 11.0, 529.0 / 12.0, 625.0 / 13.0, 729.0 / 14.0, 841.0 / 15.0, 961.0 / 16.0, 1089.0 / 17.0, 1225.0 / 18.0, 1369.0 / 19.0, 1521.0 / 20.0};
+// 1/k as pairs of floats hi + lo (hi = 1/k rounded to single precision, lo
+// the rest), for the double-float terms.
+static __constant__ float kMuInvKh[21] = {0.0f, 0x1.p+0f, 0x1.p-1f, 0x1.555556p-2f, 0x1.p-2f, 0x1.99999ap-3f, 0x1.555556p-3f, 0x1.24924ap-3f, 0x1.p-3f, 0x1.c71c72p-4f, 0x1.99999ap-4f, 0x1.745d18p-4f, 0x1.555556p-4f, 0x1.3b13b2p-4f, 0x1.24924ap-4f, 0x1.111112p-4f, 0x1.p-4f, 0x1.e1e1e2p-5f, 0x1.c71c72p-5f, 0x1.af286cp-5f, 0x1.99999ap-5f};
+static __constant__ float kMuInvKl[21] = {0.0f, 0.0f, 0.0f, -0x1.555556p-27f, 0.0f, -0x1.99999ap-29f, -0x1.555556p-28f, -0x1.b6db6ep-28f, 0.0f, -0x1.c71c72p-31f, -0x1.99999ap-30f, -0x1.745d18p-29f, -0x1.555556p-29f, -0x1.89d89ep-29f, -0x1.b6db6ep-29f, -0x1.dddddep-29f, 0.0f, -0x1.e1e1e2p-33f, -0x1.c71c72p-32f, -0x1.af286cp-32f, -0x1.99999ap-31f};
 
 // mu_K with the lane's term count n given (at most K); all 32 lanes of the
 // warp call it together.
 template <int KIND, int K>
 __device__ __forceinline__ double mu_expr_n(double v, double x, int n) {
   n = __reduce_max_sync(0xffffffffu, n);
+  const int h = __reduce_max_sync(0xffffffffu, mu_head<K>((float)v, (float)x));
   const double mu = 4.0 * v * v;
   const double rx = ix_rcp_call(8.0 * x);                             // 1/(8x) on the integer pipe
   const double inv8x = (KIND == KIND_I) ? -rx : rx;                   // the sign s folded in
   double P = 1.0;
-  // Three FP64 operations per term: a = mu/k - (2k-1)^2/k, P = 1 + (a s/(8x)) P,
-  // for the warp's n terms only.
+  int top = n;
+  if (n > h) {
+    // terms h+1..n in double-float: r_k = (mu s/(8x) - (2k-1)^2 s/(8x)) / k,
+    // P <- 1 + r_k P
+    const dfloat wd = df_from_double(inv8x), muw = df_from_double(mu * inv8x);
+    dfloat Pd = df_make(1.0f, 0.0f);
 #pragma unroll 1
-  for (int k = n; k >= 1; --k) {
+    for (int k = n; k > h; --k) {
+      const float odd = (float)((2 * k - 1) * (2 * k - 1));           // exact
+      const dfloat ow = df_mul(wd, df_make(-odd, 0.0f));
+      const dfloat r = df_mul(df_add(muw, ow), df_make(kMuInvKh[k], kMuInvKl[k]));
+      Pd = df_mul_add(r, Pd, df_make(1.0f, 0.0f));
+    }
+    P = df_to_double(Pd);
+    top = h;
+  }
+  // Three FP64 operations per leading term: a = mu/k - (2k-1)^2/k,
+  // P = 1 + (a s/(8x)) P, for the warp's leading terms only.
+#pragma unroll 1
+  for (int k = top; k >= 1; --k) {
     const double a = fma(mu, kMuInvK[k], -kMuOddK[k]);
     P = fma(a * inv8x, P, 1.0);
   }
@@ -240,6 +283,24 @@ __device__ __forceinline__ T debye_P(int k, T p) {
     case 11: return lb_debye_P11(p);
     case 12: return lb_debye_P12(p);
     default: return lb_debye_P13(p);
+  }
+}
+
+// P_k(p) in double-float, k = 2..13 (compile-time after unrolling).
+__device__ __forceinline__ dfloat debye_P_df(int k, dfloat p) {
+  switch (k) {
+    case 2: return lb_debye_P2_df(p);
+    case 3: return lb_debye_P3_df(p);
+    case 4: return lb_debye_P4_df(p);
+    case 5: return lb_debye_P5_df(p);
+    case 6: return lb_debye_P6_df(p);
+    case 7: return lb_debye_P7_df(p);
+    case 8: return lb_debye_P8_df(p);
+    case 9: return lb_debye_P9_df(p);
+    case 10: return lb_debye_P10_df(p);
+    case 11: return lb_debye_P11_df(p);
+    case 12: return lb_debye_P12_df(p);
+    default: return lb_debye_P13_df(p);
   }
 }
 
@@ -288,10 +349,15 @@ __device__ __forceinline__ double u_expr(double v, double x) {
   const double p = t * t;
   double q = t * inv_v;
   if (KIND == KIND_K) q = -q;
-  // Horner in q over k = K..1:  S = 1 + q (P_1 + q (P_2 + ... + q P_K))
-  double acc = debye_P(K, p);
+  // Horner in q over k = K..1:  S = 1 + q (P_1 + q (P_2 + ... + q P_K)).
+  // The terms k >= 2 (at most 1/v^2 of the sum, with v > 0.7 and x' > 35 or
+  // v > 16 in the U regions: below 1e-3 of it) in double-float, P_1 and the
+  // two outer steps in FP64.
+  const dfloat pd = df_from_double(p), qd = df_from_double(q);
+  dfloat accd = debye_P_df(K, pd);
 #pragma unroll
-  for (int k = K - 1; k >= 1; --k) acc = fma(acc, q, debye_P(k, p));
+  for (int k = K - 1; k >= 2; --k) accd = df_mul_add(accd, qd, debye_P_df(k, pd));
+  const double acc = fma(df_to_double(accd), q, lb_debye_P1(p));
   const double S = fma(acc, q, 1.0);
   const double eta = r + (ix_log_call(xp) - ix_log_call(1.0 + r));      // log(x' / (1 + r)), no division
   // log(S / sqrt(2 pi v r)) = log(S^2 t / (2 pi v)) / 2, and for K
@@ -368,9 +434,12 @@ __device__ __forceinline__ double series_log_i(double v, double x) {
 // ---------------------------------------------------------------------------
 struct ScalarOrder {
   double v, inv_v, lg1;                 // v, 1/v, lgamma(v + 1)
-  double mu[21];                        // a_0..a_20 (sign s of the kind folded in)
+  double sig;                           // sigma: a power of two near mu/8 (1 for mu < 8)
+  double mu[21];                        // a_0..a_20 / sigma^k (sign s of the kind folded in)
   double ser[91];                       // 1 / (k (k + v)), k = 1..90
-  double u4[13], u6[19], u9[28], u13[40];   // C_0..C_3K
+  double u4[4], u6[4], u9[4], u13[4];   // C_0..C_3 of U_K
+  dfloat mud[21];                       // mu[] in double-float
+  dfloat u4d[13], u6d[19], u9d[28], u13d[40];   // C_0..C_3K in double-float (C_4.. used)
 };
 
 // All threads of the block call it; ends with a barrier.
@@ -382,11 +451,19 @@ __device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
     so.inv_v = 1.0 / v;
     so.lg1 = lgamma(v + 1.0);
     const double mu = 4.0 * v * v, s = KIND == KIND_I ? -1.0 : 1.0;
+    // a_k w^k = (a_k / sigma^k) (sigma w)^k: with sigma near mu/8 the scaled
+    // coefficients stay below 8^k / k! (the unscaled ones overflow for
+    // orders above about 1e9, and the double-float ones above 1e38)
+    int j = 0;
+    if (mu >= 16.0) j = ilogb(mu) - 3;
+    so.sig = ldexp(1.0, j);
     double a = 1.0;
     so.mu[0] = 1.0;
+    so.mud[0] = df_make(1.0f, 0.0f);
     for (int k = 1; k <= 20; ++k) {
-      a = a * (s * (mu - (double)((2 * k - 1) * (2 * k - 1)))) / (double)k;
+      a = ldexp(a * (s * (mu - (double)((2 * k - 1) * (2 * k - 1)))) / (double)k, -j);
       so.mu[k] = a;
+      so.mud[k] = df_from_double(a);
     }
   } else if (tid <= 90) {
     so.ser[tid] = 1.0 / ((double)tid * ((double)tid + v));
@@ -394,10 +471,11 @@ __device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
     // C_m of U_K: the coefficients of t^m, sum over k + 2i = m of c_{k,i} (s/v)^k
     int j = tid - 128, K, m;
     double* dst;
-    if (j < 13) { K = 4; m = j; dst = so.u4; }
-    else if (j < 32) { K = 6; m = j - 13; dst = so.u6; }
-    else if (j < 60) { K = 9; m = j - 32; dst = so.u9; }
-    else { K = 13; m = j - 60; dst = so.u13; }
+    dfloat* dstd;
+    if (j < 13) { K = 4; m = j; dst = so.u4; dstd = so.u4d; }
+    else if (j < 32) { K = 6; m = j - 13; dst = so.u6; dstd = so.u6d; }
+    else if (j < 60) { K = 9; m = j - 32; dst = so.u9; dstd = so.u9d; }
+    else { K = 13; m = j - 60; dst = so.u13; dstd = so.u13d; }
     const double sv = (KIND == KIND_I ? 1.0 : -1.0) / v;
     double c = 0.0, pk = 1.0;
     for (int k = 0; k <= K; ++k) {
@@ -405,7 +483,8 @@ __device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
       const int twoi = m - k;
       if (twoi >= 0 && (twoi & 1) == 0 && (twoi >> 1) <= k) c = fma(lb_debye_c[k][twoi >> 1], pk, c);
     }
-    dst[m] = c;
+    if (m < 4) dst[m] = c;
+    dstd[m] = df_from_double(c);
   }
   __syncthreads();
 }
@@ -413,10 +492,21 @@ __device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
 template <int KIND>
 __device__ __forceinline__ double mu_expr_so(const ScalarOrder& so, double x, int n) {
   n = __reduce_max_sync(0xffffffffu, n);
+  const int h = __reduce_max_sync(0xffffffffu, mu_head<20>((float)so.v, (float)x));
   const double w = ix_rcp_call(8.0 * x);
+  const double ws = w * so.sig;                   // exact: sigma is a power of two
   double P = 0.0;
+  int top = n;
+  if (n > h) {                                    // terms h+1..n in double-float
+    const dfloat wd = df_from_double(ws);
+    dfloat Pd = so.mud[n];
 #pragma unroll 1
-  for (int k = n; k >= 0; --k) P = fma(P, w, so.mu[k]);   // the warp's n terms only
+    for (int k = n - 1; k > h; --k) Pd = df_mul_add(Pd, wd, so.mud[k]);
+    P = df_to_double(Pd);
+    top = h;
+  }
+#pragma unroll 1
+  for (int k = top; k >= 0; --k) P = fma(P, ws, so.mu[k]);   // the warp's leading terms
   const double S2 = P * P;
   if (KIND == KIND_I) return fma(0.5, ix_log_call(S2 * w * (8.0 / kTwoPi)), x);
   return fma(0.5, ix_log_call(S2 * w * (4.0 * kPi)), -x);
@@ -436,9 +526,17 @@ __device__ __forceinline__ double u_expr_so(const ScalarOrder& so, double x) {
     t = ix_rcp_call(r);
   }
   const double* C = K == 4 ? so.u4 : (K == 6 ? so.u6 : (K == 9 ? so.u9 : so.u13));
-  double S = C[3 * K];
+  const dfloat* Cd = K == 4 ? so.u4d : (K == 6 ? so.u6d : (K == 9 ? so.u9d : so.u13d));
+  // S = sum_m C_m t^m.  C_m for m >= 4 holds the parts of u_k, k >= 2 only
+  // (u_k has the powers t^k .. t^3k), at most about 2e-3 of the sum in the
+  // U regions: those terms in double-float, C_3 .. C_0 in FP64.
+  const dfloat td = df_from_double(t);
+  dfloat Sd = Cd[3 * K];
 #pragma unroll
-  for (int m = 3 * K - 1; m >= 0; --m) S = fma(S, t, C[m]);
+  for (int m = 3 * K - 1; m >= 4; --m) Sd = df_mul_add(Sd, td, Cd[m]);
+  double S = df_to_double(Sd);
+#pragma unroll
+  for (int m = 3; m >= 0; --m) S = fma(S, t, C[m]);
   const double eta = r + (ix_log_call(xp) - ix_log_call(1.0 + r));
   const double w = S * S * t * inv_v;
   if (KIND == KIND_I) return fma(v, eta, 0.5 * ix_log_call(w * (1.0 / kTwoPi)));

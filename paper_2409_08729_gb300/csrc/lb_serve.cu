@@ -62,6 +62,12 @@ constexpr int kKWindowMin = 512;       // smallest window of a class queue (pair
 // Costliest class first, as the phases of lb_kint_kernel: the split rule,
 // the 64- and 32-node fixed rules, the packed rule, the one-slot rules.
 constexpr int kKClassOrder[kKClasses] = {0, 5, 4, 3, 2, 1};
+// Item families of the device time accounts (lb_server_device_stats): FP64
+// tiles of log I and log K, FP32 tiles of log I and log K, FP64 K windows of
+// each rule class (or the one queue of the paper modes, as class 0), FP32 K
+// windows.
+constexpr int kFamilies = LB_SERVER_FAMILIES;
+static_assert(kFamilies == 4 + kKClasses + 1, "item families");
 
 struct SlotDesc {          // mapped host memory: written by the host, read by the device
   int kind;                // 0 = I, 1 = K
@@ -98,8 +104,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Shared memory of the persistent kernel: one tile, or the node table of a
 // K window with one order for all pairs.
 union ServeShared {
-  TileShared<double> d;
-  TileShared<float> f;
+  TileShared<double, LB_THREADS> d;
+  TileShared<float, LB_THREADS> f;
   KintScalar ks;
   KintScalar32 ks32;
 };
@@ -113,7 +119,7 @@ struct ServeAux {          // per-tile class counts and queue bases of the K pai
 // queue of their rule class (class 0 when the request has one queue); their
 // order within a queue does not change any result.
 template <int KIND, typename T>
-__device__ __forceinline__ void serve_tile(TileShared<T>& S, ServeAux& A, const SlotDesc& d, int64_t tile,
+__device__ __forceinline__ void serve_tile(TileShared<T, LB_THREADS>& S, ServeAux& A, const SlotDesc& d, int64_t tile,
                                            unsigned* qc) {
   const T* v = reinterpret_cast<const T*>(d.v);
   const T* x = reinterpret_cast<const T*>(d.x);
@@ -196,7 +202,8 @@ __device__ __forceinline__ void signal_system(int* flag) {
 __global__ void __launch_bounds__(LB_THREADS, LB_SERVE_CTAS_PER_SM)
 lb_serve_kernel(Ctl* ctl, const SlotDesc* slots, const WorkItem* ring, int ring_cap, unsigned long long* head,
                 long long* tiles_done, long long* kdone, unsigned* qcount, int* slot_done, int* stage_done,
-                unsigned* kcount, long long idle_ns) {
+                unsigned* kcount, long long idle_ns, unsigned long long* dstat,
+                unsigned long long* claim_pos) {
   __shared__ ServeShared U;
   __shared__ ServeAux A;
   __shared__ long long claimed;
@@ -204,10 +211,18 @@ lb_serve_kernel(Ctl* ctl, const SlotDesc* slots, const WorkItem* ring, int ring_
   __shared__ WorkItem item;
   cuda::atomic_ref<long long, cuda::thread_scope_system> tail_ref(ctl->tail);
   cuda::atomic_ref<int, cuda::thread_scope_system> stop_ref(ctl->stop);
+  // thread 0: the family of the item in hand and when it was claimed
+  int fam = -1;
+  unsigned long long t_item = 0;
   for (;;) {
     if (threadIdx.x == 0) {
+      const unsigned long long t_free = global_ns();
+      if (fam >= 0) {                              // device time of the item just finished
+        atomicAdd(dstat + 1 + fam, t_free - t_item);
+        atomicAdd(dstat + 1 + kFamilies + fam, 1ull);
+      }
       long long got = -1;
-      const unsigned long long deadline = global_ns() + (unsigned long long)idle_ns;
+      const unsigned long long deadline = t_free + (unsigned long long)idle_ns;
       for (;;) {
         if (stop_ref.load(cuda::memory_order_relaxed)) break;
         const long long t = tail_ref.load(cuda::memory_order_acquire);
@@ -220,10 +235,18 @@ lb_serve_kernel(Ctl* ctl, const SlotDesc* slots, const WorkItem* ring, int ring_
         __nanosleep(2000);
       }
       claimed = got;
+      fam = -1;
       if (got >= 0) {
+        // the ring position past this claim, for the host's count of items not yet taken
+        cuda::atomic_ref<unsigned long long, cuda::thread_scope_system> pos(claim_pos[blockIdx.x]);
+        pos.store((unsigned long long)got + 1ull, cuda::memory_order_relaxed);
         item = ring[got % ring_cap];
         desc = slots[item.slot];
+        fam = item.type == 0 ? (desc.dtype == LB_F64 ? 0 : 2) + desc.kind
+                             : (desc.dtype == LB_F64 ? 4 + (item.type - 1) : 4 + kKClasses);
       }
+      t_item = global_ns();
+      atomicAdd(dstat, t_item - t_free);           // claiming, and waiting for work
     }
     __syncthreads();
     if (claimed < 0) return;
@@ -366,6 +389,13 @@ struct lb_server {
   long long* d_tiles_done = nullptr;
   long long* d_kdone = nullptr;
   unsigned* d_qcount = nullptr;     // device [max_slots][8]: class queue counters (reset by the device)
+  unsigned long long* claim_pos = nullptr;     // mapped host memory [ctas]: ring position after each CTA's last claim
+  unsigned long long* d_claim_pos = nullptr;
+  int ctas = 0;                                  // CTAs of the persistent kernel
+  unsigned long long* d_dstat = nullptr;   // device [1 + 2 kFamilies]: claim ns, busy ns and items per family
+  unsigned long long* h_dstat = nullptr;   // pinned copy of d_dstat (lb_server_device_stats)
+  cudaStream_t s_stats = nullptr;
+  std::mutex stats_mu;
   char* d_arena = nullptr;
   cudaStream_t s_compute = nullptr, s_copy = nullptr;
   cudaEvent_t kernel_done = nullptr;
@@ -381,6 +411,9 @@ struct lb_server {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> free_slots;
   std::atomic<long long> kernel_launches{0};
+  // items ready but not yet published, per item family, with the time each became ready
+  std::deque<std::pair<WorkItem, double>> pend[kFamilies];
+  long long pend_count = 0;
 
   // shared, under mu
   std::mutex mu;
@@ -399,6 +432,8 @@ struct lb_server {
   bool step(std::vector<Request*>& finished);
   void publish_tiles(Request* r);
   void publish_k(Request* r);
+  void hold(int fam, const WorkItem& w, double t);
+  bool publish_runs();
   void finish(Request* r, std::vector<Request*>& finished);
   cudaEvent_t take_event();
   lb_status submit(Request* r, long long* ticket);
@@ -423,6 +458,46 @@ cudaEvent_t lb_server::take_event() {
   return e;
 }
 
+void lb_server::hold(int fam, const WorkItem& w, double t) {
+  pend[fam].push_back({w, t});
+  ++pend_count;
+}
+
+// Publishing.  Items of different families that run at the same time on an
+// SM slow each other down (measured with lb_server_device_stats on a mix of
+// the four request classes: the K-integral windows took 1.3x their time
+// served alone, the FP32 items 2.2-2.6x; the kernels share the SMs'
+// instruction caches).  So ready items wait in per-family lists and go to
+// the ring in runs of one family: whenever fewer than one item per CTA is
+// left untaken, the family whose oldest item has waited longest publishes
+// up to four items per CTA.  The CTAs then work through a run of one family
+// before the next; families mix only at the ends of runs.
+bool lb_server::publish_runs() {
+  if (pend_count == 0) return false;
+  unsigned long long head = 0;
+  for (int i = 0; i < ctas; ++i) {
+    const unsigned long long p = __atomic_load_n(&claim_pos[i], __ATOMIC_RELAXED);
+    head = p > head ? p : head;
+  }
+  long long ahead = tail - (long long)head;
+  bool progress = false;
+  while (ahead < ctas && pend_count > 0) {
+    int f = -1;
+    for (int g = 0; g < kFamilies; ++g)
+      if (!pend[g].empty() && (f < 0 || pend[g].front().second < pend[f].front().second)) f = g;
+    const long long m = std::min<long long>((long long)pend[f].size(), 4ll * ctas);
+    for (long long i = 0; i < m; ++i) {
+      ring[tail % ring_cap] = pend[f].front().first;
+      pend[f].pop_front();
+      ++tail;
+    }
+    pend_count -= m;
+    ahead += m;
+    progress = true;
+  }
+  return progress;
+}
+
 // Stage A of a request: its tiles, in at most kItemsPerRequest items; FP32
 // tiles are cheap, so an FP32 item holds at least four of them.
 void lb_server::publish_tiles(Request* r) {
@@ -430,13 +505,15 @@ void lb_server::publish_tiles(Request* r) {
   long long per = (nt + kItemsPerRequest - 1) / kItemsPerRequest;
   const long long min_tiles = r->dtype == LB_F64 ? 1 : 4;
   if (per < min_tiles) per = min_tiles;
+  const int fam = (r->dtype == LB_F64 ? 0 : 2) + r->kind;
+  const double t = now_s();
   for (long long b = 0; b < nt; b += per) {
-    WorkItem& w = ring[tail % ring_cap];
+    WorkItem w;
     w.slot = r->slot;
     w.begin = (int)b;
     w.end = (int)(b + per < nt ? b + per : nt);
     w.type = 0;
-    ++tail;
+    hold(fam, w, t);
   }
   r->state.store(RS_RUNNING, std::memory_order_relaxed);
   running.push_back(r);
@@ -445,6 +522,7 @@ void lb_server::publish_tiles(Request* r) {
 // Stage B of a K request: windows of each class queue, costliest class first.
 void lb_server::publish_k(Request* r) {
   const unsigned* kc = kcount + 8 * r->slot;
+  const double t = now_s();
   long long items = 0;
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) slots[r->slot].kitems = items;            // read by the device with the items
@@ -460,12 +538,12 @@ void lb_server::publish_k(Request* r) {
           ++items;
           continue;
         }
-        WorkItem& it = ring[tail % ring_cap];
+        WorkItem it;
         it.slot = r->slot;
         it.begin = (int)b;
         it.end = (int)(b + w < m ? b + w : m);
         it.type = 1 + c;
-        ++tail;
+        hold(r->dtype == LB_F64 ? 4 + c : 4 + kKClasses, it, t);
       }
     }
   }
@@ -592,15 +670,14 @@ bool lb_server::step(std::vector<Request*>& finished) {
       ++i;
     }
   }
+  if (publish_runs()) progress = true;
   if (tail != tail0) __atomic_store_n(&ctl->tail, tail, __ATOMIC_RELEASE);
   // keep the persistent kernel running while work is published
   if (kernel_live && cudaEventQuery(kernel_done) == cudaSuccess) kernel_live = false;
   if (!running.empty() && !kernel_live) {
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    lb_serve_kernel<<<sms * ctas_per_sm, LB_THREADS, 0, s_compute>>>(
+    lb_serve_kernel<<<ctas, LB_THREADS, 0, s_compute>>>(
         d_ctl, d_slots, d_ring, ring_cap, d_head, d_tiles_done, d_kdone, d_qcount, d_slot_done, d_stage_done,
-        d_kcount, idle_ns);
+        d_kcount, idle_ns, d_dstat, d_claim_pos);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       std::lock_guard<std::mutex> lk(mu);
@@ -705,35 +782,49 @@ lb_status lb_server_create(const lb_server_config* cfg, lb_server** out) {
   s->ring_cap = cfg->max_slots * 2 * (kItemsPerRequest + kKClasses * kKItemsPerClass);
   s->ctas_per_sm = cfg->ctas_per_sm;
   s->idle_ns = (long long)(cfg->idle_ms * 1e6);
+  {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    s->ctas = sms * cfg->ctas_per_sm;
+  }
   const size_t ms = (size_t)cfg->max_slots;
   bool ok = cudaHostAlloc((void**)&s->ctl, sizeof(Ctl), cudaHostAllocMapped) == cudaSuccess &&
             cudaHostAlloc((void**)&s->slots, sizeof(SlotDesc) * ms, cudaHostAllocMapped) == cudaSuccess &&
             cudaHostAlloc((void**)&s->ring, sizeof(WorkItem) * s->ring_cap, cudaHostAllocMapped) == cudaSuccess &&
             cudaHostAlloc((void**)&s->slot_done, sizeof(int) * ms, cudaHostAllocMapped) == cudaSuccess &&
             cudaHostAlloc((void**)&s->stage_done, sizeof(int) * ms, cudaHostAllocMapped) == cudaSuccess &&
-            cudaHostAlloc((void**)&s->kcount, sizeof(unsigned) * 8 * ms, cudaHostAllocMapped) == cudaSuccess;
+            cudaHostAlloc((void**)&s->kcount, sizeof(unsigned) * 8 * ms, cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostAlloc((void**)&s->claim_pos, sizeof(unsigned long long) * s->ctas, cudaHostAllocMapped) ==
+                cudaSuccess;
   if (ok) {
     memset(s->ctl, 0, sizeof(Ctl));
     memset(s->slot_done, 0, sizeof(int) * ms);
     memset(s->stage_done, 0, sizeof(int) * ms);
     memset(s->kcount, 0, sizeof(unsigned) * 8 * ms);
+    memset(s->claim_pos, 0, sizeof(unsigned long long) * s->ctas);
     ok = cudaHostGetDevicePointer((void**)&s->d_ctl, s->ctl, 0) == cudaSuccess &&
          cudaHostGetDevicePointer((void**)&s->d_slots, s->slots, 0) == cudaSuccess &&
          cudaHostGetDevicePointer((void**)&s->d_ring, s->ring, 0) == cudaSuccess &&
          cudaHostGetDevicePointer((void**)&s->d_slot_done, s->slot_done, 0) == cudaSuccess &&
          cudaHostGetDevicePointer((void**)&s->d_stage_done, s->stage_done, 0) == cudaSuccess &&
          cudaHostGetDevicePointer((void**)&s->d_kcount, s->kcount, 0) == cudaSuccess &&
+         cudaHostGetDevicePointer((void**)&s->d_claim_pos, s->claim_pos, 0) == cudaSuccess &&
          cudaMalloc((void**)&s->d_head, sizeof(unsigned long long)) == cudaSuccess &&
          cudaMalloc((void**)&s->d_tiles_done, sizeof(long long) * ms) == cudaSuccess &&
          cudaMalloc((void**)&s->d_kdone, sizeof(long long) * ms) == cudaSuccess &&
          cudaMalloc((void**)&s->d_qcount, sizeof(unsigned) * 8 * ms) == cudaSuccess &&
          cudaMalloc((void**)&s->d_arena, (size_t)cfg->arena_bytes) == cudaSuccess &&
+         cudaMalloc((void**)&s->d_dstat, sizeof(unsigned long long) * (1 + 2 * kFamilies)) == cudaSuccess &&
+         cudaHostAlloc((void**)&s->h_dstat, sizeof(unsigned long long) * (1 + 2 * kFamilies),
+                       cudaHostAllocDefault) == cudaSuccess &&
+         cudaMemset(s->d_dstat, 0, sizeof(unsigned long long) * (1 + 2 * kFamilies)) == cudaSuccess &&
          cudaMemset(s->d_head, 0, sizeof(unsigned long long)) == cudaSuccess &&
          cudaMemset(s->d_tiles_done, 0, sizeof(long long) * ms) == cudaSuccess &&
          cudaMemset(s->d_kdone, 0, sizeof(long long) * ms) == cudaSuccess &&
          cudaMemset(s->d_qcount, 0, sizeof(unsigned) * 8 * ms) == cudaSuccess &&
          cudaStreamCreateWithFlags(&s->s_compute, cudaStreamNonBlocking) == cudaSuccess &&
          cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&s->s_stats, cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&s->kernel_done, cudaEventDisableTiming) == cudaSuccess;
   }
   if (!ok) {
@@ -819,6 +910,24 @@ lb_status lb_server_stats(lb_server* s, long long* completed, long long* evals, 
   return LB_OK;
 }
 
+lb_status lb_server_device_stats(lb_server* s, long long* claim_ns, long long* busy_ns, long long* items) {
+  if (!s) return serve_fail(LB_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lk(s->stats_mu);
+  const size_t nb = sizeof(unsigned long long) * (1 + 2 * kFamilies);
+  // a copy engine reads the counters while the persistent kernel runs (its own non-blocking stream)
+  if (cudaMemcpyAsync(s->h_dstat, s->d_dstat, nb, cudaMemcpyDeviceToHost, s->s_stats) != cudaSuccess ||
+      cudaStreamSynchronize(s->s_stats) != cudaSuccess) {
+    cudaGetLastError();
+    return serve_fail(LB_ECUDA, "reading the device counters failed");
+  }
+  if (claim_ns) *claim_ns = (long long)s->h_dstat[0];
+  for (int f = 0; f < kFamilies; ++f) {
+    if (busy_ns) busy_ns[f] = (long long)s->h_dstat[1 + f];
+    if (items) items[f] = (long long)s->h_dstat[1 + kFamilies + f];
+  }
+  return LB_OK;
+}
+
 lb_status lb_server_destroy(lb_server* s) {
   if (!s) return LB_OK;
   if (s->sched.joinable()) {
@@ -838,12 +947,16 @@ lb_status lb_server_destroy(lb_server* s) {
   if (s->kernel_done) cudaEventDestroy(s->kernel_done);
   if (s->s_compute) cudaStreamDestroy(s->s_compute);
   if (s->s_copy) cudaStreamDestroy(s->s_copy);
+  if (s->s_stats) cudaStreamDestroy(s->s_stats);
+  cudaFree(s->d_dstat);
+  if (s->h_dstat) cudaFreeHost(s->h_dstat);
   cudaFree(s->d_arena);
   cudaFree(s->d_qcount);
   cudaFree(s->d_kdone);
   cudaFree(s->d_tiles_done);
   cudaFree(s->d_head);
   if (s->kcount) cudaFreeHost(s->kcount);
+  if (s->claim_pos) cudaFreeHost(s->claim_pos);
   if (s->stage_done) cudaFreeHost(s->stage_done);
   if (s->slot_done) cudaFreeHost(s->slot_done);
   if (s->ring) cudaFreeHost(s->ring);

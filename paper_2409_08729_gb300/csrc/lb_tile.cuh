@@ -2,7 +2,7 @@
 //
 // The paper sorts all pairs by expression before launching one thread per
 // pair (Sec. 4.3), so that warps do not diverge.  Here the grouping happens
-// on chip, per tile of LB_TILE pairs:
+// on chip, per tile of NT * LB_ITEMS pairs (NT threads per block):
 //   tile_bin   loads the tile (coalesced, two pairs per load instruction),
 //              handles domain edges, classifies the rest (Table "input
 //              ranges") and sorts the pairs into one shared-memory list by
@@ -23,13 +23,16 @@
 #include "lb_expr32.cuh"
 #include "lb_kint.cuh"
 
+// Threads per block of the serving kernel and of the K-integral and
+// auxiliary kernels; the per-call tile kernel takes its own block size
+// (LB_TILE_THREADS in logbessel.cu).  A tile holds LB_ITEMS pairs per thread.
 #ifndef LB_THREADS
 #define LB_THREADS 256
 #endif
 #ifndef LB_ITEMS
 #define LB_ITEMS 4
 #endif
-#define LB_TILE (LB_THREADS * LB_ITEMS)
+#define LB_TILE (LB_THREADS * LB_ITEMS)            // tile of the serving kernel
 
 namespace lb {
 
@@ -75,17 +78,20 @@ __host__ __device__ constexpr int region_key_end(int r) {
   return r == R_MU20 ? KEY_MU20 + 20 : r == R_FALLBACK ? KEY_FB + 15 : region_key_first(r) + 1;
 }
 
-template <typename T>
+// One tile of NT * LB_ITEMS pairs in the shared memory of a block of NT threads.
+template <typename T, int NT>
 struct TileShared {
-  T sv[LB_TILE];
+  static constexpr int kThreads = NT;
+  static constexpr int kTile = NT * LB_ITEMS;
+  T sv[kTile];
   union {                                          // a pair's result replaces its argument
-    T sx[LB_TILE];
-    T sres[LB_TILE];                               // results, stored coalesced at the end of the tile
+    T sx[kTile];
+    T sres[kTile];                                 // results, stored coalesced at the end of the tile
   };
-  uint16_t list[LB_TILE];                          // tile offsets of the pairs to evaluate, sorted by key
-  uint8_t nt[LB_TILE];                             // estimated term count (mu_20; FP64 values)
-  uint8_t keep[LB_TILE];                           // 1: sres holds this pair's result
-  uint16_t wcount[LB_ITEMS][LB_THREADS / 32][NKEYS];   // pairs per (item round, warp, key), then offsets
+  uint16_t list[kTile];                            // tile offsets of the pairs to evaluate, sorted by key
+  uint8_t nt[kTile];                               // estimated term count (mu_20; FP64 values)
+  uint8_t keep[kTile];                             // 1: sres holds this pair's result
+  uint16_t wcount[LB_ITEMS][NT / 32][NKEYS];       // pairs per (item round, warp, key), then offsets
   int kbeg[NKEYS + 1];                             // start of each key's range in list
   int next_chunk[8];                               // per region: next chunk of 32 pairs to hand out (tile_eval)
   unsigned int qbase;
@@ -165,8 +171,9 @@ __device__ __forceinline__ int tile_key(int r, T v, T x, int* n) {
 // Tile offset of item round `it` of thread `tid`: each thread handles two
 // adjacent pairs per pair of rounds, so it loads and stores them with one
 // 16-byte (FP64) or 8-byte (FP32) instruction.
+template <int NT>
 __device__ __forceinline__ int tile_offset(int it, int tid) {
-  return (it >> 1) * (2 * LB_THREADS) + 2 * tid + (it & 1);
+  return (it >> 1) * (2 * NT) + 2 * tid + (it & 1);
 }
 
 template <typename T>
@@ -176,26 +183,26 @@ struct Vec2<double> { typedef double2 type; };
 template <>
 struct Vec2<float> { typedef float2 type; };
 
-// Load, edge-handle, classify and sort pairs [t0, min(t0 + LB_TILE, n)).
+// Load, edge-handle, classify and sort pairs [t0, min(t0 + NT * LB_ITEMS, n)).
 // All threads of the block call it; it ends with a barrier.  The list is
 // ordered by (key, item round, warp, lane), from one warp match per item
 // and a per-key prefix over (item round, warp): the order, and so the warp
 // mates of every pair, do not depend on scheduling.
-template <int KIND, bool DX, typename T>
-__device__ __forceinline__ void tile_bin(TileShared<T>& S, const T* __restrict__ v, int64_t v_stride,
+template <int KIND, bool DX, typename T, int NT>
+__device__ __forceinline__ void tile_bin(TileShared<T, NT>& S, const T* __restrict__ v, int64_t v_stride,
                                          const T* __restrict__ x, int64_t t0, int64_t n, int mode,
                                          int forced_region) {
   typedef typename Vec2<T>::type T2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned int lt = (1u << lane) - 1u;
-  // the pair offsets t0 are multiples of LB_TILE, so aligned bases keep every pair of loads aligned
+  // the pair offsets t0 are multiples of the tile size, so aligned bases keep every pair of loads aligned
   const bool vec = ((reinterpret_cast<uintptr_t>(x) | (v_stride ? reinterpret_cast<uintptr_t>(v) : 0)) &
                     (2 * sizeof(T) - 1)) == 0;
   const T v0 = v_stride ? T(0) : v[0];
   T vv[LB_ITEMS], xx[LB_ITEMS];
 #pragma unroll
   for (int h = 0; h < LB_ITEMS / 2; ++h) {
-    const int li = tile_offset(2 * h, tid);
+    const int li = tile_offset<NT>(2 * h, tid);
     const int64_t i = t0 + li;
     if (vec && i + 1 < n) {
       const T2 xv = *reinterpret_cast<const T2*>(x + i);
@@ -219,7 +226,7 @@ __device__ __forceinline__ void tile_bin(TileShared<T>& S, const T* __restrict__
   int key[LB_ITEMS], rank[LB_ITEMS];
 #pragma unroll
   for (int it = 0; it < LB_ITEMS; ++it) {
-    const int li = tile_offset(it, tid);
+    const int li = tile_offset<NT>(it, tid);
     const int64_t i = t0 + li;
     int k = NKEYS;                                 // NKEYS: no list entry
     uint8_t keep = 0;
@@ -255,7 +262,7 @@ __device__ __forceinline__ void tile_bin(TileShared<T>& S, const T* __restrict__
   if (tid < NKEYS) {
     int acc = 0;
     for (int it = 0; it < LB_ITEMS; ++it)
-      for (int w = 0; w < LB_THREADS / 32; ++w) {
+      for (int w = 0; w < NT / 32; ++w) {
         const int c = S.wcount[it][w][tid];
         S.wcount[it][w][tid] = (uint16_t)acc;
         acc += c;
@@ -283,7 +290,7 @@ __device__ __forceinline__ void tile_bin(TileShared<T>& S, const T* __restrict__
   for (int it = 0; it < LB_ITEMS; ++it)
     if (key[it] < NKEYS) {
       const int pos = S.kbeg[key[it]] + S.wcount[it][warp][key[it]] + rank[it];
-      if (LB_CHECK(pos >= 0 && pos < LB_TILE, 1u)) S.list[pos] = (uint16_t)tile_offset(it, tid);
+      if (LB_CHECK(pos >= 0 && pos < (NT * LB_ITEMS), 1u)) S.list[pos] = (uint16_t)tile_offset<NT>(it, tid);
     }
   __syncthreads();
 }
@@ -308,8 +315,8 @@ __device__ __forceinline__ double tile_expr_so(int r, const ScalarOrder& so, dou
 // range recompute the chunk's first entry and do not keep it.  `so` (FP64
 // values only) holds the constants of a call whose pairs all have one
 // order, or is NULL.
-template <int KIND, bool DX, typename T, int R>
-__device__ __forceinline__ void tile_eval_region(TileShared<T>& S, int lane, const ScalarOrder* so) {
+template <int KIND, bool DX, typename T, int R, int NT>
+__device__ __forceinline__ void tile_eval_region(TileShared<T, NT>& S, int lane, const ScalarOrder* so) {
   const int b0 = S.rbeg(R), c = S.rend(R) - b0;
   const int nch = (c + 31) >> 5;
   for (;;) {
@@ -320,7 +327,7 @@ __device__ __forceinline__ void tile_eval_region(TileShared<T>& S, int lane, con
     const int j0 = id << 5, j = j0 + lane;
     bool ok = j < c;
     int jl = b0 + (ok ? j : j0);
-    if (!LB_CHECK(jl >= 0 && jl < LB_TILE, 2u)) {
+    if (!LB_CHECK(jl >= 0 && jl < (NT * LB_ITEMS), 2u)) {
       jl = 0;                                      // clamped: the warp still runs the expression together
       ok = false;
     }
@@ -348,23 +355,23 @@ __device__ __forceinline__ void tile_eval_region(TileShared<T>& S, int lane, con
 // instruction where both are kept and the buffer is aligned.  The K fallback
 // pairs are left to the K integral: neither evaluated nor stored (so out may
 // equal x: their arguments stay in place for it).  Ends with a barrier.
-template <int KIND, bool DX, typename T>
-__device__ __forceinline__ void tile_eval(TileShared<T>& S, T* __restrict__ out, int64_t t0, int64_t n,
+template <int KIND, bool DX, typename T, int NT>
+__device__ __forceinline__ void tile_eval(TileShared<T, NT>& S, T* __restrict__ out, int64_t t0, int64_t n,
                                           const ScalarOrder* so = nullptr) {
   typedef typename Vec2<T>::type T2;
   const int tid = threadIdx.x, lane = tid & 31;
-  if (KIND == KIND_I) tile_eval_region<KIND, DX, T, R_FALLBACK>(S, lane, so);
-  tile_eval_region<KIND, DX, T, R_U13>(S, lane, so);
-  tile_eval_region<KIND, DX, T, R_U9>(S, lane, so);
-  tile_eval_region<KIND, DX, T, R_MU20>(S, lane, so);
-  tile_eval_region<KIND, DX, T, R_U6>(S, lane, so);
-  tile_eval_region<KIND, DX, T, R_MU3>(S, lane, so);
-  tile_eval_region<KIND, DX, T, R_U4>(S, lane, so);
+  if (KIND == KIND_I) tile_eval_region<KIND, DX, T, R_FALLBACK, NT>(S, lane, so);
+  tile_eval_region<KIND, DX, T, R_U13, NT>(S, lane, so);
+  tile_eval_region<KIND, DX, T, R_U9, NT>(S, lane, so);
+  tile_eval_region<KIND, DX, T, R_MU20, NT>(S, lane, so);
+  tile_eval_region<KIND, DX, T, R_U6, NT>(S, lane, so);
+  tile_eval_region<KIND, DX, T, R_MU3, NT>(S, lane, so);
+  tile_eval_region<KIND, DX, T, R_U4, NT>(S, lane, so);
   __syncthreads();
   const bool vec = (reinterpret_cast<uintptr_t>(out) & (2 * sizeof(T) - 1)) == 0;
 #pragma unroll
   for (int h = 0; h < LB_ITEMS / 2; ++h) {
-    const int li = tile_offset(2 * h, tid);
+    const int li = tile_offset<NT>(2 * h, tid);
     const int64_t i = t0 + li;
     const bool k0 = i < n && S.keep[li], k1 = i + 1 < n && S.keep[li + 1];
     if (vec && k0 && k1) {

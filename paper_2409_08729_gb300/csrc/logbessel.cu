@@ -3,7 +3,7 @@
 // Pipeline for one call (paper Sec. 4.3 sorts the pairs by expression before
 // launch so that warps do not diverge; here the grouping is done on chip):
 //
-//   1. lb_tiles_kernel: persistent CTAs walk tiles of LB_TILE pairs.  Each
+//   1. lb_tiles_kernel: persistent CTAs walk tiles of kTile pairs.  Each
 //      thread loads LB_ITEMS pairs (coalesced), handles domain edges, and
 //      classifies the rest (Table "input ranges").  The tile's pairs are
 //      binned per region into shared-memory index lists; the warps take
@@ -39,8 +39,18 @@ namespace {
 
 // Resident CTAs per SM the two kernels are built and launched for (launch
 // bounds and persistent grid sizes: a multiple of the SM count).
+// The tile kernel runs blocks of LB_TILE_THREADS threads, so a tile holds
+// LB_TILE_THREADS * LB_ITEMS pairs: 2048 at 512 threads.  Larger tiles leave
+// fewer partly filled 32-pair chunks at the end of each region's range of a
+// tile (lanes that idle through an expression); at 512 threads and 3 CTAs
+// per SM the SM keeps its 48 resident warps and 40 registers a thread, and
+// the sweep's tile kernel time fell 4 % against 1024-pair tiles (256
+// threads, 6 CTAs per SM).
+#ifndef LB_TILE_THREADS
+#define LB_TILE_THREADS 512
+#endif
 #ifndef LB_TILES_CTAS_PER_SM
-#define LB_TILES_CTAS_PER_SM 6
+#define LB_TILES_CTAS_PER_SM 3
 #endif
 #ifndef LB_KINT_CTAS_PER_SM
 #define LB_KINT_CTAS_PER_SM 4
@@ -73,6 +83,9 @@ __host__ __device__ constexpr int kint_ctas_per_sm(int cls) {
 // at most 2^26 pairs) in the low 26 bits, the quadrature rule class of the
 // FP64 Gauss rules (kint_class; 0 otherwise) above them, so that a kernel
 // that takes one class finds its pairs by reading the queue alone.
+constexpr int kTileThreads = LB_TILE_THREADS;
+constexpr int kTile = kTileThreads * LB_ITEMS;     // pairs per tile of the tile kernel
+static_assert((1 << 26) % kTile == 0, "chunks of 2^26 pairs hold whole tiles");
 constexpr int kQueueOffsetBits = 26;
 constexpr uint32_t kQueueOffsetMask = (1u << kQueueOffsetBits) - 1u;
 
@@ -80,13 +93,13 @@ constexpr uint32_t kQueueOffsetMask = (1u << kQueueOffsetBits) - 1u;
 // per-thread expressions (lb_tile.cuh); K fallback pairs go to a global queue
 // for lb_kint_kernel.  T = double (FP64) or float (FP32-mixed).
 template <int KIND, bool DX, typename T>
-__global__ void __launch_bounds__(LB_THREADS, LB_TILES_CTAS_PER_SM)
+__global__ void __launch_bounds__(kTileThreads, LB_TILES_CTAS_PER_SM)
 lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
                 int64_t n, int mode, int forced_region, unsigned int* __restrict__ qcount,
                 uint32_t* __restrict__ queue, int64_t qcap) {
-  __shared__ TileShared<T> S;
+  __shared__ TileShared<T, kTileThreads> S;
   const int tid = threadIdx.x;
-  const int64_t ntiles = (n + LB_TILE - 1) / LB_TILE;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
   const ScalarOrder* so = nullptr;
   if constexpr (sizeof(T) == 8 && !DX) {
     // one order for every argument: its constants once per block
@@ -97,7 +110,7 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
     }
   }
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t t0 = tile * LB_TILE;
+    const int64_t t0 = tile * kTile;
     tile_bin<KIND, DX, T>(S, v, v_stride, x, t0, n, mode, forced_region);
     tile_eval<KIND, DX, T>(S, out, t0, n, so);
     if (KIND == KIND_K) {
@@ -107,7 +120,7 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
         __syncthreads();
         const unsigned int b = S.qbase;
         unsigned cls = 0;                          // quadrature rule classes of the queued pairs
-        for (int j = tid; j < c; j += LB_THREADS) {
+        for (int j = tid; j < c; j += kTileThreads) {
           const int li = S.list[f0 + j];
           uint32_t cl = 0;
           if constexpr (sizeof(T) == 8) {
@@ -431,6 +444,9 @@ lb_status launch_kint_classes(int sms, cudaStream_t st, const T* v, int64_t v_st
 
 // Largest chunk handled with one queue: the queue entries hold 26-bit offsets.
 const int64_t kChunk = (int64_t)1 << kQueueOffsetBits;
+// Smallest caller workspace: the counters and the queue of one tile.
+const int64_t kWsMin = 256 + 4 * kTile;
+static_assert(256 + 4 * kTile == 8448, "the documented smallest workspace");
 
 // Enqueue the evaluation of n pairs.  The K fallback goes through a queue
 // of 32-bit pair offsets in scratch memory (qcount: the counter and the
@@ -441,11 +457,11 @@ template <int KIND, bool DX, typename T>
 lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, int mode, int forced_region,
                    cudaStream_t st, void* scratch, int64_t chunk) {
   const int sms = sm_count();
-  const int64_t ntiles_all = (n + LB_TILE - 1) / LB_TILE;
+  const int64_t ntiles_all = (n + kTile - 1) / kTile;
   if (KIND == KIND_I || (forced_region >= 0 && forced_region != R_FALLBACK)) {
     const int grid = (int)(ntiles_all < (int64_t)sms * LB_TILES_CTAS_PER_SM ? ntiles_all : (int64_t)sms * LB_TILES_CTAS_PER_SM);
     return launch(PS_TILES, st, [&] {
-      lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, n, mode, forced_region,
+      lb_tiles_kernel<KIND, DX, T><<<grid, kTileThreads, 0, st>>>(v, v_stride, x, out, n, mode, forced_region,
                                                                  nullptr, nullptr, 0);
     });
   }
@@ -470,10 +486,10 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
     const T* vc = v + c0 * v_stride;
     const T* xc = x + c0;
     T* oc = out + c0;
-    const int64_t ntiles = (cn + LB_TILE - 1) / LB_TILE;
+    const int64_t ntiles = (cn + kTile - 1) / kTile;
     const int grid = (int)(ntiles < (int64_t)sms * LB_TILES_CTAS_PER_SM ? ntiles : (int64_t)sms * LB_TILES_CTAS_PER_SM);
     status = launch(PS_TILES, st, [&] {
-      lb_tiles_kernel<KIND, DX, T><<<grid, LB_THREADS, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount,
+      lb_tiles_kernel<KIND, DX, T><<<grid, kTileThreads, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount,
                                                                  queue, cap);
     });
     if (status != LB_OK) break;
@@ -603,20 +619,21 @@ lb_status logbessel_k_noalloc(lb_dtype dtype, const void* v, int64_t v_stride, c
 
 int64_t logbessel_workspace_bytes(int64_t n) {
   if (n < 0) return 0;
-  return 256 + 4 * (n < kChunk ? n : kChunk);
+  const int64_t m = (n + kTile - 1) / kTile * kTile;        // passes hold whole tiles
+  return 256 + 4 * (m < kTile ? kTile : (m < kChunk ? m : kChunk));
 }
 
 lb_status logbessel_k_ws(lb_dtype dtype, const void* v, int64_t v_stride, const void* x, void* out, int64_t n,
                          lb_mode mode, void* workspace, int64_t ws_bytes, void* cuda_stream) {
   lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
   if (s != LB_OK) return s;
-  if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < 256 + 4 * 1024)
-    return fail(LB_EINVAL, "%sworkspace must be non-NULL, 256-byte aligned and at least 4352 bytes (got %lld)", "",
+  if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < kWsMin)
+    return fail(LB_EINVAL, "%sworkspace must be non-NULL, 256-byte aligned and at least 8448 bytes (got %lld)", "",
                 (long long)ws_bytes);
   if (n == 0) return LB_OK;
   // passes start on tile boundaries, so the results equal those of one pass
   const int64_t cap0 = (ws_bytes - 256) / 4;
-  const int64_t cap = ((cap0 < kChunk ? cap0 : kChunk) / LB_TILE) * LB_TILE;
+  const int64_t cap = ((cap0 < kChunk ? cap0 : kChunk) / kTile) * kTile;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (dtype == LB_F32)
     return run_impl<KIND_K, false, float>((const float*)v, v_stride, (const float*)x, (float*)out, n, (int)mode, -1,
@@ -629,15 +646,15 @@ lb_status logbessel_k_dx_ws(lb_dtype dtype, const void* v, int64_t v_stride, con
                             lb_mode mode, void* workspace, int64_t ws_bytes, void* cuda_stream) {
   lb_status s = validate(dtype, v, v_stride, x, out, n, (int)mode);
   if (s != LB_OK) return s;
-  if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < 256 + 4 * 1024)
-    return fail(LB_EINVAL, "%sworkspace must be non-NULL, 256-byte aligned and at least 4352 bytes (got %lld)", "",
+  if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < kWsMin)
+    return fail(LB_EINVAL, "%sworkspace must be non-NULL, 256-byte aligned and at least 8448 bytes (got %lld)", "",
                 (long long)ws_bytes);
   if (n == 0) return LB_OK;
   if (dtype != LB_F64) return fail(LB_ENOTSUP, "%sthe derivatives are implemented for LB_F64 only", "", 0);
   if (mode != LB_TIGHT) return fail(LB_ENOTSUP, "%sd/dx log K is implemented for LB_TIGHT only", "", 0);
   // passes start on tile boundaries, so the results equal those of one pass
   const int64_t cap0 = (ws_bytes - 256) / 4;
-  const int64_t cap = ((cap0 < kChunk ? cap0 : kChunk) / LB_TILE) * LB_TILE;
+  const int64_t cap = ((cap0 < kChunk ? cap0 : kChunk) / kTile) * kTile;
   return run_impl<KIND_K, true, double>((const double*)v, v_stride, (const double*)x, (double*)out, n, (int)mode, -1,
                                         (cudaStream_t)cuda_stream, workspace, cap);
 }
@@ -818,7 +835,7 @@ lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride
   // the last copy-out, which nothing overlaps, are short; piece edges stay
   // on tile boundaries (chunk a multiple of 8 tiles), so the results equal
   // those of one pass.
-  const bool ramp = chunk % (8 * LB_TILE) == 0;
+  const bool ramp = chunk % (8 * kTile) == 0;
   int64_t cn = 0;
   for (int64_t c0 = 0, i = 0; s == LB_OK && c0 < n; c0 += cn, ++i) {
     const int64_t r = n - c0;
@@ -826,7 +843,7 @@ lb_status logbessel_host(int fn, lb_dtype dtype, const void* v, int64_t v_stride
     if (ramp) {
       if (i < 3) cn = chunk >> (3 - i);
       if (r <= chunk) {
-        const int64_t half = (r / 2) / LB_TILE * LB_TILE;
+        const int64_t half = (r / 2) / kTile * kTile;
         cn = half > chunk / 8 ? half : chunk / 8;
       }
     }

@@ -32,12 +32,13 @@ def _lib():
         L.lb_server_ticket_info.argtypes = [vp, ll, ctypes.POINTER(i32), dp, dp, dp]
         L.lb_server_release.argtypes = [vp, ll]
         L.lb_server_stats.argtypes = [vp] + [ctypes.POINTER(ll)] * 4
+        L.lb_server_device_stats.argtypes = [vp] + [ctypes.POINTER(ll)] * 3
         L.lb_server_destroy.argtypes = [vp]
         L.lb_server_last_error.argtypes = []
         L.lb_server_last_error.restype = ctypes.c_char_p
         for nm in ("lb_server_create", "lb_server_submit", "lb_server_submit_device", "lb_server_wait",
                    "lb_server_ticket_info",
-                   "lb_server_release", "lb_server_stats", "lb_server_destroy"):
+                   "lb_server_release", "lb_server_stats", "lb_server_device_stats", "lb_server_destroy"):
             getattr(L, nm).restype = i32
         L._serve_ready = True
     return L
@@ -144,6 +145,21 @@ class Server:
         v = [ctypes.c_longlong() for _ in range(4)]
         _check(_lib().lb_server_stats(self._h, *[ctypes.byref(a) for a in v]))
         return dict(zip(("completed", "evals", "kernel_launches", "in_flight"), [a.value for a in v]))
+
+    FAMILIES = ("tiles_i_f64", "tiles_k_f64", "tiles_i_f32", "tiles_k_f32", "kint_f64_c0", "kint_f64_c1",
+                "kint_f64_c2", "kint_f64_c3", "kint_f64_c4", "kint_f64_c5", "kint_f32")
+
+    def device_stats(self):
+        """The persistent kernel's device time accounts, cumulative: claim_ns
+        (claiming and waiting for items, summed over CTAs), and per item
+        family the summed busy ns and the items run."""
+        nf = len(self.FAMILIES)
+        claim = ctypes.c_longlong()
+        busy = (ctypes.c_longlong * nf)()
+        items = (ctypes.c_longlong * nf)()
+        _check(_lib().lb_server_device_stats(self._h, ctypes.byref(claim), busy, items))
+        return {"claim_ns": claim.value, "busy_ns": dict(zip(self.FAMILIES, list(busy))),
+                "items": dict(zip(self.FAMILIES, list(items)))}
 
     def close(self):
         if self._h:

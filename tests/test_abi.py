@@ -90,8 +90,9 @@ def test_python_api_requires_cuda_tensors():
 def test_workspace_entry_points_validate(L):
     """Workspace size rule and argument checks of the caller-workspace K entry points (no launch)."""
     from paper_2409_08729_gb300 import _binding as B
-    assert L.logbessel_workspace_bytes(0) == 256
-    assert L.logbessel_workspace_bytes(1000) == 256 + 4000
+    assert L.logbessel_workspace_bytes(0) == 256 + 4 * 2048
+    assert L.logbessel_workspace_bytes(1000) == 256 + 4 * 2048
+    assert L.logbessel_workspace_bytes(5000) == 256 + 4 * 6144
     assert L.logbessel_workspace_bytes(1 << 30) == 256 + 4 * (1 << 26)
     assert L.logbessel_workspace_bytes(-1) == 0
     buf = ctypes.create_string_buffer(64)

@@ -110,10 +110,10 @@ def test_checked_build_matches_release_and_stays_clear(libs, cuda):
                 assert _same(_run(R, fn, B.LB_F64, tv, 1, tx, n, mode, (stream,)),
                              _run(C, fn, B.LB_F64, tv, 1, tx, n, mode, (stream,))), (fn, n, mode)
                 cases += 1
-        # a caller workspace of 1024-pair passes, and the entry point without allocation
-        ws = torch.empty(4352 // 8, dtype=torch.float64, device=cuda)
-        assert _same(_run(R, "logbessel_k_ws", B.LB_F64, tv, 1, tx, n, 0, (ws.data_ptr(), 4352, stream)),
-                     _run(C, "logbessel_k_ws", B.LB_F64, tv, 1, tx, n, 0, (ws.data_ptr(), 4352, stream)))
+        # a caller workspace of 2048-pair passes, and the entry point without allocation
+        ws = torch.empty(8448 // 8, dtype=torch.float64, device=cuda)
+        assert _same(_run(R, "logbessel_k_ws", B.LB_F64, tv, 1, tx, n, 0, (ws.data_ptr(), 8448, stream)),
+                     _run(C, "logbessel_k_ws", B.LB_F64, tv, 1, tx, n, 0, (ws.data_ptr(), 8448, stream)))
         assert _same(_run(R, "logbessel_k", B.LB_F64, tv, 1, tx, n, extra=(stream,)),
                      _run(C, "logbessel_k_noalloc", B.LB_F64, tv, 1, tx, n, extra=(stream,)))
         cases += 2

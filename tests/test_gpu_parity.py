@@ -97,6 +97,35 @@ def test_scalar_order(cuda, kind):
 
 
 @pytest.mark.parametrize("kind", ["i", "k"])
+def test_scalar_order_every_region(cuda, kind):
+    """One order per call in the range of every expansion (per-order
+    constants, high-order terms in double-float): mu_20 at small and large
+    orders, U_13, U_9, U_6, U_4, x from 1e-3 to 1e5."""
+    rng = np.random.default_rng(4)
+    for v0 in (3.0, 12.0, 20.0, 40.0, 100.0, 400.0, 3000.0):
+        x = np.exp(rng.uniform(np.log(1e-3), np.log(1e5), 2000))
+        v = np.full_like(x, v0)
+        ref, scale = _ref(kind, v, x)
+        got = _run(kind, v, x, cuda, scalar_v=True)
+        _report(kind, v, x, got, ref, scale, TOL64)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_huge_scalar_order_large_argument(cuda, kind):
+    """v = 1e10 where the large-argument expansion applies (v^2 < 3.24 x):
+    the per-order coefficients a_k of a single-order call would overflow
+    unscaled (a_20 ~ (4 v^2)^20 / 20!); scaled, the call agrees with the
+    per-pair path on the same pairs, and both are finite.  The error floor
+    of the metric is about x here (x d/dx log f ~ x)."""
+    x = np.exp(np.random.default_rng(5).uniform(np.log(3.1e19), np.log(1e24), 2000))
+    v = np.full_like(x, 1e10)
+    got_s = _run(kind, v, x, cuda, scalar_v=True)
+    got_p = _run(kind, v, x, cuda)
+    assert np.all(np.isfinite(got_s)) and np.all(np.isfinite(got_p))
+    assert np.max(np.abs(got_s - got_p) / np.maximum(np.abs(got_p), x)) <= TOL64
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
 def test_region_boundaries(cuda, kind):
     """Pairs straddling every threshold of the paper's table and of the tight dispatch."""
     v, x = W.boundary_pairs(seed=5)

@@ -215,3 +215,35 @@ def test_relaunch_after_idle(cuda):
         srv.wait(srv.submit("i", v, x, o2), timeout=30)
         assert srv.stats()["kernel_launches"] >= 2
         assert np.array_equal(o1, o2)
+
+
+def test_device_time_accounts(cuda):
+    """The persistent kernel's device time accounts: the items of each family
+    are counted (tiles per item as the scheduler splits them), their busy time
+    is positive, and the counters only grow."""
+    rng = np.random.default_rng(11)
+    x_i = torch.tensor(rng.uniform(1.0, 100.0, 5000), device=cuda)             # 5 tiles: 5 FP64 items
+    # 8 tiles, 2 items; x > 30 at v = 5: mu_20 only, no integral
+    x_k32 = torch.tensor(rng.uniform(31.0, 100.0, 8000), device=cuda, dtype=torch.float32)
+    v_kf = torch.tensor(rng.uniform(0.0, 16.0, 4000), device=cuda)             # every pair in the integral
+    x_kf = torch.tensor(rng.uniform(0.5, 25.0, 4000), device=cuda)
+    with Server(arena_bytes=64 << 20, max_slots=8) as srv:
+        d0 = srv.device_stats()
+        assert d0["claim_ns"] == 0 and sum(d0["items"].values()) == 0
+        ts = [srv.submit_device("i", torch.tensor([3.0], device=cuda, dtype=torch.float64), x_i,
+                                torch.empty_like(x_i)),
+              srv.submit_device("k", torch.tensor([5.0], device=cuda, dtype=torch.float32), x_k32,
+                                torch.empty_like(x_k32)),
+              srv.submit_device("k", v_kf, x_kf, torch.empty_like(x_kf))]
+        for t in ts:
+            srv.wait(t, timeout=120)
+        time.sleep(0.05)                           # the last item's time is booked at the next claim
+        d1 = srv.device_stats()
+    items, busy = d1["items"], d1["busy_ns"]
+    assert items["tiles_i_f64"] == 5 and busy["tiles_i_f64"] > 0
+    assert items["tiles_k_f32"] == 2 and busy["tiles_k_f32"] > 0
+    assert items["tiles_k_f64"] == 4 and busy["tiles_k_f64"] > 0
+    kint = [f for f in items if f.startswith("kint_f64")]
+    assert sum(items[f] for f in kint) >= 1 and sum(busy[f] for f in kint) > 0
+    assert items["tiles_i_f32"] == 0 and items["kint_f32"] == 0
+    assert d1["claim_ns"] > d0["claim_ns"]

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("ws_pairs", [1024, 5000, 1 << 20])
+@pytest.mark.parametrize("ws_pairs", [2048, 5000, 1 << 20])
 def test_k_ws_matches_logbessel_k(cuda, dtype, ws_pairs):
     v, x = robust_pairs(300_000, seed=41)
     vt = torch.tensor(v, dtype=dtype, device=cuda)
