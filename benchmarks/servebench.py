@@ -170,7 +170,7 @@ def _run(n_req, seed, max_n, loads, device, pool_n, out_slots, per_call_requests
            "mix": "sizes log-uniform [1, %d]; I/K 50/50; FP32 70%%; v log-uniform [1e-6, 1e4], "
                   "x log-uniform [1e-3, 1e4]" % max_n}
     torch.cuda.synchronize()
-    with Server(arena_bytes=16 << 30, max_slots=256, ctas_per_sm=4, idle_ms=20.0) as srv:
+    with Server(arena_bytes=16 << 30, max_slots=1024, ctas_per_sm=4, idle_ms=20.0) as srv:
         def sub_host(i):
             k, dt, v, x, o, n = host_ptrs[i]
             return srv.submit_ptr(k, dt, v, 1, x, o, n)

@@ -98,16 +98,6 @@ def _f32_lit(f):
     return float(f).hex() + "f"
 
 
-def _horner_df(cs, fn_name):
-    pairs = [f32_split(c) for c in cs]
-    lines = ["__host__ __device__ __forceinline__ lb::dfloat %s(lb::dfloat p) {" % fn_name,
-             "  lb::dfloat r = lb::df_make(%s, %s);" % (_f32_lit(pairs[-1][0]), _f32_lit(pairs[-1][1]))]
-    for j in range(len(pairs) - 2, -1, -1):
-        lines.append("  r = lb::df_mul_add(r, p, lb::df_make(%s, %s));" % (_f32_lit(pairs[j][0]), _f32_lit(pairs[j][1])))
-    lines += ["  return r;", "}", ""]
-    return lines
-
-
 def render_header(polys):
     lines = [
         "// Generated by gen_debye.py -- do not edit.",
@@ -136,10 +126,19 @@ def render_header(polys):
     for k in range(1, KMAX + 1):
         lines += _horner(q_coeffs(k, polys), "lb_debye_Q%d" % k)
     lines.append("// P_k(p) in double-float (lb_df.cuh), k = 2..13: each coefficient as the")
-    lines.append("// pair hi + lo of floats nearest to it (exact hexadecimal literals).")
-    lines.append("")
+    lines.append("// pair hi + lo of floats nearest to it (exact hexadecimal literals), in one")
+    lines.append("// table: the k + 1 coefficients of P_k, ascending, from lb_debye_df_off[k].")
+    offs, rows, o = [0, 0], [], 0
     for k in range(2, KMAX + 1):
-        lines += _horner_df(p_coeffs(k, polys), "lb_debye_P%d_df" % k)
+        offs.append(o)
+        for c in p_coeffs(k, polys):
+            hi, lo = f32_split(c)
+            rows.append("  {%s, %s}" % (_f32_lit(hi), _f32_lit(lo)))
+        o += k + 1
+    lines.append("#define LB_DEBYE_DF_N %d" % o)
+    lines.append("static __constant__ const int lb_debye_df_off[%d] = {%s};" % (KMAX + 1, ", ".join(map(str, offs))))
+    lines.append("static __constant__ const float lb_debye_df[%d][2] = {\n%s};" % (o, ",\n".join(rows)))
+    lines.append("")
     return "\n".join(lines) + "\n"
 
 

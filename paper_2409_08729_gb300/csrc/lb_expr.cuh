@@ -168,10 +168,14 @@ __device__ __forceinline__ int mu_terms(float v, float x) {
 }
 
 // Terms of the power series of log I (series_log_i, series_so): the count
-// after which a term falls below 2^-56 of the running sum past the peak
-// index (Eq. "K"), by a single-precision pass; at most 90.
+// n after which a term falls below 2^-56 of the running sum past the peak
+// index (Eq. "K"), by a single-precision pass; at most 90.  Returned packed
+// with the number h of leading terms kept in FP64: the terms past the peak
+// from the first one below 1e-4 of the running sum on are summed in
+// double-float (their part of the sum is below 1e-3 of it), as
+// n + 128 h (series_count, series_head unpack it).
 __device__ __forceinline__ int series_terms(float v, float x) {
-  int n = 1;
+  int n = 1, h = 0;
   const float yf = 0.25f * x * x;
   const float kpk = 0.5f * (sqrtf(fmaf(x, x, v * v)) - v);
   float term = 1.0f, T = 0.0f, kf = 0.0f;
@@ -181,10 +185,13 @@ __device__ __forceinline__ int series_terms(float v, float x) {
     term *= __fdividef(yf, kf * (kf + v));         // an estimate: the fast division suffices
     T += term;
     n = k;
+    if (h == 0 && kf > kpk && term <= 1e-4f * (1.0f + T)) h = k;
     if (kf > kpk && term <= 1.4e-17f * (1.0f + T)) break;
   }
-  return n;
+  return n + 128 * (h == 0 ? n : h);
 }
+__device__ __forceinline__ int series_count(int packed) { return packed & 127; }
+__device__ __forceinline__ int series_head(int packed) { return packed >> 7; }
 
 // Leading terms of mu_K kept in FP64: the smallest k at which the running
 // product of the term ratios (the k-th term against the leading 1) falls
@@ -286,22 +293,17 @@ __device__ __forceinline__ T debye_P(int k, T p) {
   }
 }
 
-// P_k(p) in double-float, k = 2..13 (compile-time after unrolling).
+// P_k(p) in double-float, k = 2..13 (warp-uniform), by a rolled Horner
+// loop over the coefficient pairs of lb_debye_df (constant memory, read by
+// all lanes at once): the unrolled sums of U_13 alone would be about 1500
+// instructions, and the tile kernel's warps run several expressions at a
+// time out of one instruction cache.
 __device__ __forceinline__ dfloat debye_P_df(int k, dfloat p) {
-  switch (k) {
-    case 2: return lb_debye_P2_df(p);
-    case 3: return lb_debye_P3_df(p);
-    case 4: return lb_debye_P4_df(p);
-    case 5: return lb_debye_P5_df(p);
-    case 6: return lb_debye_P6_df(p);
-    case 7: return lb_debye_P7_df(p);
-    case 8: return lb_debye_P8_df(p);
-    case 9: return lb_debye_P9_df(p);
-    case 10: return lb_debye_P10_df(p);
-    case 11: return lb_debye_P11_df(p);
-    case 12: return lb_debye_P12_df(p);
-    default: return lb_debye_P13_df(p);
-  }
+  const float(*c)[2] = lb_debye_df + lb_debye_df_off[k];
+  dfloat r = df_make(c[k][0], c[k][1]);
+#pragma unroll 1
+  for (int i = k - 1; i >= 0; --i) r = df_mul_add(r, p, df_make(c[i][0], c[i][1]));
+  return r;
 }
 
 template <typename T>
@@ -355,7 +357,7 @@ __device__ __forceinline__ double u_expr(double v, double x) {
   // two outer steps in FP64.
   const dfloat pd = df_from_double(p), qd = df_from_double(q);
   dfloat accd = debye_P_df(K, pd);
-#pragma unroll
+#pragma unroll 1
   for (int k = K - 1; k >= 2; --k) accd = df_mul_add(accd, qd, debye_P_df(k, pd));
   const double acc = fma(df_to_double(accd), q, lb_debye_P1(p));
   const double S = fma(acc, q, 1.0);
@@ -400,12 +402,39 @@ static __constant__ double kSeriesK2[91] = {
     5041, 5184, 5329, 5476, 5625, 5776, 5929, 6084, 6241, 6400, 6561, 6724, 6889, 7056, 7225, 7396,
     7569, 7744, 7921, 8100};
 
-__device__ __forceinline__ double series_log_i_n(double v, double x, int n) {
-  n = __reduce_max_sync(0xffffffffu, n);
+// y / (k (k + v)) in double-float: the denominator from k v + k^2 (k^2
+// exact), the quotient as q1 + q2 (Dekker: q1 from the leading parts, q2
+// from the remainder y - q1 d).
+__device__ __forceinline__ dfloat series_ratio_df(dfloat y, dfloat v, int k) {
+  const float kf = (float)k;
+  const dfloat d = df_add(df_mul(v, df_make(kf, 0.0f)), df_make(kf * kf, 0.0f));
+  const float q1 = y.h * __frcp_rn(d.h);
+  const dfloat rem = df_add(y, df_mul(d, df_make(-q1, 0.0f)));
+  const float q2 = rem.h * __frcp_rn(d.h);
+  dfloat r;
+  r.h = q1 + q2;
+  r.l = q2 - (r.h - q1);
+  return r;
+}
+
+__device__ __forceinline__ double series_log_i_n(double v, double x, int packed) {
+  const int n = __reduce_max_sync(0xffffffffu, series_count(packed));
+  const int h = __reduce_max_sync(0xffffffffu, series_head(packed));
   const double y = 0.25 * x * x;
   double A = 1.0, B = 1.0;
+  int top = n;
+  if (n > h) {
+    // terms h+1..n: P <- 1 + (y / (k (k + v))) P in double-float; its value
+    // then starts the FP64 fraction (A / B = P)
+    const dfloat yd = df_from_double(y), vd = df_from_double(v);
+    dfloat Pd = df_make(1.0f, 0.0f);
 #pragma unroll 1
-  for (int k = n; k >= 1; --k) {
+    for (int k = n; k > h; --k) Pd = df_mul_add(series_ratio_df(yd, vd, k), Pd, df_make(1.0f, 0.0f));
+    A = df_to_double(Pd);
+    top = h;
+  }
+#pragma unroll 1
+  for (int k = top; k >= 1; --k) {
     const double d = fma(kSeriesK[k], v, kSeriesK2[k]);   // k (k + v), exact up to one rounding
     A = fma(d, B, y * A);
     B *= d;
@@ -439,6 +468,7 @@ struct ScalarOrder {
   double ser[91];                       // 1 / (k (k + v)), k = 1..90
   double u4[4], u6[4], u9[4], u13[4];   // C_0..C_3 of U_K
   dfloat mud[21];                       // mu[] in double-float
+  dfloat serd[91];                      // ser[] in double-float
   dfloat u4d[13], u6d[19], u9d[28], u13d[40];   // C_0..C_3K in double-float (C_4.. used)
 };
 
@@ -467,6 +497,7 @@ __device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
     }
   } else if (tid <= 90) {
     so.ser[tid] = 1.0 / ((double)tid * ((double)tid + v));
+    so.serd[tid] = df_from_double(so.ser[tid]);
   } else if (tid >= 128 && tid < 228) {
     // C_m of U_K: the coefficients of t^m, sum over k + 2i = m of c_{k,i} (s/v)^k
     int j = tid - 128, K, m;
@@ -532,7 +563,7 @@ __device__ __forceinline__ double u_expr_so(const ScalarOrder& so, double x) {
   // U regions: those terms in double-float, C_3 .. C_0 in FP64.
   const dfloat td = df_from_double(t);
   dfloat Sd = Cd[3 * K];
-#pragma unroll
+#pragma unroll 1
   for (int m = 3 * K - 1; m >= 4; --m) Sd = df_mul_add(Sd, td, Cd[m]);
   double S = df_to_double(Sd);
 #pragma unroll
@@ -543,13 +574,23 @@ __device__ __forceinline__ double u_expr_so(const ScalarOrder& so, double x) {
   return fma(-v, eta, 0.5 * ix_log_call(w * (0.5 * kPi)));
 }
 
-__device__ __forceinline__ double series_so(const ScalarOrder& so, double x, int n) {
+__device__ __forceinline__ double series_so(const ScalarOrder& so, double x, int packed) {
   const double v = so.v;
-  n = __reduce_max_sync(0xffffffffu, n);
+  const int n = __reduce_max_sync(0xffffffffu, series_count(packed));
+  const int h = __reduce_max_sync(0xffffffffu, series_head(packed));
   const double y = 0.25 * x * x;
   double P = 1.0;
+  int top = n;
+  if (n > h) {                                    // terms h+1..n in double-float
+    const dfloat yd = df_from_double(y);
+    dfloat Pd = df_make(1.0f, 0.0f);
 #pragma unroll 1
-  for (int k = n; k >= 1; --k) P = fma(y * so.ser[k], P, 1.0);
+    for (int k = n; k > h; --k) Pd = df_mul_add(df_mul(yd, so.serd[k]), Pd, df_make(1.0f, 0.0f));
+    P = df_to_double(Pd);
+    top = h;
+  }
+#pragma unroll 1
+  for (int k = top; k >= 1; --k) P = fma(y * so.ser[k], P, 1.0);
   double res = ix_log_call(P) - so.lg1;
   if (v != 0.0) res = fma(v, ix_log_call(0.5 * x), res);
   return res;

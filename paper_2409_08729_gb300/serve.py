@@ -50,7 +50,7 @@ def _check(st):
 
 
 class Server:
-    def __init__(self, arena_bytes=1 << 30, max_slots=256, ctas_per_sm=4, idle_ms=50.0):
+    def __init__(self, arena_bytes=1 << 30, max_slots=1024, ctas_per_sm=4, idle_ms=50.0):
         L = _lib()
         cfg = _Config(arena_bytes, max_slots, ctas_per_sm, idle_ms)
         h = ctypes.c_void_p()

@@ -20,6 +20,7 @@ _SRC = r'''
 #define __host__
 #define __device__
 #define __forceinline__ inline
+#define __constant__
 #include <math.h>
 template <typename T> inline T lb_fma(T a, T b, T c);
 template <> inline double lb_fma<double>(double a, double b, double c) { return fma(a, b, c); }
@@ -48,12 +49,15 @@ extern "C" void df_mul_add2(const float* in, float* out, long n) {   // mul and 
     out[4 * i] = m.h; out[4 * i + 1] = m.l; out[4 * i + 2] = s.h; out[4 * i + 3] = s.l;
   }
 }
-typedef dfloat (*pfn)(dfloat);
-static const pfn P[14] = {0, 0, lb_debye_P2_df, lb_debye_P3_df, lb_debye_P4_df, lb_debye_P5_df, lb_debye_P6_df,
-                          lb_debye_P7_df, lb_debye_P8_df, lb_debye_P9_df, lb_debye_P10_df, lb_debye_P11_df,
-                          lb_debye_P12_df, lb_debye_P13_df};
+// the Horner loop of debye_P_df (lb_expr.cuh) over the generated table
+static dfloat P(int k, dfloat p) {
+  const float(*c)[2] = lb_debye_df + lb_debye_df_off[k];
+  dfloat r = lb::df_make(c[k][0], c[k][1]);
+  for (int i = k - 1; i >= 0; --i) r = lb::df_mul_add(r, p, lb::df_make(c[i][0], c[i][1]));
+  return r;
+}
 extern "C" void df_debye(int k, const double* p, double* out, long n) {
-  for (long i = 0; i < n; ++i) out[i] = lb::df_to_double(P[k](lb::df_from_double(p[i])));
+  for (long i = 0; i < n; ++i) out[i] = lb::df_to_double(P(k, lb::df_from_double(p[i])));
 }
 '''
 _lib = None
