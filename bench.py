@@ -40,7 +40,7 @@ NCU_DRAM_BYTES_PER_STEP = {"lb_kint_kernel": (11.232e9, 90)}
 # the XU (special-function) pipe while active, and the share of cycles that
 # issue; empty when stale.
 NCU_PIPES = {
-    "lb_tiles_kernel": {"fp64": 0.723, "alu": 0.378, "fma": 0.153, "xu": 0.019, "issue_active": 0.450,
+    "lb_tiles_kernel": {"fp64": 0.719, "alu": 0.360, "fma": 0.250, "xu": 0.022, "issue_active": 0.560,
                         "launch": "log I, mixed orders, 11M pairs"},
     "lb_kint_kernel": {"fp64": 0.625, "alu": 0.659, "fma": 0.188, "xu": 0.017, "issue_active": 0.680,
                        "launch": "one-slot class kernel of a mixed-order log K call (class 4: fp64 0.492, "

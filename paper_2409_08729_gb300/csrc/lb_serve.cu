@@ -468,13 +468,15 @@ void lb_server::hold(int fam, const WorkItem& w, double t) {
 // the four request classes: the K-integral windows took 1.3x their time
 // served alone, the FP32 items 2.2-2.6x; the kernels share the SMs'
 // instruction caches).  So ready items wait in per-family lists and go to
-// the ring in runs of one family: whenever fewer than two items per CTA are
-// left untaken, a family publishes up to sixteen items per CTA -- the family
-// with the most items waiting, unless one has waited more than 2 ms (then
+// the ring in runs of one family: whenever fewer than one item per CTA is
+// left untaken, a family publishes up to four items per CTA -- the family
+// with the most items waiting, unless one has waited more than 1 ms (then
 // the one that has waited longest).  The CTAs work through a run of one
-// family before the next; families mix only at the ends of runs.  On a mix
-// of 20,000 requests served from 1024 slots the runs averaged 1400 items
-// and the capacity rose from 0.77 to about 0.93 of large direct calls.
+// family before the next; families mix only at the ends of runs.  On the
+// serving benchmark's mix (100,000 requests from 1024 slots) the capacity
+// rose from 0.77 to 0.94 of large direct calls; runs of sixteen items per
+// CTA gave the same capacity and a p99 latency of 79 ms at 80 % load
+// (10 ms with four).
 bool lb_server::publish_runs() {
   if (pend_count == 0) return false;
   unsigned long long head = 0;
@@ -485,16 +487,16 @@ bool lb_server::publish_runs() {
   long long ahead = tail - (long long)head;
   bool progress = false;
   const double t_now = now_s();
-  while (ahead < 2ll * ctas && pend_count > 0) {
+  while (ahead < ctas && pend_count > 0) {
     int f = -1;
     for (int g = 0; g < kFamilies; ++g)
-      if (!pend[g].empty() && t_now - pend[g].front().second > 2e-3 &&
+      if (!pend[g].empty() && t_now - pend[g].front().second > 1e-3 &&
           (f < 0 || pend[g].front().second < pend[f].front().second))
         f = g;
     if (f < 0)
       for (int g = 0; g < kFamilies; ++g)
         if (!pend[g].empty() && (f < 0 || pend[g].size() > pend[f].size())) f = g;
-    const long long m = std::min<long long>((long long)pend[f].size(), 16ll * ctas);
+    const long long m = std::min<long long>((long long)pend[f].size(), 4ll * ctas);
     for (long long i = 0; i < m; ++i) {
       ring[tail % ring_cap] = pend[f].front().first;
       pend[f].pop_front();
