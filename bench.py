@@ -32,7 +32,7 @@ METRIC = "Gevals/s (log I_v and log K_v, FP64)"
 # capture of every launch of one full-size step (the launch list of
 # profiles/launches_paper_sweep_fp64.md, with dram__bytes_read.sum and
 # dram__bytes_write.sum); empty when the kernels changed since.
-NCU_DRAM_BYTES_PER_STEP = {"lb_kint_kernel": (11.232e9, 90)}
+NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.799e9, 27), "lb_kint_kernel": (11.470e9, 90)}
 # Pipe utilisation of each kernel from ncu --set full on a small case of the
 # same workload (profiles/lb_tiles_kernel_sweep_small.md,
 # profiles/lb_kint_kernel_sweep_small.md, profiles/fp32_mixed_sweep_small.md):

@@ -134,12 +134,11 @@ lb_status logbessel_k_dx_ws(lb_dtype dtype, const void* v, int64_t v_stride, con
  * defines in device global memory: 4 MiB plus 256 bytes, resident on every
  * GPU that loads the library until the process exits.  Hence at most
  * 1048576 pairs per call; a larger n returns LB_EINVAL with a message and
- * launches nothing.  The first call on a device looks up the scratch
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture on the device.  The address is kept for the
- * life of the process: after cudaDeviceReset (or any other teardown of the
- * device's primary context) the module reloads elsewhere, so this entry point
- * must not be called again in that process.  Every call shares the one
+ * launches nothing.  Every call looks up the scratch address
+ * (cudaGetSymbolAddress, no allocation) in the current context, so the entry
+ * point stays valid after cudaDeviceReset; the first call on a device may
+ * load the library's module, so make it before any stream capture on that
+ * device.  Every call shares the one
  * array and clears its counter and mask on the stream: calls whose work overlaps on
  * the GPU (different streams, or concurrent host threads) race and must be
  * serialized by the caller.  Other arguments, results and errors as in
@@ -180,10 +179,10 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
  * 2 d/dx log I, 3 d/dx log K.  v, x, out are host pointers (pinned memory
  * lets the copies overlap with the computation; pageable memory works but
  * copies synchronously).  The pairs are processed in chunks of `chunk`
- * (0 = 8M pairs; at most 2^26) through four device chunk slots and three
+ * (0 = 16M pairs; at most 2^26) through four device chunk slots and three
  * internal streams, so the copy-in of one chunk, the evaluation of the
  * previous one and the copy-out of the one before overlap; when chunk is a
- * multiple of 8192 the first and last pieces are smaller (down to chunk/8)
+ * multiple of 16384 the first and last pieces are smaller (down to chunk/8)
  * to shorten the unoverlapped copies, with results equal to one pass.  The call
  * returns when every result is in `out` (it synchronizes).  The streams,
  * events and one device buffer (four chunk slots of v, x and out, plus the
