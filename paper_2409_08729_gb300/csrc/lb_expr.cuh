@@ -109,17 +109,36 @@ __device__ __forceinline__ bool tight_mu20(double v, double x) {
 }
 __device__ __forceinline__ bool tight_u13(double v, double x) { return (LB_GT(x, 25.0) && LB_GT(v, 0.7)) || LB_GT(v, 16.0); }
 
+// log K values (not the x-derivative) take mu_20 and U_13 further into the
+// fallback region than log I: the truncation error of both expansions for
+// log K, measured the same way (exact arithmetic of the truncated sums
+// against the oracle, 1500 random points per added region, dense at its
+// edges), stays at or below 3.1e-16 of the error scale in
+//   mu_20:  x > 18.5, v < 9.5;  x > 20, v < 12.5;  x > 22, v < 13.6
+//   U_13:   x > 19, v > 10;     x > 14, v > 14
+// (log I's mu_20 errs by up to 1e-13 there: its thresholds stay).  Pairs of
+// these ranges leave the K integral, the costliest expression.
+__device__ __forceinline__ bool tight_mu20_kv(double v, double x) {
+  return tight_mu20(v, x) || (LB_GT(x, 18.5) && LB_LT(v, 9.5)) || (LB_GT(x, 20.0) && LB_LT(v, 12.5)) ||
+         (LB_GT(x, 22.0) && LB_LT(v, 13.6));
+}
+__device__ __forceinline__ bool tight_u13_kv(double v, double x) {
+  return tight_u13(v, x) || (LB_GT(x, 19.0) && LB_GT(v, 10.0)) || (LB_GT(x, 14.0) && LB_GT(v, 14.0));
+}
+
 // With the pairs binned per expression on chip (no warp divergence), the
 // tight dispatch also uses the shorter uniform expansions of the paper's CPU
 // order, with order thresholds from the same error map: U_4 for v > 230,
 // U_6 for v > 70, U_9 for v > 28 (truncation <= 2e-16 for every x).
-__device__ __forceinline__ int classify(double v, double x, int mode) {
+// kv: the pair is a log K value (K callers pass |v|), which has the wider
+// mu_20 and U_13 ranges of tight_mu20_kv and tight_u13_kv.
+__device__ __forceinline__ int classify(double v, double x, int mode, bool kv = false) {
   if (mode == MODE_TIGHT) {
-    if (tight_mu20(v, x)) return R_MU20;
+    if (kv ? tight_mu20_kv(v, x) : tight_mu20(v, x)) return R_MU20;
     if (LB_GT(v, 230.0)) return R_U4;
     if (LB_GT(v, 70.0)) return R_U6;
     if (LB_GT(v, 28.0)) return R_U9;
-    if (tight_u13(v, x)) return R_U13;
+    if (kv ? tight_u13_kv(v, x) : tight_u13(v, x)) return R_U13;
     return R_FALLBACK;
   }
   if (mode == MODE_PAPER_CPU) {

@@ -110,9 +110,9 @@ __device__ __forceinline__ bool tile_special(T v, T x, T* r) {
   }
 }
 
-template <typename T>
+template <int KIND, bool DX, typename T>
 __device__ __forceinline__ int tile_classify(T v, T x, int mode) {
-  if constexpr (sizeof(T) == 8) return classify(v, x, mode);
+  if constexpr (sizeof(T) == 8) return classify(v, x, mode, KIND == KIND_K && !DX);
   else return classify32(v, x, mode);
 }
 
@@ -241,7 +241,7 @@ __device__ __forceinline__ void tile_bin(TileShared<T, NT>& S, const T* __restri
       } else {
         S.sv[li] = vi;
         S.sx[li] = xi;
-        const int r = forced_region >= 0 ? forced_region : tile_classify<T>(vi, xi, mode);
+        const int r = forced_region >= 0 ? forced_region : tile_classify<KIND, DX, T>(vi, xi, mode);
         int nterm;
         k = tile_key<KIND, DX, T>(r, vi, xi, &nterm);
         S.nt[li] = (uint8_t)nterm;
