@@ -109,36 +109,53 @@ __device__ __forceinline__ bool tight_mu20(double v, double x) {
 }
 __device__ __forceinline__ bool tight_u13(double v, double x) { return (LB_GT(x, 25.0) && LB_GT(v, 0.7)) || LB_GT(v, 16.0); }
 
-// log K values (not the x-derivative) take mu_20 and U_13 further into the
-// fallback region than log I: the truncation error of both expansions for
-// log K, measured the same way (exact arithmetic of the truncated sums
-// against the oracle, 1500 random points per added region, dense at its
-// edges), stays at or below 3.1e-16 of the error scale in
-//   mu_20:  x > 18.5, v < 9.5;  x > 20, v < 12.5;  x > 22, v < 13.6
-//   U_13:   x > 19, v > 10;     x > 14, v > 14
-// (log I's mu_20 errs by up to 1e-13 there: its thresholds stay).  Pairs of
-// these ranges leave the K integral, the costliest expression.
-__device__ __forceinline__ bool tight_mu20_kv(double v, double x) {
-  return tight_mu20(v, x) || (LB_GT(x, 18.5) && LB_LT(v, 9.5)) || (LB_GT(x, 20.0) && LB_LT(v, 12.5)) ||
-         (LB_GT(x, 22.0) && LB_LT(v, 13.6));
+// Values (not the x-derivatives) take mu_20 and U_13 further into the
+// fallback region than the shared thresholds: the truncation error of both
+// expansions, measured the same way for each function (exact arithmetic of
+// the truncated sums against the oracle, 1500 random points per added
+// range, half of them at its edges), stays at or below 3.1e-16 of the error
+// scale in
+//   log K:  mu_20  x > 18.5, v < 9.5;  x > 20, v < 12.5;  x > 22, v < 13.6
+//           U_13   x > 19, v > 10;     x > 14, v > 14
+//   log I:  mu_20  x > 19, v < 4.5;    x > 21, v < 7.5;   x > 23, v < 9.5
+//           U_13   x > 19.5, v > 10;   x > 17.5, v > 12;  x > 14.5, v > 14
+// (log I's mu_20 converges more slowly as v^2/x grows: up to 1e-13 inside
+// log K's ranges).  Pairs of these ranges leave the power series and the K
+// integral, the costliest expressions.
+enum WideRanges { WIDE_NONE = 0, WIDE_I = 1, WIDE_K = 2 };
+__device__ __forceinline__ bool tight_mu20_w(double v, double x, int w) {
+  if (tight_mu20(v, x)) return true;
+  if (w == WIDE_K)
+    return (LB_GT(x, 18.5) && LB_LT(v, 9.5)) || (LB_GT(x, 20.0) && LB_LT(v, 12.5)) ||
+           (LB_GT(x, 22.0) && LB_LT(v, 13.6));
+  if (w == WIDE_I)
+    return (LB_GT(x, 19.0) && LB_LT(v, 4.5)) || (LB_GT(x, 21.0) && LB_LT(v, 7.5)) ||
+           (LB_GT(x, 23.0) && LB_LT(v, 9.5));
+  return false;
 }
-__device__ __forceinline__ bool tight_u13_kv(double v, double x) {
-  return tight_u13(v, x) || (LB_GT(x, 19.0) && LB_GT(v, 10.0)) || (LB_GT(x, 14.0) && LB_GT(v, 14.0));
+__device__ __forceinline__ bool tight_u13_w(double v, double x, int w) {
+  if (tight_u13(v, x)) return true;
+  if (w == WIDE_K) return (LB_GT(x, 19.0) && LB_GT(v, 10.0)) || (LB_GT(x, 14.0) && LB_GT(v, 14.0));
+  if (w == WIDE_I)
+    return (LB_GT(x, 19.5) && LB_GT(v, 10.0)) || (LB_GT(x, 17.5) && LB_GT(v, 12.0)) ||
+           (LB_GT(x, 14.5) && LB_GT(v, 14.0));
+  return false;
 }
 
 // With the pairs binned per expression on chip (no warp divergence), the
 // tight dispatch also uses the shorter uniform expansions of the paper's CPU
 // order, with order thresholds from the same error map: U_4 for v > 230,
 // U_6 for v > 70, U_9 for v > 28 (truncation <= 2e-16 for every x).
-// kv: the pair is a log K value (K callers pass |v|), which has the wider
-// mu_20 and U_13 ranges of tight_mu20_kv and tight_u13_kv.
-__device__ __forceinline__ int classify(double v, double x, int mode, bool kv = false) {
+// w: WIDE_I or WIDE_K for values of log I or log K (K callers pass |v|),
+// which take the wider mu_20 and U_13 ranges above; WIDE_NONE for the
+// x-derivatives.
+__device__ __forceinline__ int classify(double v, double x, int mode, int w = WIDE_NONE) {
   if (mode == MODE_TIGHT) {
-    if (kv ? tight_mu20_kv(v, x) : tight_mu20(v, x)) return R_MU20;
+    if (tight_mu20_w(v, x, w)) return R_MU20;
     if (LB_GT(v, 230.0)) return R_U4;
     if (LB_GT(v, 70.0)) return R_U6;
     if (LB_GT(v, 28.0)) return R_U9;
-    if (kv ? tight_u13_kv(v, x) : tight_u13(v, x)) return R_U13;
+    if (tight_u13_w(v, x, w)) return R_U13;
     return R_FALLBACK;
   }
   if (mode == MODE_PAPER_CPU) {

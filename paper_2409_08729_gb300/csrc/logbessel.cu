@@ -261,7 +261,7 @@ __global__ void lb_classify_kernel(const double* __restrict__ v, int64_t v_strid
     const double xi = x[i];
     if (KIND == KIND_K) vi = fabs(vi);
     double sp;
-    reg[i] = special_value<KIND>(vi, xi, &sp) ? (uint8_t)R_SPECIAL : (uint8_t)classify(vi, xi, mode, KIND == KIND_K);
+    reg[i] = special_value<KIND>(vi, xi, &sp) ? (uint8_t)R_SPECIAL : (uint8_t)classify(vi, xi, mode, KIND == KIND_K ? WIDE_K : WIDE_I);
   }
 }
 

@@ -84,8 +84,9 @@ PAPER_EDGES_X = (19.6931, 30.0, 35.9074, 59.6925, 84.4153, 274.2377, 1400.0)
 PAPER_EDGES_V = (0.3, 0.46, 0.6, 0.7, 3.05, 3.1, 12.6964, 15.3919, 20.1534, 56.9971, 163.6993)
 TIGHT_EDGES_X = (25.0, 30.0, 59.6925)
 TIGHT_EDGES_V = (0.7, 13.6, 16.0)
-# corners (x, v) of the wider mu_20 and U_13 ranges of log K values
+# corners (x, v) of the wider mu_20 and U_13 ranges of log K and log I values
 K_VALUE_CORNERS = ((18.5, 9.5), (20.0, 12.5), (22.0, 13.6), (19.0, 10.0), (14.0, 14.0))
+I_VALUE_CORNERS = ((19.0, 4.5), (21.0, 7.5), (23.0, 9.5), (19.5, 10.0), (17.5, 12.0), (14.5, 14.0))
 
 
 def boundary_pairs(seed=0, per_edge=24):
@@ -100,9 +101,9 @@ def boundary_pairs(seed=0, per_edge=24):
         for rel in (-1e-2, -1e-6, 0.0, 1e-6, 1e-2):
             vs.append(np.full(per_edge, e * (1 + rel)))
             xs.append(np.exp(rng.uniform(np.log(1e-3), np.log(2000.0), per_edge)))
-    # the edges of the log K value ranges: x near each corner's x with v up to
+    # the edges of the wider value ranges: x near each corner's x with v up to
     # just past its v, and v near its v with x up to 30
-    for xe, ve in K_VALUE_CORNERS:
+    for xe, ve in K_VALUE_CORNERS + I_VALUE_CORNERS:
         for rel in (-1e-2, -1e-6, 0.0, 1e-6, 1e-2):
             xs.append(np.full(per_edge, xe * (1 + rel)))
             vs.append(rng.uniform(0.0, ve * 1.02, per_edge))

@@ -179,21 +179,20 @@ def test_tiny_arguments(cuda, kind):
     _report(kind, v, x, got, ref, scale, TOL64)
 
 
-def test_log_k_wider_expansion_ranges(cuda):
-    """log K values take mu_20 and U_13 below the shared thresholds (x in
-    (14, 30], v up to 16): dense random pairs there against the oracle, and
-    the dispatch seen through logbessel_classify (log I keeps the power
-    series at the same pairs; the x-derivative keeps the K integral)."""
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_wider_expansion_ranges(cuda, kind):
+    """Values take mu_20 and U_13 below the shared thresholds (x in (14, 30],
+    v up to 16; wider for log K than for log I): dense random pairs there
+    against the oracle, and the dispatch seen through logbessel_classify."""
     rng = np.random.default_rng(21)
     v = rng.uniform(0.0, 16.0, 20000)
     x = rng.uniform(13.0, 30.0, 20000)
-    ref, scale = _ref("k", v, x)
-    got = _run("k", v, x, cuda)
-    _report("k", v, x, got, ref, scale, TOL64)
-    pts = torch.tensor([[5.0, 19.0], [12.0, 21.0], [13.0, 23.0], [11.0, 19.5], [15.0, 15.0], [5.0, 18.0]],
-                       dtype=torch.float64, device=cuda)
-    rk = lb.classify("k", pts[:, 0], pts[:, 1]).cpu().tolist()
-    ri = lb.classify("i", pts[:, 0], pts[:, 1]).cpu().tolist()
-    R = lb.REGIONS
-    assert rk == [R["mu20"], R["mu20"], R["mu20"], R["u13"], R["u13"], R["fallback"]], rk
-    assert ri == [R["fallback"]] * 6, ri
+    ref, scale = _ref(kind, v, x)
+    got = _run(kind, v, x, cuda)
+    _report(kind, v, x, got, ref, scale, TOL64)
+    pts = torch.tensor([[5.0, 19.0], [12.0, 21.0], [13.0, 23.0], [11.0, 19.5], [15.0, 15.0], [5.0, 18.0],
+                        [4.0, 19.5], [9.0, 23.5]], dtype=torch.float64, device=cuda)
+    reg = lb.classify(kind, pts[:, 0], pts[:, 1]).cpu().tolist()
+    mu, u, fb = lb.REGIONS["mu20"], lb.REGIONS["u13"], lb.REGIONS["fallback"]
+    want = [mu, mu, mu, u, u, fb, mu, mu] if kind == "k" else [fb, u, u, fb, u, fb, mu, mu]
+    assert reg == want, (kind, reg)
