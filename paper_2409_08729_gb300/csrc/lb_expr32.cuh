@@ -33,13 +33,24 @@ __device__ __forceinline__ bool special_value32(float v, float x, float* r) {
 // evaluation itself).  A pair within one float rounding of a threshold may
 // land on the other side than in the FP64 path; both expressions are
 // accurate there.
-__device__ __forceinline__ int classify32(float v, float x, int mode) {
+// w: WIDE_I / WIDE_K for values of log I / log K, which take the wider
+// mu_20 and U_13 ranges of the FP64 form (tight_mu20_w, tight_u13_w; there
+// the truncation error is below 3.1e-16; in single precision the mu_20
+// terms grow to at most 3 there, and the Debye sums' rounding, bounded by
+// 6e-8 sum_k sum_i |c_ki| / v^k, stays below 5e-8 for v > 10).
+__device__ __forceinline__ int classify32(float v, float x, int mode, int w = WIDE_NONE) {
   if (mode == MODE_TIGHT) {
-    if ((x > 30.0f && v < 13.6f) || (x > 59.6925f && v * v < 3.24f * x)) return R_MU20;
+    bool mu = (x > 30.0f && v < 13.6f) || (x > 59.6925f && v * v < 3.24f * x);
+    if (w == WIDE_K) mu = mu || (x > 18.5f && v < 9.5f) || (x > 20.0f && v < 12.5f) || (x > 22.0f && v < 13.6f);
+    if (w == WIDE_I) mu = mu || (x > 19.0f && v < 4.5f) || (x > 21.0f && v < 7.5f) || (x > 23.0f && v < 9.5f);
+    if (mu) return R_MU20;
     if (v > 230.0f) return R_U4;
     if (v > 70.0f) return R_U6;
     if (v > 28.0f) return R_U9;
-    if ((x > 25.0f && v > 0.7f) || v > 16.0f) return R_U13;
+    bool u = (x > 25.0f && v > 0.7f) || v > 16.0f;
+    if (w == WIDE_K) u = u || (x > 19.0f && v > 10.0f) || (x > 14.0f && v > 14.0f);
+    if (w == WIDE_I) u = u || (x > 19.5f && v > 10.0f) || (x > 17.5f && v > 12.0f) || (x > 14.5f && v > 14.0f);
+    if (u) return R_U13;
     return R_FALLBACK;
   }
   const float lx = logf(x), lv = logf(v);

@@ -113,7 +113,7 @@ __device__ __forceinline__ bool tile_special(T v, T x, T* r) {
 template <int KIND, bool DX, typename T>
 __device__ __forceinline__ int tile_classify(T v, T x, int mode) {
   if constexpr (sizeof(T) == 8) return classify(v, x, mode, DX ? WIDE_NONE : (KIND == KIND_K ? WIDE_K : WIDE_I));
-  else return classify32(v, x, mode);
+  else return classify32(v, x, mode, DX ? WIDE_NONE : (KIND == KIND_K ? WIDE_K : WIDE_I));
 }
 
 // FP64 values with the lane's term count n (mu_20, series) given.

@@ -92,22 +92,24 @@ constexpr uint32_t kQueueOffsetMask = (1u << kQueueOffsetBits) - 1u;
 // Tile kernel: classify, bin per region in shared memory, evaluate the
 // per-thread expressions (lb_tile.cuh); K fallback pairs go to a global queue
 // for lb_kint_kernel.  T = double (FP64) or float (FP32-mixed).
-template <int KIND, bool DX, typename T>
+// SO: one order for every argument (FP64 values, v_stride 0, no forced
+// region): the order's constants once per block, and only the per-order
+// forms of the expressions compiled in (each kernel carries one form's
+// code, half the instruction footprint).
+template <int KIND, bool DX, typename T, bool SO>
 __global__ void __launch_bounds__(kTileThreads, LB_TILES_CTAS_PER_SM)
 lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
                 int64_t n, int mode, int forced_region, unsigned int* __restrict__ qcount,
                 uint32_t* __restrict__ queue, int64_t qcap) {
+  static_assert(!SO || (sizeof(T) == 8 && !DX), "per-order constants are built for FP64 values");
   __shared__ TileShared<T, kTileThreads> S;
   const int tid = threadIdx.x;
   const int64_t ntiles = (n + kTile - 1) / kTile;
   const ScalarOrder* so = nullptr;
-  if constexpr (sizeof(T) == 8 && !DX) {
-    // one order for every argument: its constants once per block
-    __shared__ ScalarOrder SO;
-    if (v_stride == 0 && forced_region < 0 && n > 0) {
-      scalar_order_setup<KIND>(SO, KIND == KIND_K ? fabs((double)v[0]) : (double)v[0]);
-      so = &SO;
-    }
+  if constexpr (SO) {
+    __shared__ ScalarOrder SOC;
+    scalar_order_setup<KIND>(SOC, KIND == KIND_K ? fabs((double)v[0]) : (double)v[0]);
+    so = &SOC;
   }
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t t0 = tile * kTile;
@@ -247,7 +249,7 @@ __global__ void lb_classify_kernel32(const float* __restrict__ v, int64_t v_stri
     const float xi = x[i];
     if (KIND == KIND_K) vi = fabsf(vi);
     float sp;
-    reg[i] = special_value32<KIND>(vi, xi, &sp) ? (uint8_t)R_SPECIAL : (uint8_t)classify32(vi, xi, mode);
+    reg[i] = special_value32<KIND>(vi, xi, &sp) ? (uint8_t)R_SPECIAL : (uint8_t)classify32(vi, xi, mode, KIND == KIND_K ? WIDE_K : WIDE_I);
   }
 }
 
@@ -458,11 +460,16 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
                    cudaStream_t st, void* scratch, int64_t chunk) {
   const int sms = sm_count();
   const int64_t ntiles_all = (n + kTile - 1) / kTile;
+  const bool per_order = sizeof(T) == 8 && !DX && v_stride == 0 && forced_region < 0;
   if (KIND == KIND_I || (forced_region >= 0 && forced_region != R_FALLBACK)) {
     const int grid = (int)(ntiles_all < (int64_t)sms * LB_TILES_CTAS_PER_SM ? ntiles_all : (int64_t)sms * LB_TILES_CTAS_PER_SM);
     return launch(PS_TILES, st, [&] {
-      lb_tiles_kernel<KIND, DX, T><<<grid, kTileThreads, 0, st>>>(v, v_stride, x, out, n, mode, forced_region,
-                                                                 nullptr, nullptr, 0);
+      if (per_order)
+        lb_tiles_kernel<KIND, DX, T, !DX && sizeof(T) == 8><<<grid, kTileThreads, 0, st>>>(
+            v, v_stride, x, out, n, mode, forced_region, nullptr, nullptr, 0);
+      else
+        lb_tiles_kernel<KIND, DX, T, false><<<grid, kTileThreads, 0, st>>>(v, v_stride, x, out, n, mode,
+                                                                          forced_region, nullptr, nullptr, 0);
     });
   }
   if (sizeof(T) == 4 && mode != MODE_TIGHT)
@@ -489,8 +496,12 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
     const int64_t ntiles = (cn + kTile - 1) / kTile;
     const int grid = (int)(ntiles < (int64_t)sms * LB_TILES_CTAS_PER_SM ? ntiles : (int64_t)sms * LB_TILES_CTAS_PER_SM);
     status = launch(PS_TILES, st, [&] {
-      lb_tiles_kernel<KIND, DX, T><<<grid, kTileThreads, 0, st>>>(vc, v_stride, xc, oc, cn, mode, forced_region, qcount,
-                                                                 queue, cap);
+      if (per_order)
+        lb_tiles_kernel<KIND, DX, T, !DX && sizeof(T) == 8><<<grid, kTileThreads, 0, st>>>(
+            vc, v_stride, xc, oc, cn, mode, forced_region, qcount, queue, cap);
+      else
+        lb_tiles_kernel<KIND, DX, T, false><<<grid, kTileThreads, 0, st>>>(vc, v_stride, xc, oc, cn, mode,
+                                                                          forced_region, qcount, queue, cap);
     });
     if (status != LB_OK) break;
     bool done = false;

@@ -73,3 +73,13 @@ def test_tiny_arguments(cuda, kind):
     v = rng.uniform(0, 0.6, 6000)
     x = np.exp(rng.uniform(np.log(1e-37), np.log(1e-2), 6000))
     _check(kind, v, x, cuda)
+
+
+@pytest.mark.parametrize("kind", ["i", "k"])
+def test_wider_expansion_ranges(cuda, kind):
+    """Values take mu_20 and U_13 below the shared thresholds in FP32 too:
+    dense random pairs over x in (13, 30], v up to 16."""
+    rng = np.random.default_rng(23)
+    v = rng.uniform(0.0, 16.0, 20000)
+    x = rng.uniform(13.0, 30.0, 20000)
+    _check(kind, v, x, cuda)
