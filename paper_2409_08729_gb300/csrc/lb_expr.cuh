@@ -28,6 +28,8 @@ namespace lb {
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr double kTwoPi = 6.283185307179586476925286766559005768;
 constexpr double kHalfLogPi = 0.5723649429247000870717136756012478;   // log(pi)/2
+constexpr double kHalfLog2Pi = 0.9189385332046727417803297364056177;  // log(2 pi)/2
+constexpr double kHalfLogHalfPi = 0.2257913526447274323630976149;     // log(pi/2)/2
 
 enum Kind { KIND_I = 0, KIND_K = 1 };
 enum Region { R_MU20 = 0, R_U13 = 1, R_FALLBACK = 2, R_SPECIAL = 3, R_MU3 = 4, R_U4 = 5, R_U6 = 6, R_U9 = 7 };
@@ -385,8 +387,8 @@ __device__ __forceinline__ double u_expr(double v, double x) {
     t = ix_rcp_call(r);
   }
   const double p = t * t;
-  double q = t * inv_v;
-  if (KIND == KIND_K) q = -q;
+  const double tq = t * inv_v;                    // t / v
+  const double q = (KIND == KIND_K) ? -tq : tq;
   // Horner in q over k = K..1:  S = 1 + q (P_1 + q (P_2 + ... + q P_K)).
   // The terms k >= 2 (at most 1/v^2 of the sum, with v > 0.7 and x' > 35 or
   // v > 16 in the U regions: below 1e-3 of it) in double-float, P_1 and the
@@ -398,11 +400,12 @@ __device__ __forceinline__ double u_expr(double v, double x) {
   const double acc = fma(df_to_double(accd), q, lb_debye_P1(p));
   const double S = fma(acc, q, 1.0);
   const double eta = r + (ix_log_call(xp) - ix_log_call(1.0 + r));      // log(x' / (1 + r)), no division
-  // log(S / sqrt(2 pi v r)) = log(S^2 t / (2 pi v)) / 2, and for K
-  // log(S sqrt(pi / (2 v r))) = log(S^2 t pi / (2 v)) / 2 (t = 1/r): no root.
-  const double w = S * S * t * inv_v;
-  if (KIND == KIND_I) return fma(v, eta, 0.5 * ix_log_call(w * (1.0 / kTwoPi)));
-  return fma(-v, eta, 0.5 * ix_log_call(w * (0.5 * kPi)));
+  // log(S / sqrt(2 pi v r)) = log(S^2 t / v) / 2 - log(2 pi) / 2, and for K
+  // log(S sqrt(pi / (2 v r))) = log(S^2 t / v) / 2 + log(pi / 2) / 2
+  // (t = 1/r): no root, and the constant joins the FMA with v eta.
+  const double w = S * S * tq;
+  if (KIND == KIND_I) return fma(0.5, ix_log_call(w), fma(v, eta, -kHalfLog2Pi));
+  return fma(0.5, ix_log_call(w), fma(-v, eta, kHalfLogHalfPi));
 }
 
 // ---------------------------------------------------------------------------
@@ -605,9 +608,9 @@ __device__ __forceinline__ double u_expr_so(const ScalarOrder& so, double x) {
 #pragma unroll
   for (int m = 3; m >= 0; --m) S = fma(S, t, C[m]);
   const double eta = r + (ix_log_call(xp) - ix_log_call(1.0 + r));
-  const double w = S * S * t * inv_v;
-  if (KIND == KIND_I) return fma(v, eta, 0.5 * ix_log_call(w * (1.0 / kTwoPi)));
-  return fma(-v, eta, 0.5 * ix_log_call(w * (0.5 * kPi)));
+  const double w = S * S * (t * inv_v);          // as in u_expr
+  if (KIND == KIND_I) return fma(0.5, ix_log_call(w), fma(v, eta, -kHalfLog2Pi));
+  return fma(0.5, ix_log_call(w), fma(-v, eta, kHalfLogHalfPi));
 }
 
 __device__ __forceinline__ double series_so(const ScalarOrder& so, double x, int packed) {
