@@ -69,13 +69,14 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
 // the derivative (v = 0, x = 0.25) and the 64-node rule 8e-15 (v = 0,
 // x = 1e-3); the rules taken instead stay below 1.2e-16 (error map of the
 // derivative rules against the oracle's Bessel ratio).
+// (v, x >= 0: the compares run on the bit patterns, integer instructions.)
 __device__ __forceinline__ int kint_rule(double v, double x, bool dx) {
-  if (!dx && v >= 2.0 && v <= 16.5) return v < 7.0 ? (22 | (4 << 8)) : (12 | (5 << 8));
-  if (v > 1.2 && v <= 5.0) return 24 | (3 << 8);
-  const bool dsmall = dx && v < 0.1;
+  if (!dx && LB_GE(v, 2.0) && LB_LE(v, 16.5)) return LB_LT(v, 7.0) ? (22 | (4 << 8)) : (12 | (5 << 8));
+  if (LB_GT(v, 1.2) && LB_LE(v, 5.0)) return 24 | (3 << 8);
+  const bool dsmall = dx && LB_LT(v, 0.1);
   const double x32 = dsmall ? 0.6 : 0.25, xsplit = dsmall ? 5e-3 : 1e-3;
-  const int ng = (v >= 0.9 || x >= x32) ? 32 : ((v >= 0.4 || x >= xsplit) ? 64 : 0);
-  const int hr = (v <= 1.2) ? 0 : ((v <= 5.0) ? 1 : 2);
+  const int ng = (LB_GE(v, 0.9) || LB_GE(x, x32)) ? 32 : ((LB_GE(v, 0.4) || LB_GE(x, xsplit)) ? 64 : 0);
+  const int hr = LB_LE(v, 1.2) ? 0 : (LB_LE(v, 5.0) ? 1 : 2);
   return ng | (hr << 8);
 }
 
