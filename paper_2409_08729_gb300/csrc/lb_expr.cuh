@@ -108,14 +108,17 @@ __device__ __forceinline__ bool paper_u13(double v, double x) { return (x > 19.6
 #define LB_LT(a, c) (__double_as_longlong(a) < __double_as_longlong(c))
 #define LB_GE(a, c) (!LB_LT(a, c))
 #define LB_LE(a, c) (!LB_GT(a, c))
-// A non-negative double cut to single precision from its bit fields (0 below
-// 2^-126, +inf from 2^128 up): integer instructions, no FP64 conversion.
+// A double cut (truncated) to single precision from its bit fields (signed
+// 0 below 2^-126, signed inf from 2^128 up; NaN not expected): integer
+// instructions, no FP64 conversion instruction.  For the single-precision
+// estimates (edges, term counts) of the FP64 expressions.
 __device__ __forceinline__ float f32_cut(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const int e = (int)(b >> 52) - 1023;
-  if (e < -126) return 0.0f;
-  if (e > 127) return __int_as_float(0x7f800000);
-  return __uint_as_float(((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < -126) return __uint_as_float(sgn);
+  if (e > 127) return __uint_as_float(sgn | 0x7f800000u);
+  return __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
 }
 // The curved edge v^2 < 3.24 x in single precision: it moves the edge by at
 // most a few 1e-7 relative, where the truncation error of mu_20 changes by
@@ -285,7 +288,7 @@ static __constant__ float kMuInvKl[21] = {0.0f, 0.0f, 0.0f, -0x1.555556p-27f, 0.
 template <int KIND, int K>
 __device__ __forceinline__ double mu_expr_n(double v, double x, int n) {
   n = __reduce_max_sync(0xffffffffu, n);
-  const int h = __reduce_max_sync(0xffffffffu, mu_head<K>((float)v, (float)x));
+  const int h = __reduce_max_sync(0xffffffffu, mu_head<K>(f32_cut(v), f32_cut(x)));
   const double mu = 4.0 * v * v;
   const double rx = ix_rcp_call(8.0 * x);                             // 1/(8x) on the integer pipe
   const double inv8x = (KIND == KIND_I) ? -rx : rx;                   // the sign s folded in
@@ -317,14 +320,13 @@ __device__ __forceinline__ double mu_expr_n(double v, double x, int n) {
   // log(S sqrt(pi / (2x))) = log(S^2 pi / (2x)) / 2, with 1/x = 8 |inv8x|:
   // no square root needed.
   const double S2 = P * P;
-  const double ax = fabs(inv8x);
-  if (KIND == KIND_I) return fma(0.5, ix_log_call(S2 * ax * (8.0 / kTwoPi)), x);
-  return fma(0.5, ix_log_call(S2 * ax * (4.0 * kPi)), -x);
+  if (KIND == KIND_I) return fma(0.5, ix_log_call(S2 * rx * (8.0 / kTwoPi)), x);   // rx = |inv8x|
+  return fma(0.5, ix_log_call(S2 * rx * (4.0 * kPi)), -x);
 }
 
 template <int KIND, int K>
 __device__ __forceinline__ double mu_expr(double v, double x) {
-  return mu_expr_n<KIND, K>(v, x, mu_terms<K>((float)v, (float)x));
+  return mu_expr_n<KIND, K>(v, x, mu_terms<K>(f32_cut(v), f32_cut(x)));
 }
 
 // P_k(p) of the Debye polynomial u_k(t) = t^k P_k(t^2); k is a compile-time
@@ -501,7 +503,7 @@ __device__ __forceinline__ double series_log_i_n(double v, double x, int packed)
 }
 
 __device__ __forceinline__ double series_log_i(double v, double x) {
-  return series_log_i_n(v, x, series_terms((float)v, (float)x));
+  return series_log_i_n(v, x, series_terms(f32_cut(v), f32_cut(x)));
 }
 
 // ---------------------------------------------------------------------------
@@ -579,7 +581,7 @@ __device__ __forceinline__ void scalar_order_setup(ScalarOrder& so, double v) {
 template <int KIND>
 __device__ __forceinline__ double mu_expr_so(const ScalarOrder& so, double x, int n) {
   n = __reduce_max_sync(0xffffffffu, n);
-  const int h = __reduce_max_sync(0xffffffffu, mu_head<20>((float)so.v, (float)x));
+  const int h = __reduce_max_sync(0xffffffffu, mu_head<20>(f32_cut(so.v), f32_cut(x)));
   const double w = ix_rcp_call(8.0 * x);
   const double ws = w * so.sig;                   // exact: sigma is a power of two
   double P = 0.0;

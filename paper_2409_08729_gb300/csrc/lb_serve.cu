@@ -144,7 +144,7 @@ __device__ __forceinline__ void serve_tile(TileShared<T, LB_THREADS>& S, ServeAu
           li[q] = S.list[f0 + j];
           int k = 0;
           if constexpr (sizeof(T) == 8) {
-            if (d.nclass > 1) k = kint_class(fabs((double)S.sv[li[q]]), (double)S.sx[li[q]], false);
+            if (d.nclass > 1) k = kint_class((double)S.sv[li[q]], (double)S.sx[li[q]], false);   // sv holds |v|
           }
           cl[q] = k;
           rk[q] = atomicAdd(&A.kc[k], 1);

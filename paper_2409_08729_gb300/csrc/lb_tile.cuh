@@ -159,12 +159,12 @@ __device__ __forceinline__ int tile_key(int r, T v, T x, int* n) {
   *n = 0;
   if constexpr (sizeof(T) == 8 && !DX) {
     if (r == R_MU20) {
-      *n = mu_terms<20>((float)v, (float)x);
+      *n = mu_terms<20>(f32_cut(v), f32_cut(x));
       return KEY_MU20 + *n - 1;
     }
   }
   if (KIND == KIND_I && r == R_FALLBACK)
-    return KEY_FB + min(14, (int)(3.0f * __log2f(1.0f + (float)x)));
+    return KEY_FB + min(14, (int)(3.0f * __log2f(1.0f + (sizeof(T) == 8 ? f32_cut((double)x) : (float)x))));
   return region_key_first(r);
 }
 
@@ -233,7 +233,10 @@ __device__ __forceinline__ void tile_bin(TileShared<T, NT>& S, const T* __restri
     if (i < n) {
       T vi = vv[it];
       const T xi = xx[it];
-      if (KIND == KIND_K) vi = fabs(vi);
+      if constexpr (KIND == KIND_K) {
+        if constexpr (sizeof(T) == 8) vi = __longlong_as_double(__double_as_longlong(vi) & 0x7fffffffffffffffLL);
+        else vi = fabsf(vi);
+      }
       T sp;
       if (tile_special<KIND, DX, T>(vi, xi, &sp)) {
         S.sres[li] = sp;
@@ -334,7 +337,7 @@ __device__ __forceinline__ void tile_eval_region(TileShared<T, NT>& S, int lane,
     const int li = S.list[jl];
     int nterm = S.nt[li];
     if constexpr (sizeof(T) == 8 && !DX && KIND == KIND_I && R == R_FALLBACK)
-      nterm = series_terms((float)(so ? so->v : (double)S.sv[li]), (float)S.sx[li]);
+      nterm = series_terms(f32_cut(so ? so->v : (double)S.sv[li]), f32_cut((double)S.sx[li]));
     T val;
     if constexpr (sizeof(T) == 8 && !DX) {
       if (so) val = tile_expr_so<KIND>(R, *so, S.sx[li], nterm);

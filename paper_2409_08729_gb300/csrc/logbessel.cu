@@ -127,7 +127,7 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
           uint32_t cl = 0;
           if constexpr (sizeof(T) == 8) {
             if (mode == MODE_TIGHT) {
-              cl = (uint32_t)kint_class(fabs((double)S.sv[li]), (double)S.sx[li], DX);
+              cl = (uint32_t)kint_class((double)S.sv[li], (double)S.sx[li], DX);   // sv holds |v|
               cls |= 1u << cl;
             }
           }
