@@ -32,7 +32,7 @@ METRIC = "Gevals/s (log I_v and log K_v, FP64)"
 # capture of every launch of one full-size step (the launch list of
 # profiles/launches_paper_sweep_fp64.md, with dram__bytes_read.sum and
 # dram__bytes_write.sum); empty when the kernels changed since.
-NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.415e9, 27), "lb_kint_kernel": (8.555e9, 90)}
+NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.418e9, 27), "lb_kint_kernel": (8.564e9, 90)}
 # Pipe utilisation of each kernel from ncu --set full on a small case of the
 # same workload (profiles/lb_tiles_kernel_sweep_small.md,
 # profiles/lb_kint_kernel_sweep_small.md, profiles/fp32_mixed_sweep_small.md):
@@ -40,11 +40,11 @@ NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.415e9, 27), "lb_kint_kernel": 
 # the XU (special-function) pipe while active, and the share of cycles that
 # issue; empty when stale.
 NCU_PIPES = {
-    "lb_tiles_kernel": {"fp64": 0.739, "alu": 0.404, "fma": 0.275, "xu": 0.023, "issue_active": 0.618,
+    "lb_tiles_kernel": {"fp64": 0.618, "alu": 0.460, "fma": 0.300, "xu": 0.025, "issue_active": 0.675,
                         "launch": "log I, mixed orders, 11M pairs"},
-    "lb_kint_kernel": {"fp64": 0.655, "alu": 0.646, "fma": 0.185, "xu": 0.017, "issue_active": 0.671,
-                       "launch": "one-slot class kernel of a mixed-order log K call (class 4: fp64 0.508, "
-                                 "alu 0.630, issue 0.624)"},
+    "lb_kint_kernel": {"fp64": 0.646, "alu": 0.648, "fma": 0.185, "xu": 0.017, "issue_active": 0.671,
+                       "launch": "one-slot class kernel of a mixed-order log K call (class 4: fp64 0.486, "
+                                 "alu 0.638, issue 0.632)"},
 }
 NCU_PIPES_FP32 = {
     "lb_tiles_kernel": {"fp64": 0.0, "alu": 0.450, "fma": 0.235, "xu": 0.111, "issue_active": 0.760,
