@@ -12,6 +12,10 @@ in 64- and 128-bit integers instead of doubles:
        Q116 (the entry for j = 511 is this same constant).
   Horner coefficients of e^r - 1 and log(1 + r) in Q31 (inner steps, done
   with 32-bit multiplies) and Q62.
+  Fixed-point forms for sums of exponentials of logarithms (the K-integral
+       nodes, ix_log_q53 and ix_exp_q58_fx): -log(C_j / 2^13) in Q63; ln 2
+       as A 2^-31 + B 2^-63 + C 2^-95 (A, B, C integers below 2^32); ln2/512
+       as (H + M 2^-32) 2^-64.
   rcp and rsqrt reuse the log's C_j (m C_j / 2^13 = 1 + r): 1/m =
        (C_j / 2^13) / (1 + r), m^-1/2 = sqrt(C_j / 2^13) (1 + r)^-1/2, with
        sqrt(C_j / 2^13) in Q63 and the binomial coefficients of
@@ -68,12 +72,23 @@ def main():
     L.append(arr("uint16_t", "lb_ix_log_c", c, lambda v: "%d" % v))
     L.append(arr("int64_t", "lb_ix_log_thi", th, lambda v: "%dll" % v))
     L.append(arr("uint64_t", "lb_ix_log_tlo", tl, u64))
+    t63 = [0 if j == 0 else q(-mp.log(mp.mpf(cj) / 2 ** 13), 63) for j, cj in enumerate(c)]
+    assert all(abs(v) < 1 << 63 for v in t63) and t63[511] == q(mp.log(2), 63)
+    L.append(arr("int64_t", "lb_ix_log_t63", t63, lambda v: "%dll" % v))
     hi, lo = split128(q(mp.log(2) / 512, 116))
     L.append("#define LB_IX_L512_HI %dull" % hi)
     L.append("#define LB_IX_L512_LO 0x%016xull" % lo)
     hi, lo = split128(ln2)
     L.append("#define LB_IX_LN2_HI %dull" % hi)
     L.append("#define LB_IX_LN2_LO 0x%016xull" % lo)
+    l95 = q(mp.log(2), 95)
+    assert l95 >> 64 < 1 << 31
+    L.append("#define LB_IX_LN2_A %dll" % (l95 >> 64))
+    L.append("#define LB_IX_LN2_B %dll" % ((l95 >> 32) & 0xffffffff))
+    L.append("#define LB_IX_LN2_C %dll" % (l95 & 0xffffffff))
+    l96 = q(mp.log(2) / 512, 96)
+    L.append("#define LB_IX_L512_H %dull" % (l96 >> 32))
+    L.append("#define LB_IX_L512_M %dull" % (l96 & 0xffffffff))
     # e^r - 1 = r (1 + r (1/2 + r (1/6 + r (1/24 + r/120)))): the inner three
     # coefficients in Q31 (32-bit steps), the outer two in Q62
     for k in (3, 4, 5):
@@ -86,6 +101,8 @@ def main():
         L.append("#define LB_IX_L%d %d" % (k, q(mp.mpf(1) / k, 31)))
     for k in (1, 2, 3):
         L.append("#define LB_IX_L%d %dll" % (k, q(mp.mpf(1) / k, 62)))
+    # the Q53 log (ix_log_q53) stops at r^5 and takes 1/3 in Q31 too
+    L.append("#define LB_IX_L3S %d" % q(mp.mpf(1) / 3, 31))
     # rsqrt: sqrt(C_j / 2^13) in Q63 (at most 2^63, for j = 0)
     rsq = [q(mp.sqrt(mp.mpf(cj) / 2 ** 13), 63) for cj in c]
     assert all(v <= 1 << 63 for v in rsq)

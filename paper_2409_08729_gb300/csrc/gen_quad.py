@@ -25,7 +25,10 @@ N = 600.  These tables hold Gauss rules for the same two pieces instead:
            22 + 10 nodes (2 <= v < 7), s0 = 3 with 12 + 20 (7 <= v <= 16.5).
 
 Writes kquad_tables.h beside this file.  Nodes and weights are computed in
-40-digit arithmetic and rounded to double.
+40-digit arithmetic and rounded to double.  The log terms that the values'
+fixed-point node sums use (c_j and y_j of the tables the one-slot, packed
+and fixed rules take, log 8 and log 3) are also written in Q53 (int64,
+round(value 2^53)), rounded from the 40-digit values.
 """
 import os
 import sys
@@ -76,6 +79,14 @@ def arr(name, vals):
             + "static __device__ const float %s[%d] = {\n  %s};\n" % (name.replace("lb_kq_", "lb_kqf_"), len(fl), bodyf))
 
 
+def arrq(name, vals):
+    """The table in Q53: round(value 2^53) as int64, named name + "_q"."""
+    q = [int(mp.nint(mp.mpf(v) * mp.mpf(2) ** 53)) for v in vals]
+    assert all(abs(v) < 1 << 63 for v in q)
+    body = ",\n  ".join(", ".join("%dll" % v for v in q[i:i + 4]) for i in range(0, len(q), 4))
+    return "static __device__ const long long %s_q[%d] = {\n  %s};\n" % (name, len(q), body)
+
+
 def main():
     out = sys.argv[1] if len(sys.argv) > 1 else os.path.join(os.path.dirname(os.path.abspath(__file__)), "kquad_tables.h")
     parts = ["// Generated by gen_quad.py -- do not edit.",
@@ -88,6 +99,7 @@ def main():
         parts.append(arr("lb_kq_g%d_logw" % N, [mp.log(a) for a in w]))
         parts.append("// log w_j + (n - 1) log u_j with n = 8 (the u^(n-1) factor of g folded in)")
         parts.append(arr("lb_kq_g%d_c" % N, [mp.log(b) + 7 * mp.log(a) for a, b in zip(u, w)]))
+        parts.append(arrq("lb_kq_g%d_c" % N, [mp.log(b) + 7 * mp.log(a) for a, b in zip(u, w)]))
     for N in (16, 32):
         t, w = gauss_legendre01(N)
         parts.append("// plain Gauss-Legendre on [0,1], %d nodes: t_j and log w_j (panels placed per pair)" % N)
@@ -102,11 +114,15 @@ def main():
         parts.append(arr("lb_kq_hl%d_s" % N, [mp.exp(a) for a in ys]))
         parts.append(arr("lb_kq_hl%d_y" % N, ys))
         parts.append(arr("lb_kq_hl%d_c" % N, [mp.log(wj * Y) + yj - mp.exp(yj) for wj, yj in zip(w, ys)]))
+        parts.append(arrq("lb_kq_hl%d_y" % N, ys))
+        parts.append(arrq("lb_kq_hl%d_c" % N, [mp.log(wj * Y) + yj - mp.exp(yj) for wj, yj in zip(w, ys)]))
     t, lam = gauss_laguerre(32)
     parts.append("// h piece, Gauss-Laguerre in t = s - 1, 32 nodes: 1 + t_j, log(1 + t_j), log(lambda_j) - 1")
     parts.append(arr("lb_kq_hq32_s", [1 + a for a in t]))
     parts.append(arr("lb_kq_hq32_y", [mp.log(1 + a) for a in t]))
     parts.append(arr("lb_kq_hq32_c", [mp.log(a) - 1 for a in lam]))
+    parts.append(arrq("lb_kq_hq32_y", [mp.log(1 + a) for a in t]))
+    parts.append(arrq("lb_kq_hq32_c", [mp.log(a) - 1 for a in lam]))
     for N, s0 in ((10, 8), (20, 3)):
         t, lam = gauss_laguerre(N)
         tag = "hq%do%d" % (N, s0)
@@ -115,9 +131,13 @@ def main():
         parts.append(arr("lb_kq_%s_s" % tag, [s0 + a for a in t]))
         parts.append(arr("lb_kq_%s_y" % tag, [mp.log(s0 + a) for a in t]))
         parts.append(arr("lb_kq_%s_c" % tag, [mp.log(a) - s0 for a in lam]))
+        parts.append(arrq("lb_kq_%s_y" % tag, [mp.log(s0 + a) for a in t]))
+        parts.append(arrq("lb_kq_%s_c" % tag, [mp.log(a) - s0 for a in lam]))
     parts.append("// log 8 and log 3, the split points of the one-slot rules")
     parts.append("#define LB_KQ_LOG8 %r" % float(mp.log(8)))
     parts.append("#define LB_KQ_LOG3 %r" % float(mp.log(3)))
+    parts.append("#define LB_KQ_LOG8_Q53 %dll" % int(mp.nint(mp.log(8) * mp.mpf(2) ** 53)))
+    parts.append("#define LB_KQ_LOG3_Q53 %dll" % int(mp.nint(mp.log(3) * mp.mpf(2) ** 53)))
     with open(out, "w") as f:
         f.write("\n".join(parts) + "\n")
 

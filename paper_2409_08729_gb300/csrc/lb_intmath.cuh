@@ -25,6 +25,9 @@
 //     degree-6 polynomial, and e ln2 - log(C_j / 2^13) + log(1 + r) summed
 //     in Q116 (128 bits): error below 0.51 ulp.  Other arguments (zero,
 //     negative, subnormal, infinite, NaN) go to the libm log.
+//   ix_log_q53, ix_mul_q58, ix_exp_q58_fx: the same methods between fixed-
+//     point values (Q53 logarithms in, a Q58 exponential out), for sums of
+//     e^(c + a log z - m) that never need the intermediate doubles.
 //
 // The functions are plain integer code: compiled for the host (without
 // __CUDACC__) they give bit-identical results, which the CPU test suite
@@ -130,6 +133,22 @@ LB_IX_FN uint32_t ix_fbits(float f) {
 #endif
 }
 
+// 2^(j/512) (1 + p) in Q62 for y = (k/512) ln2 + r, r in Q73 (|r| < 2^-10.2),
+// j = k mod 512, p = e^r - 1.
+LB_IX_FN int64_t ix_exp_finish(int64_t r, int k) {
+  // e^r - 1 = r (1 + r (1/2 + r (1/6 + r (1/24 + r/120)))).  The steps for
+  // 1/24 and 1/6 enter the result times r^3 (|r| < 2^-10.2), so 32-bit
+  // precision (Q31, r in Q41) suffices there; 1/2 and 1 are carried in Q62.
+  const int32_t r32 = (int32_t)(r >> 32);                   // Q41
+  int32_t a3 = LB_IX_E4 + (ix_mulhi32(LB_IX_E5, r32) >> 9);
+  a3 = LB_IX_E3 + (ix_mulhi32(a3, r32) >> 9);
+  int64_t a = LB_IX_E2 + (ix_mul64x32hi(r, a3) >> 10);      // r a3 in Q72
+  a = LB_IX_E1 + (ix_mulhi(a, r) >> 9);
+  const int64_t p = ix_mulhi(a, r);                         // Q71
+  const int64_t t = (int64_t)LB_IX_LOAD(lb_ix_exp_t + (k & 511));   // 2^(j/512), Q62
+  return t + (ix_mulhi(t, p) >> 7);                         // Q62, in [0.999, 2.002)
+}
+
 // e^y = 2^(k/512) (1 + p) for 2^-64 <= |y| <= 708, y given by its bits b
 // (biased exponent E, sign neg): returns 2^(j/512) (1 + p) in Q62, in
 // [0.999, 2.002), and k.
@@ -153,18 +172,8 @@ LB_IX_FN int64_t ix_exp_core(uint64_t b, int E, bool neg, int& kout) {
   int64_t r = (int64_t)((rhi << 21) | (rlo >> 43));
   int k = (int)ak;
   if (neg) { r = -r; k = -k; }
-  // e^r - 1 = r (1 + r (1/2 + r (1/6 + r (1/24 + r/120)))).  The steps for
-  // 1/24 and 1/6 enter the result times r^3 (|r| < 2^-10.4), so 32-bit
-  // precision (Q31, r in Q41) suffices there; 1/2 and 1 are carried in Q62.
-  const int32_t r32 = (int32_t)(r >> 32);                   // Q41
-  int32_t a3 = LB_IX_E4 + (ix_mulhi32(LB_IX_E5, r32) >> 9);
-  a3 = LB_IX_E3 + (ix_mulhi32(a3, r32) >> 9);
-  int64_t a = LB_IX_E2 + (ix_mul64x32hi(r, a3) >> 10);      // r a3 in Q72
-  a = LB_IX_E1 + (ix_mulhi(a, r) >> 9);
-  const int64_t p = ix_mulhi(a, r);                         // Q71
-  const int64_t t = (int64_t)LB_IX_LOAD(lb_ix_exp_t + (k & 511));   // 2^(j/512), Q62
   kout = k;
-  return t + (ix_mulhi(t, p) >> 7);                         // Q62, in [0.999, 2.002)
+  return ix_exp_finish(r, k);
 }
 
 LB_IX_FN double ix_exp(double y) {
@@ -263,6 +272,86 @@ LB_IX_FN double ix_log(double z) {
   const uint64_t m53 = (top >> 11) + ((top >> 10) & 1u);    // [2^52, 2^53] (no overflow at top ~ 2^64)
   const int biased = 11 - lz + 1023;                        // value = top 2^(11 - lz - 63)
   return ix_double(sign | (((uint64_t)(biased - 1) << 52) + m53));
+}
+
+// ---------------------------------------------------------------------------
+// Fixed point for sums of terms e^(c + a log z - m): the K-integral nodes
+// (lb_kint.cuh) keep each node's logarithm term in Q53 (an int64 holding
+// value 2^53; |value| < 2^10), form it, its warp maximum and the shift by
+// that maximum with integer instructions, and exponentiate the shifted
+// term from Q53 straight into the Q58 sum.  No double is packed or unpacked
+// between the steps, and no FP64 instruction runs.
+// ---------------------------------------------------------------------------
+
+// round(d 2^q) for |d| < 2^(62 - q), from the bit fields (ties away from 0;
+// zero and subnormals give 0).
+LB_IX_FN int64_t ix_fix(double d, int q) {
+  const uint64_t b = ix_bits(d);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const uint64_t M = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
+  const int s = E - 1075 + q;                               // value 2^q = M 2^s
+  int64_t m;
+  if (E == 0 || s < -54) m = 0;
+  else if (s >= 0) m = (int64_t)(M << s);
+  else m = (int64_t)((M + (1ull << (-s - 1))) >> -s);
+  return (b >> 63) ? -m : m;
+}
+
+// round(a b 2^-58): a in Q58 times b in Q53, in Q53 (|a b| below 2^10 in
+// value); ties up.
+LB_IX_FN int64_t ix_mul_q58(int64_t a, int64_t b) {
+  const int64_t hi = ix_mulhi(a, b);
+  const uint64_t lo = (uint64_t)a * (uint64_t)b;
+  const uint64_t lo2 = lo + (1ull << 57);
+  const uint64_t hi2 = (uint64_t)hi + (lo2 < lo ? 1u : 0u);
+  return (int64_t)((hi2 << 6) | (lo2 >> 58));
+}
+
+// log z in Q53 for positive normal z (the reduction of ix_log; the sum
+// -log(C_j / 2^13) + log(1 + r) in Q63 and e ln2 from its 95-bit form):
+// within 0.56 units of 2^-53.  For this precision log(1 + r) stops at r^5
+// (r^6/6 below 2^-61.4, and below 2^-56.6 in the first interval, j = 0,
+// where r reaches 2^-9), and a step's error enters times r^k after k more
+// steps, so 1/4 - r/5 and 1/3 - r(...) run in 32 bits (Q31),
+// 1/2 - r(...) as a 64 x 32-bit product and only the last two in 64 bits.
+// Zero, negative, subnormal, infinite and NaN z give -2^62 (a term that
+// vanishes); the callers pass positive normal z.
+LB_IX_FN int64_t ix_log_q53(double z) {
+  const uint64_t b = ix_bits(z);
+  const uint32_t hi = (uint32_t)(b >> 32);
+  if (hi < 0x00100000u || hi >= 0x7ff00000u) return -(1ll << 62);
+  const int e = (int)(hi >> 20) - 1023;
+  const uint64_t F = b & 0x000fffffffffffffull;
+  const int j = (int)(F >> 43);
+  const int64_t r = (int64_t)((F | 0x0010000000000000ull) * (uint64_t)LB_IX_LOAD(lb_ix_log_c + j));   // Q65
+  const int32_t r32 = (int32_t)(r >> 32);                   // Q33
+  int32_t a3 = LB_IX_L4 - (ix_mulhi32(LB_IX_L5, r32) >> 1);
+  a3 = LB_IX_L3S - (ix_mulhi32(a3, r32) >> 1);
+  int64_t a = LB_IX_L2 - (ix_mul64x32hi(r, a3) >> 2);
+  a = LB_IX_L1 - (ix_mulhi(a, r) >> 1);
+  // log(1 + r) = a r (Q62 x Q65 / 2^64 = Q63) plus -log(C_j / 2^13): |f| < 0.7
+  const int64_t f = ix_mulhi(a, r) + (int64_t)LB_IX_LOAD(lb_ix_log_t63 + j);
+  // e ln2 = e (A 2^-31 + B 2^-63 + C 2^-95): the last two parts with f in Q63
+  const int64_t lo63 = (int64_t)e * LB_IX_LN2_B + (((int64_t)e * LB_IX_LN2_C) >> 32) + f;
+  return (int64_t)((uint64_t)((int64_t)e * LB_IX_LN2_A) << 22) + ((lo63 + (1ll << 9)) >> 10);
+}
+
+// e^(d 2^-53) in unsigned Q58 (as ix_exp_q58) for d <= 0 in Q53; d <= -42
+// (in value) gives 0.  The reduction r = |y| - k ln2/512 is formed in Q64
+// modulo 2^64 (exact, as |r| < 2^-10.2) and carried to Q73.
+LB_IX_FN uint64_t ix_exp_q58_fx(int64_t d) {
+  if (d <= -(42ll << 53)) return 0;
+  const uint64_t ad = (uint64_t)(-d);                       // |y| in Q53, below 2^58.4
+  // k ~ rint(|y| 512 / ln2) from a single-precision copy of |y| (in Q21)
+  const float yf = (float)(int32_t)(ad >> 32);
+  const uint32_t ak = ix_fbits(fmaf(yf, 738.65986f / 2097152.0f, 12582912.0f)) - 0x4B400000u;
+  const uint64_t r64 = (ad << 11) - (uint64_t)ak * LB_IX_L512_H - (((uint64_t)ak * LB_IX_L512_M) >> 32);
+  const int64_t r = -(int64_t)(r64 << 9);                   // y = -|y|: r in Q73
+  const int k = -(int)ak;
+  const int64_t res = ix_exp_finish(r, k);                  // e^y = res 2^(k div 512 - 62)
+  const int sh = 4 - (k >> 9);                              // k div 512 <= 0
+  if (sh >= 64) return 0;
+  return ((uint64_t)res + (1ull << (sh - 1))) >> sh;
 }
 
 // Shared reduction of ix_rcp and ix_rsqrt: z = 2^e m, m in [1, 2),

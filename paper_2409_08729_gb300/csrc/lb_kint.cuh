@@ -98,6 +98,7 @@ __device__ __forceinline__ int kint_class(double v, double x, bool dx) {
 struct KintScalar {
   double ub24[24], ub32[32], ub64[64];
   double sg[22];                                   // s0 u_j^beta of the one-slot rule of v (if any)
+  long long ubq24[24], ubq32[32], ubq64[64], sgq[22];   // the same in Q53 (values' fixed-point terms)
   double pre;                                      // log(sqrt(pi)) - lgamma(v + 1/2)
 };
 
@@ -105,14 +106,22 @@ struct KintScalar {
 __device__ __forceinline__ void kint_scalar_setup(KintScalar& ks, double v) {
   const int tid = threadIdx.x;
   const double beta = 16.0 * ix_rcp(2.0 * v + 1.0);       // as in kint_batch_gauss
-  if (tid < 24) ks.ub24[tid] = ix_exp(beta * __ldg(lb_kq_g24_logu + tid));
-  else if (tid < 56) ks.ub32[tid - 24] = ix_exp(beta * __ldg(lb_kq_g32_logu + tid - 24));
-  else if (tid < 120) ks.ub64[tid - 56] = ix_exp(beta * __ldg(lb_kq_g64_logu + tid - 56));
-  else if (tid == 120) ks.pre = kHalfLogPi - lgamma(v + 0.5);
-  else if (tid >= 128 && tid < 150 && v >= 2.0 && v <= 16.5) {
+  if (tid < 24) {
+    ks.ub24[tid] = ix_exp(beta * __ldg(lb_kq_g24_logu + tid));
+    ks.ubq24[tid] = ix_fix(ks.ub24[tid], 53);
+  } else if (tid < 56) {
+    ks.ub32[tid - 24] = ix_exp(beta * __ldg(lb_kq_g32_logu + tid - 24));
+    ks.ubq32[tid - 24] = ix_fix(ks.ub32[tid - 24], 53);
+  } else if (tid < 120) {
+    ks.ub64[tid - 56] = ix_exp(beta * __ldg(lb_kq_g64_logu + tid - 56));
+    ks.ubq64[tid - 56] = ix_fix(ks.ub64[tid - 56], 53);
+  } else if (tid == 120) {
+    ks.pre = kHalfLogPi - lgamma(v + 0.5);
+  } else if (tid >= 128 && tid < 150 && v >= 2.0 && v <= 16.5) {
     const int j = tid - 128;
     if (v < 7.0) ks.sg[j] = ix_exp(fma(beta, __ldg(lb_kq_g22_logu + j), LB_KQ_LOG8));
     else if (j < 12) ks.sg[j] = ix_exp(fma(beta, __ldg(lb_kq_g12_logu + j), LB_KQ_LOG3));
+    if (v < 7.0 || j < 12) ks.sgq[j] = ix_fix(ks.sg[j], 53);
   }
   __syncthreads();
 }
@@ -211,22 +220,6 @@ __device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta
   }
 }
 
-// Exact warp maximum of doubles, on the integer pipe: key64 maps a double to
-// an int64 of the same order (negative values with all but the sign bit
-// flipped); the maximum key is found as its high word (one reduction) and
-// then the low word among the lanes that hold that high word (another).
-__device__ __forceinline__ long long key64(double a) {
-  const long long b = __double_as_longlong(a);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
-__device__ __forceinline__ double warp_max_key64(long long k) {
-  const int khi = (int)(k >> 32);
-  const int mhi = __reduce_max_sync(0xffffffffu, khi);
-  const unsigned mlo = __reduce_max_sync(0xffffffffu, khi == mhi ? (unsigned)k : 0u);
-  const long long m = (long long)(((unsigned long long)(unsigned)mhi << 32) | mlo);
-  return __longlong_as_double(m ^ ((m >> 63) & 0x7fffffffffffffffll));
-}
-
 // Warp sum of values below 2^63 (the result must stay below 2^64), exact,
 // on the integer pipe: three limbs of 20, 20 and 23 bits, one warp
 // reduction each (a limb sum stays below 2^28).
@@ -237,105 +230,249 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t t) {
   return (uint64_t)a0 + ((uint64_t)a1 << 20) + ((uint64_t)a2 << 40);
 }
 
-// Values (not the x-derivative) with the fixed or packed rules: the same
-// nodes as kint_sums_fixed / kint_sums_g24h40, with log beta (gk) added to
-// the g nodes' logarithms instead of beta multiplying their sum, and the
-// terms e^(L - mm) summed in Q56 fixed point on the integer pipe (mm the
-// exact maximum, so each term is at most 1; at most 4 terms per lane, so
-// the warp sum stays at most 2^63).
-__device__ __forceinline__ uint64_t kint_sumq_fixed(double v, double x, double beta, double gk, int ng, int hr,
-                                                    int lane, double& mm, const KintScalar* ks) {
-  const double vm = v - 0.5, tx = 2.0 * x;
+// Values (not the x-derivative) with the fixed, packed and one-slot rules.
+// Each node's log term L = C - S + (v - 1/2)(Y + log z) -- C the table
+// constant (plus the pair's gk for g nodes: log beta, and (v + 1/2) log s0
+// for the one-slot rules), Y = log s for h nodes, S = s for g nodes,
+// z = s + 2x -- is shifted by mm, the exact warp maximum of L, and the terms
+// e^(L - mm) are formed in Q58 (Q56 where a lane holds up to four terms)
+// and summed exactly on the integer pipe.
+//   FX (pairs with v <= 16.5, x <= 32: the K integral's whole domain in
+//   every dispatch): L, its maximum and the shift are Q53 fixed point
+//   (lb_intmath.cuh): integer instructions from log z to the Q58 term, with
+//   no double packed or unpacked between the steps.  The FP64 pipe does only
+//   z = s + 2x (and, with one order per pair, the g nodes' beta log u_j).
+//   |L| stays below 2^8 there, inside Q53's 2^10.
+//   !FX (a forced evaluation far outside, logbessel_eval_region): L as a
+//   double, whatever its size.
+
+// Warp maximum of signed 64-bit integers: the maximum high word (signed),
+// then the maximum low word (unsigned) among the lanes that hold it.
+__device__ __forceinline__ long long warp_max_i64(long long k) {
+  const int khi = (int)(k >> 32);
+  const int mhi = __reduce_max_sync(0xffffffffu, khi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, khi == mhi ? (unsigned)k : 0u);
+  return (long long)(((unsigned long long)(unsigned)mhi << 32) | mlo);
+}
+
+// A double mapped to an int64 of the same order (negative values with all
+// but the sign bit flipped), and back.
+__device__ __forceinline__ long long key64(double a) {
+  const long long b = __double_as_longlong(a);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double key64_to_double(long long m) {
+  return __longlong_as_double(m ^ ((m >> 63) & 0x7fffffffffffffffll));
+}
+
+// One node's log term in Q53 (vmq = v - 1/2 in Q58).
+__device__ __forceinline__ long long kq_term(long long vmq, double z, long long Y, long long C, long long S) {
+  return C - S + ix_mul_q58(vmq, Y + ix_log_q53(z));
+}
+
+// The pair's arguments of a values sum, broadcast to the warp: v - 1/2 and
+// gk in Q53/Q58 (FX) or as doubles, 2x, beta (g nodes per pair only).
+struct KqPair {
+  long long vmq, gkq;
+  double vm, gk, tx, beta;
+};
+
+template <bool FX> struct KqLog { typedef double type; };
+template <> struct KqLog<true> { typedef long long type; };
+
+// A node's operands: z = s + 2x, and Y, C, S of its log term (in Q53 for
+// FX, as doubles y, c, s otherwise).  Lanes that hold g nodes and lanes that
+// hold h nodes of the same slot select their operands and then share one
+// evaluation (kq_eval), so a warp runs the logarithm once per slot.
+struct KqNode {
+  double z, y, c, s;
+  long long Y, C, S;
+};
+
+// A g node: position s = e^(beta log u_j + log s0) per pair, or s from the
+// block's table (tab, tabq) with one order per call.
+template <bool FX>
+__device__ __forceinline__ KqNode kq_g(const KqPair& p, double logu, double logs0, const double* tab,
+                                       const long long* tabq, int j, const double* c, const long long* cq) {
+  KqNode n;
+  const double s = tab ? tab[j] : ix_exp(fma(p.beta, logu, logs0));
+  n.z = p.tx + s;
+  if constexpr (FX) {
+    n.S = tab ? tabq[j] : ix_fix(s, 53);
+    n.Y = 0;
+    n.C = __ldg(cq + j) + p.gkq;
+  } else {
+    n.s = s;
+    n.y = 0.0;
+    n.c = __ldg(c + j) + p.gk;
+  }
+  return n;
+}
+
+// An h node (tables s, y, c; y and c also in Q53).
+template <bool FX>
+__device__ __forceinline__ KqNode kq_h(const KqPair& p, const double* hs, const double* hy, const long long* hyq,
+                                       const double* hc, const long long* hcq, int j) {
+  KqNode n;
+  n.z = __ldg(hs + j) + p.tx;
+  if constexpr (FX) {
+    n.S = 0;
+    n.Y = __ldg(hyq + j);
+    n.C = __ldg(hcq + j);
+  } else {
+    n.s = 0.0;
+    n.y = __ldg(hy + j);
+    n.c = __ldg(hc + j);
+  }
+  return n;
+}
+
+// The node's log term C - S + (v - 1/2)(Y + log z).
+template <bool FX>
+__device__ __forceinline__ typename KqLog<FX>::type kq_eval(const KqPair& p, const KqNode& n) {
+  if constexpr (FX) return kq_term(p.vmq, n.z, n.Y, n.C, n.S);
+  else return fma(p.vm, ix_log(n.z) + n.y, n.c) - n.s;
+}
+
+// Order key of a log term for the warp maximum, the maximum from the
+// maximum key, and a term e^(L - mm) in Q58.
+template <bool FX> __device__ __forceinline__ long long kq_key(typename KqLog<FX>::type L) {
+  if constexpr (FX) return L; else return key64(L);
+}
+template <bool FX> __device__ __forceinline__ typename KqLog<FX>::type kq_max(long long key) {
+  if constexpr (FX) return warp_max_i64(key); else return key64_to_double(warp_max_i64(key));
+}
+template <bool FX>
+__device__ __forceinline__ uint64_t kq_exp(typename KqLog<FX>::type L, typename KqLog<FX>::type mm) {
+  if constexpr (FX) return ix_exp_q58_fx(L - mm); else return ix_exp_q58(L - mm);
+}
+
+template <bool FX>
+__device__ __forceinline__ uint64_t kint_sumq_fixed(const KqPair& p, int ng, int hr, int lane,
+                                                    typename KqLog<FX>::type& mm, const KintScalar* ks) {
+  typedef typename KqLog<FX>::type LT;
   const double* gu = ng == 32 ? lb_kq_g32_logu : lb_kq_g64_logu;
   const double* gc = ng == 32 ? lb_kq_g32_c : lb_kq_g64_c;
+  const long long* gcq = ng == 32 ? lb_kq_g32_c_q : lb_kq_g64_c_q;
   const double* hs = hr == 0 ? lb_kq_hl32_s : (hr == 1 ? lb_kq_hl48_s : lb_kq_hq32_s);
   const double* hy = hr == 0 ? lb_kq_hl32_y : (hr == 1 ? lb_kq_hl48_y : lb_kq_hq32_y);
+  const long long* hyq = hr == 0 ? lb_kq_hl32_y_q : (hr == 1 ? lb_kq_hl48_y_q : lb_kq_hq32_y_q);
   const double* hc = hr == 0 ? lb_kq_hl32_c : (hr == 1 ? lb_kq_hl48_c : lb_kq_hq32_c);
+  const long long* hcq = hr == 0 ? lb_kq_hl32_c_q : (hr == 1 ? lb_kq_hl48_c_q : lb_kq_hq32_c_q);
   const int nh = hr == 1 ? 48 : 32;
-  double L[4];
+  const double* gtab = ks ? (ng == 32 ? ks->ub32 : ks->ub64) : nullptr;
+  const long long* gtabq = ks ? (ng == 32 ? ks->ubq32 : ks->ubq64) : nullptr;
+  LT L[4];
   long long key = (long long)0x8000000000000000ull;   // below every key
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    L[k] = 0.0;
+    L[k] = 0;
     if (32 * k < ng) {
       const int j = lane + 32 * k;
-      const double ub = ks ? (ng == 32 ? ks->ub32[j] : ks->ub64[j]) : ix_exp(beta * __ldg(gu + j));
-      L[k] = fma(vm, ix_log(tx + ub), __ldg(gc + j) + gk) - ub;
-      key = max(key, key64(L[k]));
+      L[k] = kq_eval<FX>(p, kq_g<FX>(p, __ldg(gu + j), 0.0, gtab, gtabq, j, gc, gcq));
+      key = max(key, kq_key<FX>(L[k]));
     }
   }
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int j = lane + 32 * k;
-    L[2 + k] = 0.0;
+    L[2 + k] = 0;
     if (j < nh) {
-      const double sj = __ldg(hs + j);
-      L[2 + k] = fma(vm, __ldg(hy + j) + ix_log(sj + tx), __ldg(hc + j));
-      key = max(key, key64(L[2 + k]));
+      L[2 + k] = kq_eval<FX>(p, kq_h<FX>(p, hs, hy, hyq, hc, hcq, j));
+      key = max(key, kq_key<FX>(L[2 + k]));
     }
   }
-  mm = warp_max_key64(key);
+  mm = kq_max<FX>(key);
   uint64_t q = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const bool live = (k < 2) ? (32 * k < ng) : (lane + 32 * (k - 2) < nh);
-    if (live) q += ix_exp_q58(L[k] - mm) >> 2;
+    if (live) q += kq_exp<FX>(L[k], mm) >> 2;
   }
   return warp_sum_u64(q);
 }
 
-__device__ __forceinline__ uint64_t kint_sumq_g24h40(double v, double x, double beta, double gk, int lane,
-                                                     double& mm, const KintScalar* ks) {
-  const double vm = v - 0.5, tx = 2.0 * x;
-  const bool isg = lane < 24;
-  const int jh = isg ? 0 : lane - 24;
-  double s;
-  if (isg) s = ks ? ks->ub24[lane] : ix_exp(beta * __ldg(lb_kq_g24_logu + lane));
-  else s = __ldg(lb_kq_hl40_s + jh);
-  const double y0 = isg ? 0.0 : __ldg(lb_kq_hl40_y + jh);
-  const double c0 = isg ? __ldg(lb_kq_g24_c + lane) + gk : __ldg(lb_kq_hl40_c + jh);
-  const double L0 = fma(vm, ix_log(tx + s) + y0, c0) - (isg ? s : 0.0);
-  const double sh = __ldg(lb_kq_hl40_s + 8 + lane);
-  const double L1 = fma(vm, __ldg(lb_kq_hl40_y + 8 + lane) + ix_log(sh + tx), __ldg(lb_kq_hl40_c + 8 + lane));
-  mm = warp_max_key64(max(key64(L0), key64(L1)));
-  return warp_sum_u64((ix_exp_q58(L0 - mm) >> 2) + (ix_exp_q58(L1 - mm) >> 2));
+template <bool FX>
+__device__ __forceinline__ uint64_t kint_sumq_g24h40(const KqPair& p, int lane, typename KqLog<FX>::type& mm,
+                                                     const KintScalar* ks) {
+  typedef typename KqLog<FX>::type LT;
+  const KqNode n0 = lane < 24 ? kq_g<FX>(p, __ldg(lb_kq_g24_logu + lane), 0.0, ks ? ks->ub24 : nullptr,
+                                         ks ? ks->ubq24 : nullptr, lane, lb_kq_g24_c, lb_kq_g24_c_q)
+                              : kq_h<FX>(p, lb_kq_hl40_s, lb_kq_hl40_y, lb_kq_hl40_y_q, lb_kq_hl40_c, lb_kq_hl40_c_q,
+                                         lane - 24);
+  const LT L0 = kq_eval<FX>(p, n0);
+  const LT L1 = kq_eval<FX>(p, kq_h<FX>(p, lb_kq_hl40_s, lb_kq_hl40_y, lb_kq_hl40_y_q, lb_kq_hl40_c, lb_kq_hl40_c_q,
+                                        lane + 8));
+  mm = kq_max<FX>(max(kq_key<FX>(L0), kq_key<FX>(L1)));
+  return warp_sum_u64((kq_exp<FX>(L0, mm) >> 2) + (kq_exp<FX>(L1, mm) >> 2));
 }
 
 // One pair, one lane slot (values, 2 <= v <= 16.5).  int_0^inf F(s) ds is
 // split at s0 instead of 1: on [s0, inf), t = s - s0, the branch point s = 0
 // of (s (s + 2x))^(v-1/2) is s0 away from the Gauss-Laguerre nodes, so 10
 // or 20 of them reach 1e-17; [0, s0] takes s = s0 u^beta and Gauss-Legendre
-// in u on the remaining lanes.  A g node is c + gk + (v-1/2) log(2x + s) - s
-// with gk = (v+1/2) log s0 + log beta (per pair), an h node
-// c + (v-1/2)(y + log(s + 2x)) with y = log s and -s0 in c.  Rule 4: s0 = 8,
-// 22 g + 10 h nodes (2 <= v < 7); rule 5: s0 = 3, 12 + 20 (7 <= v <= 16.5).
-// Error map against a 34-digit reference, over x in [1e-300, 30]: below
-// 1.5e-17 of the error scale max(1, |x d/dx log K|, |v d/dv log K|).
-// The terms e^(L - mm) (each at most 1: mm is the exact warp maximum of L)
-// are formed in Q58 fixed point and summed exactly on the integer pipe
-// (warp_sum_u64): the FP64 pipe does only the node's logarithm arguments.
-// Returns the sum, on every lane, in Q58.
-__device__ __forceinline__ uint64_t kint_sum_one(double v, double x, double beta, double gk, int hr, int lane,
-                                                 double& mm, const KintScalar* ks) {
+// in u on the remaining lanes.  A g node's constant is c + gk with
+// gk = (v+1/2) log s0 + log beta (per pair), an h node's c (with -s0 folded
+// in) and Y = log s.  Rule 4: s0 = 8, 22 g + 10 h nodes (2 <= v < 7);
+// rule 5: s0 = 3, 12 + 20 (7 <= v <= 16.5).  Error map against a 34-digit
+// reference, over x in [1e-300, 30]: below 1.5e-17 of the error scale
+// max(1, |x d/dx log K|, |v d/dv log K|).  Returns the sum, on every lane,
+// in Q58.
+template <bool FX>
+__device__ __forceinline__ uint64_t kint_sum_one(const KqPair& p, int hr, int lane, typename KqLog<FX>::type& mm,
+                                                 const KintScalar* ks) {
+  typedef typename KqLog<FX>::type LT;
   const bool r4 = hr == 4;
   const int ng = r4 ? 22 : 12;
-  const double vm = v - 0.5, tx = 2.0 * x;
-  const bool isg = lane < ng;
-  double s, y, c;
-  if (isg) {
-    s = ks ? ks->sg[lane]
-           : ix_exp(fma(beta, __ldg((r4 ? lb_kq_g22_logu : lb_kq_g12_logu) + lane), r4 ? LB_KQ_LOG8 : LB_KQ_LOG3));
-    y = 0.0;
-    c = __ldg((r4 ? lb_kq_g22_c : lb_kq_g12_c) + lane) + gk;
-  } else {
-    const int j = lane - ng;
-    s = __ldg((r4 ? lb_kq_hq10o8_s : lb_kq_hq20o3_s) + j);
-    y = __ldg((r4 ? lb_kq_hq10o8_y : lb_kq_hq20o3_y) + j);
-    c = __ldg((r4 ? lb_kq_hq10o8_c : lb_kq_hq20o3_c) + j);
+  const KqNode n = lane < ng ? kq_g<FX>(p, __ldg((r4 ? lb_kq_g22_logu : lb_kq_g12_logu) + lane),
+                                        r4 ? LB_KQ_LOG8 : LB_KQ_LOG3, ks ? ks->sg : nullptr, ks ? ks->sgq : nullptr,
+                                        lane, r4 ? lb_kq_g22_c : lb_kq_g12_c, r4 ? lb_kq_g22_c_q : lb_kq_g12_c_q)
+                             : kq_h<FX>(p, r4 ? lb_kq_hq10o8_s : lb_kq_hq20o3_s, r4 ? lb_kq_hq10o8_y : lb_kq_hq20o3_y,
+                                        r4 ? lb_kq_hq10o8_y_q : lb_kq_hq20o3_y_q, r4 ? lb_kq_hq10o8_c : lb_kq_hq20o3_c,
+                                        r4 ? lb_kq_hq10o8_c_q : lb_kq_hq20o3_c_q, lane - ng);
+  const LT L = kq_eval<FX>(p, n);
+  mm = kq_max<FX>(kq_key<FX>(L));
+  return warp_sum_u64(kq_exp<FX>(L, mm));
+}
+
+// The pairs of one values rule group (lanes in grp), one at a time: the
+// pair's arguments broadcast from its lane, its sum by the warp, and the
+// sum and shift kept on its lane.
+template <bool FX, int CLS>
+__device__ __forceinline__ void kint_q_group(unsigned grp, int ng, int hr, int lane, long long vmq_i, long long gkq_i,
+                                             double vm_i, double gk_i, double tx_i, double beta_i, double& m_i,
+                                             long long& mq_i, uint64_t& q_i, const KintScalar* ks) {
+  for (; grp; grp &= grp - 1) {
+    const int e = __ffs(grp) - 1;
+    KqPair p;
+    if constexpr (FX) {
+      p.vmq = __shfl_sync(0xffffffffu, vmq_i, e);
+      p.gkq = __shfl_sync(0xffffffffu, gkq_i, e);
+    } else {
+      p.vm = __shfl_sync(0xffffffffu, vm_i, e);
+      p.gk = __shfl_sync(0xffffffffu, gk_i, e);
+    }
+    p.tx = __shfl_sync(0xffffffffu, tx_i, e);
+    p.beta = ks ? 0.0 : __shfl_sync(0xffffffffu, beta_i, e);
+    typename KqLog<FX>::type mm = 0;
+    uint64_t q = 0;
+    if constexpr (CLS == 1 || CLS == 2) {
+      q = kint_sum_one<FX>(p, hr, lane, mm, ks);
+    } else if constexpr (CLS == 3) {
+      q = kint_sumq_g24h40<FX>(p, lane, mm, ks);
+    } else if constexpr (CLS == 4 || CLS == 5) {
+      q = kint_sumq_fixed<FX>(p, ng, hr, lane, mm, ks);
+    } else if constexpr (CLS < 0) {
+      if (hr >= 4) q = kint_sum_one<FX>(p, hr, lane, mm, ks);
+      else if (ng == 24) q = kint_sumq_g24h40<FX>(p, lane, mm, ks);
+      else q = kint_sumq_fixed<FX>(p, ng, hr, lane, mm, ks);
+    }
+    if (lane == e) {
+      if constexpr (FX) mq_i = mm;                 // to a double once, after the batch
+      else m_i = mm;
+      q_i = q;
+    }
   }
-  const double L = fma(vm, ix_log(tx + s) + y, c) - (isg ? s : 0.0);
-  mm = warp_max_key64(key64(L));
-  return warp_sum_u64(ix_exp_q58(L - mm));
 }
 
 // Split g rule (v < 0.4, x < 1e-3).  (2x + u^beta)^(v-1/2) turns within a
@@ -488,14 +625,31 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
   static_assert(CLS < 0 || !DX, "class-specialized batches are built for values only");
   const double beta_i = 16.0 * ix_rcp(2.0 * vi + 1.0);   // the reciprocal on the integer pipe
   const int rule_i = kint_rule(vi, xi, DX);
-  // values: the g nodes' common factor as a log, beta (s0^(v+1/2) beta for
-  // the one-slot rules), added to their logarithms
-  double gk_i = 0.0;
+  // values: the g nodes' common factor as a log, log beta (plus
+  // (v + 1/2) log s0 = (v - 1/2) log s0 + log s0 for the one-slot rules),
+  // added to their log terms; in the fixed-point domain (v <= 16.5, x <= 32)
+  // in Q53 with v - 1/2 in Q58, else as doubles
+  const bool fx_i = !DX && LB_LE(vi, 16.5) && LB_LE(xi, 32.0);
+  long long vmq_i = 0, gkq_i = 0;
+  double vm_i = 0.0, gk_i = 0.0;
   if (!DX) {
-    gk_i = ix_log(beta_i);
-    if ((rule_i >> 8) >= 4) gk_i = fma(vi + 0.5, (rule_i >> 8) == 4 ? LB_KQ_LOG8 : LB_KQ_LOG3, gk_i);
+    const int hr_i = rule_i >> 8;
+    if (fx_i) {
+      vmq_i = ix_fix(vi - 0.5, 58);
+      gkq_i = ix_log_q53(beta_i);
+      if (hr_i >= 4) {
+        const long long ls0 = hr_i == 4 ? LB_KQ_LOG8_Q53 : LB_KQ_LOG3_Q53;
+        gkq_i += ix_mul_q58(vmq_i, ls0) + ls0;
+      }
+    } else {
+      vm_i = vi - 0.5;
+      gk_i = ix_log(beta_i);
+      if (hr_i >= 4) gk_i = fma(vi + 0.5, hr_i == 4 ? LB_KQ_LOG8 : LB_KQ_LOG3, gk_i);
+    }
   }
+  const double tx_i = 2.0 * xi;
   double m_i = 0.0, s0_i = 1.0, s1_i = 0.0;
+  long long mq_i = 0;                              // the shift of a fixed-point pair, Q53
   uint64_t q_i = 0;                                // fixed-point sum (values, all rules but the split one)
   int qb_i = 0;                                    // its fraction bits
   // The pairs are taken rule by rule (lanes with the same rule found by a
@@ -503,39 +657,22 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
   // the next rule's: in a batch that mixes rules, switching code paths at
   // every pair thrashed the instruction cache.  The order of the pairs does
   // not change any result.
+  // Pairs outside the fixed-point domain form groups of their own.
+  const int key_i = rule_i | (fx_i ? 0 : 1 << 16);
   unsigned rem = npairs >= 32 ? 0xffffffffu : ((1u << npairs) - 1u);
   while (rem) {
-    const int rule = __shfl_sync(0xffffffffu, rule_i, __ffs(rem) - 1);
-    unsigned grp = __ballot_sync(0xffffffffu, rule_i == rule) & rem;
+    const int key = __shfl_sync(0xffffffffu, key_i, __ffs(rem) - 1);
+    unsigned grp = __ballot_sync(0xffffffffu, key_i == key) & rem;
     rem &= ~grp;
+    const int rule = key & 0xffff;
     const int ng = rule & 0xff, hr = rule >> 8;
     if (!DX && CLS != 0 && ng != 0) {
       const int qb = hr >= 4 ? 58 : 56;
-      for (; grp; grp &= grp - 1) {
-        const int e = __ffs(grp) - 1;
-        const double v = __shfl_sync(0xffffffffu, vi, e);
-        const double x = __shfl_sync(0xffffffffu, xi, e);
-        const double beta = __shfl_sync(0xffffffffu, beta_i, e);
-        const double gk = __shfl_sync(0xffffffffu, gk_i, e);
-        double mm = 0.0;
-        uint64_t q = 0;
-        if constexpr (CLS == 1 || CLS == 2) {
-          q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
-        } else if constexpr (CLS == 3) {
-          q = kint_sumq_g24h40(v, x, beta, gk, lane, mm, ks);
-        } else if constexpr (CLS == 4 || CLS == 5) {
-          q = kint_sumq_fixed(v, x, beta, gk, ng, hr, lane, mm, ks);
-        } else if constexpr (CLS < 0) {
-          if (hr >= 4) q = kint_sum_one(v, x, beta, gk, hr, lane, mm, ks);
-          else if (ng == 24) q = kint_sumq_g24h40(v, x, beta, gk, lane, mm, ks);
-          else q = kint_sumq_fixed(v, x, beta, gk, ng, hr, lane, mm, ks);
-        }
-        if (lane == e) {
-          m_i = mm;
-          q_i = q;
-          qb_i = qb;
-        }
-      }
+      if ((grp >> lane) & 1u) qb_i = qb;
+      if ((key >> 16) == 0)
+        kint_q_group<true, CLS>(grp, ng, hr, lane, vmq_i, gkq_i, vm_i, gk_i, tx_i, beta_i, m_i, mq_i, q_i, ks);
+      else
+        kint_q_group<false, CLS>(grp, ng, hr, lane, vmq_i, gkq_i, vm_i, gk_i, tx_i, beta_i, m_i, mq_i, q_i, ks);
       continue;
     }
     for (; grp; grp &= grp - 1) {
@@ -560,7 +697,10 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     }
   }
   if (DX) return -(vi / xi + 1.0) + (2.0 * vi - 1.0) * (s1_i / s0_i);
-  if (qb_i) s0_i = __ull2double_rn(q_i) * (qb_i == 58 ? 0x1p-58 : 0x1p-56);   // exact scalings
+  if (qb_i) {
+    s0_i = __ull2double_rn(q_i) * (qb_i == 58 ? 0x1p-58 : 0x1p-56);   // exact scalings
+    if (fx_i) m_i = __ll2double_rn(mq_i) * 0x1p-53;
+  }
   const double pre = ks ? ks->pre - fma(vi, ix_log(2.0 * xi), xi) : kint_prefactor(vi, xi);
   return pre + m_i + ix_log(s0_i);
 }

@@ -20,6 +20,18 @@ extern "C" void ix_rsqrt_arr(const double* y, double* o, long n) { for (long i =
 extern "C" void ix_exp_q58_arr(const double* y, unsigned long long* o, long n) {
   for (long i = 0; i < n; ++i) o[i] = lb::ix_exp_q58(y[i]);
 }
+extern "C" void ix_log_q53_arr(const double* z, long long* o, long n) {
+  for (long i = 0; i < n; ++i) o[i] = lb::ix_log_q53(z[i]);
+}
+extern "C" void ix_exp_q58_fx_arr(const long long* d, unsigned long long* o, long n) {
+  for (long i = 0; i < n; ++i) o[i] = lb::ix_exp_q58_fx(d[i]);
+}
+extern "C" void ix_fix_arr(const double* d, int q, long long* o, long n) {
+  for (long i = 0; i < n; ++i) o[i] = lb::ix_fix(d[i], q);
+}
+extern "C" void ix_mul_q58_arr(const long long* a, const long long* b, long long* o, long n) {
+  for (long i = 0; i < n; ++i) o[i] = lb::ix_mul_q58(a[i], b[i]);
+}
 '''
 _lib = None
 
@@ -67,3 +79,40 @@ def ix_rcp(a):
 
 def ix_rsqrt(a):
     return _run("ix_rsqrt_arr", a)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def ix_log_q53(z):
+    """log z in Q53 (int64)."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    o = np.empty(z.size, dtype=np.int64)
+    lib().ix_log_q53_arr(_ptr(z), _ptr(o), ctypes.c_long(z.size))
+    return o
+
+
+def ix_exp_q58_fx(d):
+    """e^(d 2^-53) in Q58 (uint64) for d <= 0 in Q53 (int64)."""
+    d = np.ascontiguousarray(d, dtype=np.int64)
+    o = np.empty(d.size, dtype=np.uint64)
+    lib().ix_exp_q58_fx_arr(_ptr(d), _ptr(o), ctypes.c_long(d.size))
+    return o
+
+
+def ix_fix(d, q):
+    """round(d 2^q) as int64."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    o = np.empty(d.size, dtype=np.int64)
+    lib().ix_fix_arr(_ptr(d), ctypes.c_int(q), _ptr(o), ctypes.c_long(d.size))
+    return o
+
+
+def ix_mul_q58(a, b):
+    """round(a b 2^-58) for int64 a (Q58) and b (Q53)."""
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    b = np.ascontiguousarray(b, dtype=np.int64)
+    o = np.empty(a.size, dtype=np.int64)
+    lib().ix_mul_q58_arr(_ptr(a), _ptr(b), _ptr(o), ctypes.c_long(a.size))
+    return o

@@ -6,7 +6,7 @@ import pytest
 import oracle
 from fractions import Fraction
 
-from intmath_host import ix_exp, ix_exp_q58, ix_log, ix_rcp, ix_rsqrt
+from intmath_host import ix_exp, ix_exp_q58, ix_exp_q58_fx, ix_fix, ix_log, ix_log_q53, ix_mul_q58, ix_rcp, ix_rsqrt
 
 
 def _ref(fn, a):
@@ -159,3 +159,71 @@ def test_rcp_rsqrt_special():
     assert odd[0] == np.inf and odd[1] == -0.5 and odd[2] == 0.0 and odd[4] == 2.0 ** -1023
     r = ix_rsqrt(np.array([0.0, -1.0, np.inf]))
     assert r[0] == np.inf and np.isnan(r[1]) and r[2] == 0.0
+
+
+# --- fixed-point forms of the K-integral node chain ---------------------------
+
+Q53 = Fraction(2) ** 53
+
+
+def test_log_q53():
+    """log z in Q53: within 0.56 units of 2^-53 of the exact logarithm (the
+    polynomial stops at r^5: r^6/6 reaches 0.05 units in the first interval)
+    (50-digit reference: near |log z| = 709 a unit of 2^-53 is 1.6e-19 of
+    the value, finer than the double-double log resolves), over the whole normal range and at the
+    reduction's interval edges; non-positive, subnormal and non-finite z give
+    -2^62."""
+    rng = np.random.default_rng(21)
+    z = np.concatenate([np.exp(rng.uniform(-700, 700, 3000)), rng.uniform(1e-3, 200.0, 3000),
+                        1.0 + np.arange(512) / 512.0, 1.0 + (np.arange(512) + 1) / 512.0 - 2.0 ** -52,
+                        1.0 + np.arange(1, 50) * 2.0 ** -52, 2.0 - np.arange(1, 50) * 2.0 ** -52,
+                        2.0 ** np.arange(-1022, 1023, 7), [2.2250738585072014e-308, 1.7976931348623157e308]])
+    got = ix_log_q53(z)
+    mp = pytest.importorskip("mpmath")
+    with mp.workdps(50):
+        for zi, g in zip(z, got):
+            err = abs(mp.mpf(int(g)) - mp.log(mp.mpf(float(zi))) * 2 ** 53)
+            assert err <= 0.56, (zi, int(g), float(err))
+    odd = ix_log_q53(np.array([0.0, -1.0, 5e-324, np.inf, np.nan]))
+    assert (odd == -(2 ** 62)).all()
+
+
+def test_exp_q58_fx():
+    """e^(d 2^-53) in Q58 from d in Q53: within 0.6 units of 2^-58 of the
+    exact value; d chosen so that d 2^-53 is a double (the reference's
+    argument), over [-42, 0] and at the reduction boundaries."""
+    rng = np.random.default_rng(22)
+    small = -rng.integers(0, 2 ** 53, 3000, dtype=np.int64)                       # |y| < 1, any bits
+    big = -(rng.integers(0, 42 * 2 ** 47, 3000, dtype=np.int64) << 6)              # |y| < 42, 53 bits
+    edges = np.array([-int(Fraction(np.log(2.0) / 512) * (k + Fraction(1, 2)) * Q53) // 64 * 64 for k in range(0, 800)],
+                     dtype=np.int64)
+    d = np.concatenate([small, big, edges, np.array([0, -1, -2 ** 40, -(41 * 2 ** 53)], dtype=np.int64)])
+    got = ix_exp_q58_fx(d)
+    scale = Fraction(2) ** 58
+    for di, g in zip(d, got):
+        y = Fraction(int(di)) / Q53
+        assert Fraction(float(y)) == y
+        hi, lo = oracle.dd_exp(float(y))
+        exact = (Fraction(hi) + Fraction(lo)) * scale
+        assert abs(Fraction(int(g)) - exact) <= Fraction(6, 10), (int(di), int(g), float(exact))
+    assert int(ix_exp_q58_fx(np.array([0], dtype=np.int64))[0]) == 2 ** 58
+    assert (ix_exp_q58_fx(np.array([-(42 * 2 ** 53), -(2 ** 62)], dtype=np.int64)) == 0).all()
+
+
+def test_fix_and_mul_q58():
+    """round(d 2^q) from the bit fields, and the Q58 x Q53 product, against
+    exact rationals."""
+    rng = np.random.default_rng(23)
+    d = np.concatenate([rng.uniform(-16, 16, 2000), np.exp(rng.uniform(-60, 2.7, 1000)) * rng.choice([-1.0, 1.0], 1000),
+                        [0.0, -0.0, 5e-324, 0.5, -0.5, 15.999999999999998, 2.0 ** -59, 3 * 2.0 ** -60]])
+    for q in (53, 58):
+        got = ix_fix(d, q)
+        for di, g in zip(d, got):
+            exact = Fraction(float(di)) * Fraction(2) ** q
+            assert abs(Fraction(int(g)) - exact) <= Fraction(1, 2), (di, q, int(g))
+    a = ix_fix(rng.uniform(-0.5, 16.0, 3000), 58)
+    b = ix_fix(rng.uniform(-60.0, 60.0, 3000), 53)             # |a b| < 2^10
+    got = ix_mul_q58(a, b)
+    for ai, bi, g in zip(a, b, got):
+        exact = Fraction(int(ai)) * Fraction(int(bi)) / Fraction(2) ** 58
+        assert abs(Fraction(int(g)) - exact) <= Fraction(1, 2), (int(ai), int(bi), int(g))

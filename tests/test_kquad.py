@@ -35,58 +35,79 @@ def _tables():
         vals = [float(t) for t in m.group(3).replace("\n", " ").split(",") if t.strip()]
         assert len(vals) == int(m.group(2)), m.group(1)
         out[m.group(1)] = vals
+    for m in re.finditer(r"static __device__ const long long (\w+)\[(\d+)\] = \{([^}]*)\};", txt):
+        vals = [int(t.strip()[:-2]) for t in m.group(3).replace("\n", " ").split(",") if t.strip()]
+        assert len(vals) == int(m.group(2)), m.group(1)
+        out[m.group(1)] = vals
     for m in re.finditer(r"#define (LB_KQ_\w+) (\S+)", txt):
-        out[m.group(1)] = float(m.group(2))
+        out[m.group(1)] = int(m.group(2)[:-2]) if m.group(2).endswith("ll") else float(m.group(2))
     return out
 
 
 T = _tables()
 
 
-def _g_fixed(v, x, N):
+def _tab(name, q):
+    """A table of log terms: the double entries, or (q) the Q53 ones that
+    the values' fixed-point node sums use, as exact rationals."""
+    if q:
+        return [mp.mpf(t) / mp.mpf(2) ** 53 for t in T[name + "_q"]]
+    return T[name]
+
+
+def _g_fixed(v, x, N, q=False):
     """beta sum_j e^{c_j + (v-1/2) log(2x + u_j^beta) - u_j^beta} (s = u^beta on [0, 1])."""
     beta = mp.mpf(16) / (2 * v + 1)
     tot = mp.mpf(0)
-    for lu, c in zip(T["lb_kq_g%d_logu" % N], T["lb_kq_g%d_c" % N]):
+    for lu, c in zip(T["lb_kq_g%d_logu" % N], _tab("lb_kq_g%d_c" % N, q)):
         ub = mp.exp(beta * lu)
         tot += mp.exp(c + (v - mp.mpf(0.5)) * mp.log(2 * x + ub) - ub)
     return beta * tot
 
 
-def _h(v, x, tag):
+def _h(v, x, tag, q=False):
     """sum_j e^{c_j + (v-1/2)(y_j + log(s_j + 2x))} for the h table `tag`."""
     tot = mp.mpf(0)
-    for s, y, c in zip(T["lb_kq_%s_s" % tag], T["lb_kq_%s_y" % tag], T["lb_kq_%s_c" % tag]):
+    for s, y, c in zip(T["lb_kq_%s_s" % tag], _tab("lb_kq_%s_y" % tag, q), _tab("lb_kq_%s_c" % tag, q)):
         tot += mp.exp(c + (v - mp.mpf(0.5)) * (y + mp.log(s + 2 * x)))
     return tot
 
 
-def _g_one(v, x, N, ls0):
+def _g_one(v, x, N, ls0, q=False):
     """The [0, s0] part of a one-slot rule: s_j = e^{beta log u_j + log s0}."""
     beta = mp.mpf(16) / (2 * v + 1)
     tot = mp.mpf(0)
-    for lu, c in zip(T["lb_kq_g%d_logu" % N], T["lb_kq_g%d_c" % N]):
+    for lu, c in zip(T["lb_kq_g%d_logu" % N], _tab("lb_kq_g%d_c" % N, q)):
         s = mp.exp(beta * lu + ls0)
         tot += mp.exp(c + (v + mp.mpf(0.5)) * ls0 + (v - mp.mpf(0.5)) * mp.log(2 * x + s) - s)
     return beta * tot
 
 
+def _ls0(name, q):
+    return mp.mpf(T[name + "_Q53"]) / mp.mpf(2) ** 53 if q else mp.mpf(T[name])
+
+
 RULES = {
     # name: (sum of the rule, the orders and arguments it serves)
-    "g32+hl32": (lambda v, x: _g_fixed(v, x, 32) + _h(v, x, "hl32"), [0.9, 0.97, 1.0, 1.2], [0.25, 1.0, 7.3, 25.0, 30.0]),
-    "g64+hl32": (lambda v, x: _g_fixed(v, x, 64) + _h(v, x, "hl32"), [0.4, 0.55, 0.89], [1e-3, 0.01, 0.2]),
-    "g24+hl40": (lambda v, x: _g_fixed(v, x, 24) + _h(v, x, "hl40"), [1.21, 1.5, 1.99, 3.3, 5.0], [1e-300, 1e-6, 0.04, 1.0, 9.0, 25.0]),
-    "g32+hq32": (lambda v, x: _g_fixed(v, x, 32) + _h(v, x, "hq32"), [5.01, 8.5, 16.0], [1e-300, 0.01, 1.0, 12.0, 25.0]),
-    "one, s0 = 8": (lambda v, x: _g_one(v, x, 22, mp.mpf(T["LB_KQ_LOG8"])) + _h(v, x, "hq10o8"),
+    "g32+hl32": (lambda v, x, q: _g_fixed(v, x, 32, q) + _h(v, x, "hl32", q), [0.9, 0.97, 1.0, 1.2],
+                 [0.25, 1.0, 7.3, 25.0, 30.0]),
+    "g64+hl32": (lambda v, x, q: _g_fixed(v, x, 64, q) + _h(v, x, "hl32", q), [0.4, 0.55, 0.89], [1e-3, 0.01, 0.2]),
+    "g24+hl40": (lambda v, x, q: _g_fixed(v, x, 24, q) + _h(v, x, "hl40", q), [1.21, 1.5, 1.99, 3.3, 5.0],
+                 [1e-300, 1e-6, 0.04, 1.0, 9.0, 25.0]),
+    "g32+hq32": (lambda v, x, q: _g_fixed(v, x, 32, q) + _h(v, x, "hq32", q), [5.01, 8.5, 16.0],
+                 [1e-300, 0.01, 1.0, 12.0, 25.0]),
+    "one, s0 = 8": (lambda v, x, q: _g_one(v, x, 22, _ls0("LB_KQ_LOG8", q), q) + _h(v, x, "hq10o8", q),
                     [2.0, 2.37, 3.9, 5.5, 6.99], [1e-300, 1e-8, 0.0128, 0.3, 1.0, 4.7, 13.0, 25.0, 30.0]),
-    "one, s0 = 3": (lambda v, x: _g_one(v, x, 12, mp.mpf(T["LB_KQ_LOG3"])) + _h(v, x, "hq20o3"),
+    "one, s0 = 3": (lambda v, x, q: _g_one(v, x, 12, _ls0("LB_KQ_LOG3", q), q) + _h(v, x, "hq20o3", q),
                     [7.0, 7.9, 9.3, 12.71, 16.0, 16.5], [1e-300, 1e-8, 0.0128, 0.3, 1.0, 4.7, 13.0, 25.0, 30.0]),
 }
 
 
+@pytest.mark.parametrize("q", [False, True], ids=["double tables", "Q53 tables"])
 @pytest.mark.parametrize("name", list(RULES))
-def test_rule_error_map(name):
-    fn, vs, xs = RULES[name]
+def test_rule_error_map(name, q):
+    fn0, vs, xs = RULES[name]
+    fn = lambda v, x: fn0(v, x, q)
     V, X = np.meshgrid(np.array(vs), np.array(xs), indexing="ij")
     V, X = V.ravel(), X.ravel()
     hi, lo = oracle.log_k(V, X, want_lo=True)
@@ -101,6 +122,22 @@ def test_rule_error_map(name):
             worst = max(worst, err)
             assert err < (5e-17 if name.startswith("one") else 2e-16), (name, v, x, err)
     assert worst > 0.0
+
+
+def test_q53_tables():
+    """Every Q53 table (the log terms of the values' fixed-point node sums)
+    and the Q53 split-point logarithms hold the same 40-digit values as their
+    double twins: within half a unit of 2^-53 plus half an ulp of the double."""
+    names = [k[:-2] for k in T if k.endswith("_q")]
+    assert len(names) == 17
+    with mp.workdps(40):
+        for n in names:
+            for d, qv in zip(T[n], T[n + "_q"]):
+                err = abs(mp.mpf(qv) / mp.mpf(2) ** 53 - mp.mpf(d))
+                assert err <= mp.mpf(2) ** -54 + mp.mpf(np.spacing(abs(d))) / 2, n
+        for n in ("LB_KQ_LOG8", "LB_KQ_LOG3"):
+            err = abs(mp.mpf(T[n + "_Q53"]) / mp.mpf(2) ** 53 - mp.mpf(T[n]))
+            assert err <= mp.mpf(2) ** -54 + mp.mpf(np.spacing(T[n])) / 2, n
 
 
 def test_one_slot_tables():
