@@ -32,7 +32,7 @@ METRIC = "Gevals/s (log I_v and log K_v, FP64)"
 # capture of every launch of one full-size step (the launch list of
 # profiles/launches_paper_sweep_fp64.md, with dram__bytes_read.sum and
 # dram__bytes_write.sum); empty when the kernels changed since.
-NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.418e9, 27), "lb_kint_kernel": (8.564e9, 90)}
+NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.417e9, 27), "lb_kint_kernel": (9.431e9, 90)}
 # Pipe utilisation of each kernel from ncu --set full on a small case of the
 # same workload (profiles/lb_tiles_kernel_sweep_small.md,
 # profiles/lb_kint_kernel_sweep_small.md, profiles/fp32_mixed_sweep_small.md):
@@ -42,9 +42,9 @@ NCU_DRAM_BYTES_PER_STEP = {"lb_tiles_kernel": (17.418e9, 27), "lb_kint_kernel": 
 NCU_PIPES = {
     "lb_tiles_kernel": {"fp64": 0.618, "alu": 0.460, "fma": 0.300, "xu": 0.025, "issue_active": 0.675,
                         "launch": "log I, mixed orders, 11M pairs"},
-    "lb_kint_kernel": {"fp64": 0.646, "alu": 0.648, "fma": 0.185, "xu": 0.017, "issue_active": 0.671,
-                       "launch": "one-slot class kernel of a mixed-order log K call (class 4: fp64 0.486, "
-                                 "alu 0.638, issue 0.632)"},
+    "lb_kint_kernel": {"fp64": 0.355, "alu": 0.635, "fma": 0.193, "xu": 0.015, "issue_active": 0.662,
+                       "launch": "one-slot class kernel of a mixed-order log K call (class 4: fp64 0.257, "
+                                 "alu 0.611, issue 0.634); FMA-heavy pipe (integer multiplies) 0.48"},
 }
 NCU_PIPES_FP32 = {
     "lb_tiles_kernel": {"fp64": 0.0, "alu": 0.450, "fma": 0.235, "xu": 0.111, "issue_active": 0.760,
