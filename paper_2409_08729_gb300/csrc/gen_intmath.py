@@ -13,9 +13,9 @@ in 64- and 128-bit integers instead of doubles:
   Horner coefficients of e^r - 1 and log(1 + r) in Q31 (inner steps, done
   with 32-bit multiplies) and Q62.
   Fixed-point forms for sums of exponentials of logarithms (the K-integral
-       nodes, ix_log_q53 and ix_exp_q58_fx): -log(C_j / 2^13) in Q63; ln 2
-       as A 2^-31 + B 2^-63 + C 2^-95 (A, B, C integers below 2^32); ln2/512
-       as (H + M 2^-32) 2^-64.
+       nodes, ix_log_q53 and ix_exp_q58_fx): -log(C_j / 2^13) in Q62; ln 2
+       as A 2^-30 + B 2^-62 + C 2^-94 (A, B, C integers below 2^32); ln2/512
+       as (H + M 2^-32) 2^-64; the log's coefficients 1/3..1/5 in Q30.
   rcp and rsqrt reuse the log's C_j (m C_j / 2^13 = 1 + r): 1/m =
        (C_j / 2^13) / (1 + r), m^-1/2 = sqrt(C_j / 2^13) (1 + r)^-1/2, with
        sqrt(C_j / 2^13) in Q63 and the binomial coefficients of
@@ -72,20 +72,15 @@ def main():
     L.append(arr("uint16_t", "lb_ix_log_c", c, lambda v: "%d" % v))
     L.append(arr("int64_t", "lb_ix_log_thi", th, lambda v: "%dll" % v))
     L.append(arr("uint64_t", "lb_ix_log_tlo", tl, u64))
-    t63 = [0 if j == 0 else q(-mp.log(mp.mpf(cj) / 2 ** 13), 63) for j, cj in enumerate(c)]
-    assert all(abs(v) < 1 << 63 for v in t63) and t63[511] == q(mp.log(2), 63)
-    L.append(arr("int64_t", "lb_ix_log_t63", t63, lambda v: "%dll" % v))
+    t62 = [0 if j == 0 else q(-mp.log(mp.mpf(cj) / 2 ** 13), 62) for j, cj in enumerate(c)]
+    assert all(abs(v) < 1 << 62 for v in t62) and t62[511] == q(mp.log(2), 62)
+    L.append(arr("int64_t", "lb_ix_log_t62", t62, lambda v: "%dll" % v))
     hi, lo = split128(q(mp.log(2) / 512, 116))
     L.append("#define LB_IX_L512_HI %dull" % hi)
     L.append("#define LB_IX_L512_LO 0x%016xull" % lo)
     hi, lo = split128(ln2)
     L.append("#define LB_IX_LN2_HI %dull" % hi)
     L.append("#define LB_IX_LN2_LO 0x%016xull" % lo)
-    l95 = q(mp.log(2), 95)
-    assert l95 >> 64 < 1 << 31
-    L.append("#define LB_IX_LN2_A %dll" % (l95 >> 64))
-    L.append("#define LB_IX_LN2_B %dll" % ((l95 >> 32) & 0xffffffff))
-    L.append("#define LB_IX_LN2_C %dll" % (l95 & 0xffffffff))
     l96 = q(mp.log(2) / 512, 96)
     L.append("#define LB_IX_L512_H %dull" % (l96 >> 32))
     L.append("#define LB_IX_L512_M %dull" % (l96 & 0xffffffff))
@@ -101,8 +96,15 @@ def main():
         L.append("#define LB_IX_L%d %d" % (k, q(mp.mpf(1) / k, 31)))
     for k in (1, 2, 3):
         L.append("#define LB_IX_L%d %dll" % (k, q(mp.mpf(1) / k, 62)))
-    # the Q53 log (ix_log_q53) stops at r^5 and takes 1/3 in Q31 too
-    L.append("#define LB_IX_L3S %d" % q(mp.mpf(1) / 3, 31))
+    # the Q53 log (ix_log_q53) takes r in Q64 and stops at r^5: 1/3, 1/4 and
+    # 1/5 in Q30, -log(C_j / 2^13) in Q62, ln 2 as A 2^-30 + B 2^-62 + C 2^-94
+    for k in (3, 4, 5):
+        L.append("#define LB_IX_LQ%d %d" % (k, q(mp.mpf(1) / k, 30)))
+    l94 = q(mp.log(2), 94)
+    assert l94 >> 64 < 1 << 30
+    L.append("#define LB_IX_LN2Q_A %dll" % (l94 >> 64))
+    L.append("#define LB_IX_LN2Q_B %dll" % ((l94 >> 32) & 0xffffffff))
+    L.append("#define LB_IX_LN2Q_C %dll" % (l94 & 0xffffffff))
     # rsqrt: sqrt(C_j / 2^13) in Q63 (at most 2^63, for j = 0)
     rsq = [q(mp.sqrt(mp.mpf(cj) / 2 ** 13), 63) for cj in c]
     assert all(v <= 1 << 63 for v in rsq)

@@ -308,12 +308,13 @@ LB_IX_FN int64_t ix_mul_q58(int64_t a, int64_t b) {
 }
 
 // log z in Q53 for positive normal z (the reduction of ix_log; the sum
-// -log(C_j / 2^13) + log(1 + r) in Q63 and e ln2 from its 95-bit form):
+// -log(C_j / 2^13) + log(1 + r) in Q62 and e ln2 from its 94-bit form):
 // within 0.56 units of 2^-53.  For this precision log(1 + r) stops at r^5
 // (r^6/6 below 2^-61.4, and below 2^-56.6 in the first interval, j = 0,
 // where r reaches 2^-9), and a step's error enters times r^k after k more
-// steps, so 1/4 - r/5 and 1/3 - r(...) run in 32 bits (Q31),
-// 1/2 - r(...) as a 64 x 32-bit product and only the last two in 64 bits.
+// steps, so 1/4 - r/5 and 1/3 - r(...) run in 32 bits (Q30), 1/2 - r(...)
+// as a 64 x 32-bit product and only the last two in 64 bits.  With r in
+// Q64 every product lands in its sum's format without a shift.
 // Zero, negative, subnormal, infinite and NaN z give -2^62 (a term that
 // vanishes); the callers pass positive normal z.
 LB_IX_FN int64_t ix_log_q53(double z) {
@@ -323,17 +324,18 @@ LB_IX_FN int64_t ix_log_q53(double z) {
   const int e = (int)(hi >> 20) - 1023;
   const uint64_t F = b & 0x000fffffffffffffull;
   const int j = (int)(F >> 43);
-  const int64_t r = (int64_t)((F | 0x0010000000000000ull) * (uint64_t)LB_IX_LOAD(lb_ix_log_c + j));   // Q65
-  const int32_t r32 = (int32_t)(r >> 32);                   // Q33
-  int32_t a3 = LB_IX_L4 - (ix_mulhi32(LB_IX_L5, r32) >> 1);
-  a3 = LB_IX_L3S - (ix_mulhi32(a3, r32) >> 1);
-  int64_t a = LB_IX_L2 - (ix_mul64x32hi(r, a3) >> 2);
-  a = LB_IX_L1 - (ix_mulhi(a, r) >> 1);
-  // log(1 + r) = a r (Q62 x Q65 / 2^64 = Q63) plus -log(C_j / 2^13): |f| < 0.7
-  const int64_t f = ix_mulhi(a, r) + (int64_t)LB_IX_LOAD(lb_ix_log_t63 + j);
-  // e ln2 = e (A 2^-31 + B 2^-63 + C 2^-95): the last two parts with f in Q63
-  const int64_t lo63 = (int64_t)e * LB_IX_LN2_B + (((int64_t)e * LB_IX_LN2_C) >> 32) + f;
-  return (int64_t)((uint64_t)((int64_t)e * LB_IX_LN2_A) << 22) + ((lo63 + (1ll << 9)) >> 10);
+  // r = m C_j / 2^13 - 1: the low 64 bits of M C_j are 2^65 r; r in Q64
+  const int64_t r = (int64_t)((F | 0x0010000000000000ull) * (uint64_t)LB_IX_LOAD(lb_ix_log_c + j)) >> 1;
+  const int32_t r32 = (int32_t)(r >> 32);                   // Q32
+  int32_t a3 = LB_IX_LQ4 - ix_mulhi32(LB_IX_LQ5, r32);      // Q30
+  a3 = LB_IX_LQ3 - ix_mulhi32(a3, r32);
+  int64_t a = LB_IX_L2 - ix_mul64x32hi(r, a3);              // Q62
+  a = LB_IX_L1 - ix_mulhi(a, r);
+  // log(1 + r) = a r plus -log(C_j / 2^13), Q62: |f| < 0.7
+  const int64_t f = ix_mulhi(a, r) + (int64_t)LB_IX_LOAD(lb_ix_log_t62 + j);
+  // e ln2 = e (A 2^-30 + B 2^-62 + C 2^-94): the last two parts with f in Q62
+  const int64_t lo62 = (int64_t)e * LB_IX_LN2Q_B + (((int64_t)e * LB_IX_LN2Q_C) >> 32) + f;
+  return (int64_t)((uint64_t)((int64_t)e * LB_IX_LN2Q_A) << 23) + ((lo62 + (1ll << 8)) >> 9);
 }
 
 // e^(d 2^-53) in unsigned Q58 (as ix_exp_q58) for d <= 0 in Q53; d <= -42
@@ -345,8 +347,9 @@ LB_IX_FN uint64_t ix_exp_q58_fx(int64_t d) {
   // k ~ rint(|y| 512 / ln2) from a single-precision copy of |y| (in Q21)
   const float yf = (float)(int32_t)(ad >> 32);
   const uint32_t ak = ix_fbits(fmaf(yf, 738.65986f / 2097152.0f, 12582912.0f)) - 0x4B400000u;
-  const uint64_t r64 = (ad << 11) - (uint64_t)ak * LB_IX_L512_H - (((uint64_t)ak * LB_IX_L512_M) >> 32);
-  const int64_t r = -(int64_t)(r64 << 9);                   // y = -|y|: r in Q73
+  // y = -|y| = -k ln2/512 + r: r = k ln2/512 - |y|, in Q64 modulo 2^64, then Q73
+  const uint64_t r64 = (uint64_t)ak * LB_IX_L512_H + (((uint64_t)ak * LB_IX_L512_M) >> 32) - (ad << 11);
+  const int64_t r = (int64_t)(r64 << 9);
   const int k = -(int)ak;
   const int64_t res = ix_exp_finish(r, k);                  // e^y = res 2^(k div 512 - 62)
   const int sh = 4 - (k >> 9);                              // k div 512 <= 0
