@@ -197,6 +197,7 @@ def main():
     ap.add_argument("--ref-per-v", type=int, default=4000, help="oracle sample per order per reference step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-dx", action="store_true", help="skip the x-derivative sweep")
     ap.add_argument("--err-sample", type=int, default=4000, help="oracle-checked outputs per call type")
     ap.add_argument("--serve-requests", type=int, default=100_000,
                     help="requests in the serving measurement (0 = skip)")
@@ -406,6 +407,80 @@ def main():
             fp32["max_rel_err_mixed_calls"] = e_max
         del x32, v32, o32
 
+    # ---- the same sweep through the adjoint kernels (d/dx log I, d/dx log K,
+    # FP64), with sampled errors against the oracle's Bessel-ratio derivative ----
+    dx = None
+    if not args.no_dx:
+        odx = torch.empty((4, n_all), dtype=torch.float64, device=dev)
+
+        def step_dx():
+            for kind, fn in ((0, L.logbessel_i_dx), (1, L.logbessel_k_dx)):
+                o_per, o_mix = odx[2 * kind], odx[2 * kind + 1]
+                for k in range(nv):
+                    B.check(fn(B.LB_F64, orders[k:k + 1].data_ptr(), 0, x_all[k * n1:(k + 1) * n1].data_ptr(),
+                               o_per[k * n1:(k + 1) * n1].data_ptr(), n1, mode, sp))
+                B.check(fn(B.LB_F64, v_mixed.data_ptr(), 1, x_all.data_ptr(), o_mix.data_ptr(), n_all, mode, sp))
+
+        for _ in range(2):
+            step_dx()
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(args.steps):
+            step_dx()
+        d1.record(stream)
+        torch.cuda.synchronize()
+        msdx = max_over_ranks(d0.elapsed_time(d1), pg, dev)
+        dx = {"value": job_gevals(evals_per_step, args.steps, world, msdx), "unit": UNIT,
+              "ms_per_step": msdx / args.steps, "dtype": "f64",
+              "calls": "logbessel_i_dx, logbessel_k_dx: the sweep's per-order and mixed-order calls"}
+        if rank == 0 and args.err_sample > 0:
+            import oracle
+            errs = {}
+            for name, row, vv, kind in (("i_per_order", 0, vper, "i"), ("i_mixed", 1, vmix, "i"),
+                                        ("k_per_order", 2, vper, "k"), ("k_mixed", 3, vmix, "k")):
+                got = odx[row][idx].cpu().numpy()
+                ref = oracle.dlog_i_dx(vv, xs) if kind == "i" else oracle.dlog_k_dx(vv, xs)
+                errs[name] = float((np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)).max())
+            dx["max_rel_err"] = errs
+        del odx
+
+    # ---- vMF (paper Sec. 6.3): Newton fits of the concentration from the mean
+    # resultant length R = A_d(kappa) (the library's own mean ratio, so the fit
+    # must return kappa), and the throughput of log C_d and its derivative ----
+    vmf = None
+    if not args.no_dx:
+        from paper_2409_08729_gb300 import vmf as VM
+        fits = []
+        for d in (2048, 8192, 32768):
+            for kt in (d / 10.0, float(d), 10.0 * d):
+                R = float(VM.mean_ratio(d, torch.tensor([kt], dtype=torch.float64, device=dev)))
+                torch.cuda.synchronize()
+                tf = time.perf_counter()
+                res = VM.fit_kappa(d, R, device=str(dev))
+                fms = (time.perf_counter() - tf) * 1e3
+                fits.append({"d": d, "kappa_true": kt, "R": R, "kappa_hat": res["kappa"],
+                             "iterations": res["iterations"], "ms": fms,
+                             "rel_dev": abs(res["kappa"] / kt - 1.0)})
+        kap = torch.exp(torch.empty(n1, dtype=torch.float64, device=dev).uniform_(np.log(81.92), np.log(819200.0)))
+        ov = torch.empty_like(kap)
+        rates_vmf = {}
+        for name, deriv in (("log_c", 0), ("dlog_c", 1)):
+            for _ in range(2):
+                B.check(L.logbessel_vmf_log_c(B.LB_F64, 8192.0, kap.data_ptr(), ov.data_ptr(), n1, deriv, sp))
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for _ in range(args.steps):
+                B.check(L.logbessel_vmf_log_c(B.LB_F64, 8192.0, kap.data_ptr(), ov.data_ptr(), n1, deriv, sp))
+            v1.record(stream)
+            torch.cuda.synchronize()
+            rates_vmf[name + "_gevals"] = n1 * args.steps / (v0.elapsed_time(v1) * 1e-3) / 1e9
+        vmf = {"fits": fits, "max_rel_dev": max(f["rel_dev"] for f in fits),
+               "throughput": dict(rates_vmf, d=8192, n=n1, kappa="log-uniform [d/100, 100 d]")}
+        del kap, ov
+
     # ---- rooflines: algorithmic work of one step from the fixed operation
     # table (benchmarks/optable.py), per kernel, over the CUDA-event time of
     # the kernel's launches in the timed region ----
@@ -497,6 +572,8 @@ def main():
             "fp64_rates": {k: v / 1e9 for k, v in rates.items()}}
     line["max_rel_err"] = acc
     line["fp32_mixed"] = fp32
+    line["derivatives"] = dx
+    line["vmf"] = vmf
     del outs
     torch.cuda.empty_cache()
     if rank == 0 and args.robust_n > 0:

@@ -666,7 +666,7 @@ __device__ __forceinline__ double series_so(const ScalarOrder& so, double x, int
 template <int KIND, int K>
 __device__ __forceinline__ double mu_dx(double v, double x) {
   const double mu = 4.0 * v * v;
-  const double inv8x = 1.0 / (8.0 * x);
+  const double inv8x = ix_rcp(8.0 * x);             // the reciprocals on the integer pipe
   double term = 1.0, S = 1.0, D = 0.0;
 #pragma unroll
   for (int k = 1; k <= K; ++k) {
@@ -677,9 +677,29 @@ __device__ __forceinline__ double mu_dx(double v, double x) {
     S += term;
     D = fma((double)k, term, D);
   }
-  const double inv_x = 1.0 / x;
+  const double inv_x = 8.0 * inv8x;                 // exact scaling
   const double base = (KIND == KIND_I) ? 1.0 : -1.0;
-  return base - inv_x * (0.5 + D / S);
+  return base - inv_x * fma(D, ix_rcp(S), 0.5);
+}
+
+// The same for the first n terms only (n: the pair's term count, made
+// warp-uniform), as a rolled loop: the terms past n are below 2^-56 of S.
+template <int KIND, int K>
+__device__ __forceinline__ double mu_dx_n(double v, double x, int n) {
+  n = __reduce_max_sync(0xffffffffu, n);
+  const double mu = 4.0 * v * v;
+  const double rx = ix_rcp(8.0 * x);                // on the integer pipe
+  const double inv8x = (KIND == KIND_I) ? -rx : rx;  // the sign folded in
+  double term = 1.0, S = 1.0, D = 0.0, kd = 0.0;
+#pragma unroll 1
+  for (int k = 1; k <= n; ++k) {
+    kd += 1.0;
+    term *= fma(mu, kMuInvK[k], -kMuOddK[k]) * inv8x;
+    S += term;
+    D = fma(kd, term, D);
+  }
+  const double base = (KIND == KIND_I) ? 1.0 : -1.0;
+  return base - (8.0 * rx) * fma(D, ix_rcp(S), 0.5);
 }
 
 // U_K: with x' = x/v, t = (1 + x'^2)^-1/2, d(v eta)/dx = 1/(t x'),
@@ -689,13 +709,19 @@ __device__ __forceinline__ double mu_dx(double v, double x) {
 //   S = 1 + sum q^k P_k(t^2), SQ = sum q^k Q_k(t^2), q = +-t/v.
 template <int KIND, int K>
 __device__ __forceinline__ double u_dx(double v, double x) {
-  const double xp = x / v;
-  double r;
-  if (xp < 1e150) r = sqrt(fma(xp, xp, 1.0));
-  else r = xp;
-  const double t = 1.0 / r;
+  const double inv_v = ix_rcp(v);                  // reciprocals and 1/sqrt on the integer pipe
+  const double xp = x * inv_v;
+  double r, t;
+  if (xp < 1e150) {
+    const double w = fma(xp, xp, 1.0);
+    t = ix_rsqrt(w);
+    r = w * t;
+  } else {
+    r = xp;
+    t = ix_rcp(xp);
+  }
   const double p = t * t;
-  double q = t / v;
+  double q = t * inv_v;
   if (KIND == KIND_K) q = -q;
   double accP = debye_P(K, p), accQ = debye_Q(K, p);
 #pragma unroll
@@ -705,26 +731,46 @@ __device__ __forceinline__ double u_dx(double v, double x) {
   }
   const double S = fma(accP, q, 1.0);
   const double SQ = accQ * q;
-  const double lead = r / xp;                       // 1/(t x') = sqrt(1 + x'^2)/x'
-  const double corr = (xp * p / v) * (0.5 + SQ / S);
+  const double lead = r * ix_rcp(xp);               // 1/(t x') = sqrt(1 + x'^2)/x'
+  const double corr = (xp * p * inv_v) * fma(SQ, ix_rcp(S), 0.5);
   return (KIND == KIND_I) ? lead - corr : -lead - corr;
 }
 
 // Series: log I = v log(x/2) - lgamma(v+1) + log(1 + T), T = sum_{k>=1} a_k/a_0
 // with a_k/a_0 proportional to x^(2k):  d/dx log I = v/x + (2/x) (sum k a_k/a_0) / (1 + T).
-__device__ __forceinline__ double series_dx(double v, double x) {
+// With the pair's term count (series_terms): T and D = sum k a_k/a_0 by one
+// backward Horner pass, P <- 1 + r_k P and E <- r_k (P + E) (E collects
+// y dP/dy = D, as r_k is proportional to y), r_k = y / (k (k + v)); the
+// terms past the head in double-float (as series_log_i_n), the head as one
+// fraction P = A/B, E = C/B with A <- d B + y A, C <- y (A + C), B <- d B
+// (d = k (k + v)), so no term divides; D/(1+T) = C/A.
+__device__ __forceinline__ double series_dx_n(double v, double x, int packed) {
+  const int n = __reduce_max_sync(0xffffffffu, series_count(packed));
+  const int h = __reduce_max_sync(0xffffffffu, series_head(packed));
   const double y = 0.25 * x * x;
-  const double kpk = 0.5 * (sqrt(fma(x, x, v * v)) - v);
-  double term = 1.0, T = 0.0, D = 0.0;
-  double k = 1.0;
-  for (int it = 0; it < 400; ++it) {
-    term *= y / (k * (k + v));
-    T += term;
-    D = fma(k, term, D);
-    if (k > kpk && term <= 1.3877787807814457e-17 * (1.0 + T)) break;
-    k += 1.0;
+  double A = 1.0, C = 0.0, B = 1.0;
+  int top = n;
+  if (n > h) {
+    const dfloat yd = df_from_double(y), vd = df_from_double(v);
+    dfloat Pd = df_make(1.0f, 0.0f), Ed = df_make(0.0f, 0.0f);
+#pragma unroll 1
+    for (int k = n; k > h; --k) {
+      const dfloat r = series_ratio_df(yd, vd, k);
+      Ed = df_mul(r, df_add(Pd, Ed));
+      Pd = df_mul_add(r, Pd, df_make(1.0f, 0.0f));
+    }
+    A = df_to_double(Pd);
+    C = df_to_double(Ed);
+    top = h;
   }
-  return (v + 2.0 * D / (1.0 + T)) / x;
+#pragma unroll 1
+  for (int k = top; k >= 1; --k) {
+    const double d = fma(kSeriesK[k], v, kSeriesK2[k]);   // k (k + v)
+    C = y * (A + C);
+    A = fma(d, B, y * A);
+    B *= d;
+  }
+  return fma(2.0 * C, ix_rcp(A), v) * ix_rcp(x);
 }
 
 }  // namespace lb

@@ -130,7 +130,8 @@ __device__ __forceinline__ void kint_scalar_setup(KintScalar& ks, double v) {
 // lanes of the warp: returns on every lane its part of the shifted sums
 // s0 = sum_j e^{L_j - mm} and s1 = sum_j e^{L_j - mm} / (s_j + 2x) (DX), with
 // the common shift mm (the warp maximum of L, taken on the integer pipe).
-// The node exps and logs run on the integer pipes (lb_intmath.cuh); log beta,
+// The node exps, logs and the derivative's reciprocals 1/(s + 2x) run on the
+// integer pipes (lb_intmath.cuh); log beta,
 // common to the g nodes, multiplies their partial sums instead of entering
 // every node (any shift is exact, and beta <= 16 cannot overflow them).
 template <bool DX>
@@ -154,7 +155,7 @@ __device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta,
       const int j = lane + 32 * k;
       const double ub = ks ? (ng == 32 ? ks->ub32[j] : ks->ub64[j]) : ix_exp(beta * __ldg(gu + j));
       L[k] = fma(vm, ix_log(tx + ub), __ldg(gc + j)) - ub;
-      if (DX) A[k] = 1.0 / (tx + ub);
+      if (DX) A[k] = ix_rcp(tx + ub);
       key = max(key, order_key(L[k]));
     }
   }
@@ -166,7 +167,7 @@ __device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta,
     if (j < nh) {                                  // h node: c + (v-1/2)(log s + log(s + 2x))
       const double sj = __ldg(hs + j);
       L[2 + k] = fma(vm, __ldg(hy + j) + ix_log(sj + tx), __ldg(hc + j));
-      if (DX) A[2 + k] = 1.0 / (sj + tx);
+      if (DX) A[2 + k] = ix_rcp(sj + tx);
       key = max(key, order_key(L[2 + k]));
     }
   }
@@ -215,7 +216,7 @@ __device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta
   s0 = fma(beta, g0, h0);
   s1 = 0.0;
   if (DX) {
-    const double a0 = t0 / (tx + s), a1 = t1 / (sh + tx);
+    const double a0 = t0 * ix_rcp(tx + s), a1 = t1 * ix_rcp(sh + tx);
     s1 = fma(beta, isg ? a0 : 0.0, (isg ? 0.0 : a0) + a1);
   }
 }
@@ -513,7 +514,7 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
     const double r = ks ? ks->ub64[j] : ix_exp(beta * __ldg(lb_kq_g64_logu + j));
     const double sj = sx * r;
     L[k] = fma(vm, ix_log(r + 0.015625), __ldg(lb_kq_g64_c + j)) - sj;     // less log beta, as above
-    A[k] = DX ? 1.0 / (sj + tx) : 0.0;
+    A[k] = DX ? ix_rcp(sj + tx) : 0.0;
     live[k] = true;
     rel[k] = true;
     key = max(key, order_key(L[k] + C));
@@ -554,13 +555,13 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
         L[k] = fma(vm, ix_log(sj + tx), fma(vp, o, lwb)) - sj;
         key = max(key, order_key(L[k]));
       }
-      if (DX) A[k] = 1.0 / (sj + tx);
+      if (DX) A[k] = ix_rcp(sj + tx);
     }
   }
   {                                                // h nodes, 32-node rule in log s
     const double sj = __ldg(lb_kq_hl32_s + lane);
     L[5] = fma(vm, __ldg(lb_kq_hl32_y + lane) + ix_log(sj + tx), __ldg(lb_kq_hl32_c + lane));
-    A[5] = DX ? 1.0 / (sj + tx) : 0.0;
+    A[5] = DX ? ix_rcp(sj + tx) : 0.0;
     live[5] = true;
     rel[5] = false;
     key = max(key, order_key(L[5]));

@@ -131,13 +131,13 @@ __device__ __forceinline__ T tile_expr(int r, T v, T x, int n) {
     }
   } else if constexpr (DX) {
     switch (r) {
-      case R_MU20: return mu_dx<KIND, 20>(v, x);
+      case R_MU20: return mu_dx_n<KIND, 20>(v, x, n);
       case R_U13: return u_dx<KIND, 13>(v, x);
       case R_MU3: return mu_dx<KIND, 3>(v, x);
       case R_U4: return u_dx<KIND, 4>(v, x);
       case R_U6: return u_dx<KIND, 6>(v, x);
       case R_U9: return u_dx<KIND, 9>(v, x);
-      default: return (KIND == KIND_I) ? series_dx(v, x) : __longlong_as_double(0x7ff8000000000000LL);
+      default: return (KIND == KIND_I) ? series_dx_n(v, x, n) : __longlong_as_double(0x7ff8000000000000LL);
     }
   } else {
     switch (r) {
@@ -153,11 +153,11 @@ __device__ __forceinline__ T tile_expr(int r, T v, T x, int n) {
 }
 
 // List key of a classified pair, and the term count of mu_20 in *n (FP64
-// values; 0 otherwise).
+// values and x-derivatives; 0 otherwise).
 template <int KIND, bool DX, typename T>
 __device__ __forceinline__ int tile_key(int r, T v, T x, int* n) {
   *n = 0;
-  if constexpr (sizeof(T) == 8 && !DX) {
+  if constexpr (sizeof(T) == 8) {
     if (r == R_MU20) {
       *n = mu_terms<20>(f32_cut(v), f32_cut(x));
       return KEY_MU20 + *n - 1;
@@ -336,7 +336,7 @@ __device__ __forceinline__ void tile_eval_region(TileShared<T, NT>& S, int lane,
     }
     const int li = S.list[jl];
     int nterm = S.nt[li];
-    if constexpr (sizeof(T) == 8 && !DX && KIND == KIND_I && R == R_FALLBACK)
+    if constexpr (sizeof(T) == 8 && KIND == KIND_I && R == R_FALLBACK)
       nterm = series_terms(f32_cut(so ? so->v : (double)S.sv[li]), f32_cut((double)S.sx[li]));
     T val;
     if constexpr (sizeof(T) == 8 && !DX) {
