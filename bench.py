@@ -453,6 +453,7 @@ def main():
     if not args.no_dx:
         from paper_2409_08729_gb300 import vmf as VM
         fits = []
+        VM.fit_kappa(2048, 0.5, device=str(dev))   # first call loads the module (untimed)
         for d in (2048, 8192, 32768):
             for kt in (d / 10.0, float(d), 10.0 * d):
                 R = float(VM.mean_ratio(d, torch.tensor([kt], dtype=torch.float64, device=dev)))

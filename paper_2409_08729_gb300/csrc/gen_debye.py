@@ -138,6 +138,15 @@ def render_header(polys):
     lines.append("#define LB_DEBYE_DF_N %d" % o)
     lines.append("static __constant__ const int lb_debye_df_off[%d] = {%s};" % (KMAX + 1, ", ".join(map(str, offs))))
     lines.append("static __constant__ const float lb_debye_df[%d][2] = {\n%s};" % (o, ",\n".join(rows)))
+    lines.append("// Q_k(p) in double-float, k = 2..13, the same layout (Q_k has the degree")
+    lines.append("// of P_k): the k + 1 coefficients of Q_k, ascending, from lb_debye_df_off[k].")
+    qrows = []
+    for k in range(2, KMAX + 1):
+        for c in q_coeffs(k, polys):
+            hi, lo = f32_split(c)
+            qrows.append("  {%s, %s}" % (_f32_lit(hi), _f32_lit(lo)))
+    assert len(qrows) == o
+    lines.append("static __constant__ const float lb_debye_qdf[%d][2] = {\n%s};" % (o, ",\n".join(qrows)))
     lines.append("")
     return "\n".join(lines) + "\n"
 

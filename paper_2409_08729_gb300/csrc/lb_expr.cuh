@@ -363,6 +363,15 @@ __device__ __forceinline__ dfloat debye_P_df(int k, dfloat p) {
   return r;
 }
 
+// Q_k(p) in double-float, k = 2..13, from lb_debye_qdf (same layout).
+__device__ __forceinline__ dfloat debye_Q_df(int k, dfloat p) {
+  const float(*c)[2] = lb_debye_qdf + lb_debye_df_off[k];
+  dfloat r = df_make(c[k][0], c[k][1]);
+#pragma unroll 1
+  for (int i = k - 1; i >= 0; --i) r = df_mul_add(r, p, df_make(c[i][0], c[i][1]));
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T debye_Q(int k, T p) {
   switch (k) {
@@ -723,12 +732,18 @@ __device__ __forceinline__ double u_dx(double v, double x) {
   const double p = t * t;
   double q = t * inv_v;
   if (KIND == KIND_K) q = -q;
-  double accP = debye_P(K, p), accQ = debye_Q(K, p);
-#pragma unroll
-  for (int k = K - 1; k >= 1; --k) {
-    accP = fma(accP, q, debye_P(k, p));
-    accQ = fma(accQ, q, debye_Q(k, p));
+  // Horner in q over k = K..1 for S and SQ; as in u_expr, the terms k >= 2
+  // (at most 1/v^2 of each sum in the U regions) in double-float, rolled
+  // over the coefficient tables, and k = 1 and the outer steps in FP64.
+  const dfloat pd = df_from_double(p), qd = df_from_double(q);
+  dfloat aP = debye_P_df(K, pd), aQ = debye_Q_df(K, pd);
+#pragma unroll 1
+  for (int k = K - 1; k >= 2; --k) {
+    aP = df_mul_add(aP, qd, debye_P_df(k, pd));
+    aQ = df_mul_add(aQ, qd, debye_Q_df(k, pd));
   }
+  const double accP = fma(df_to_double(aP), q, lb_debye_P1(p));
+  const double accQ = fma(df_to_double(aQ), q, lb_debye_Q1(p));
   const double S = fma(accP, q, 1.0);
   const double SQ = accQ * q;
   const double lead = r * ix_rcp(xp);               // 1/(t x') = sqrt(1 + x'^2)/x'

@@ -44,14 +44,22 @@ def fit_kappa(d, R, device="cuda", tol=1e-15, max_iter=50):
     Returns dict(kappa, iterations, kappa0, kappa1, kappa2, history)."""
     k = torch.tensor([sra_kappa0(d, R)], dtype=torch.float64, device=device)
     hist = [float(k)]
+    prev = math.inf
     for it in range(max_iter):
         A = mean_ratio(d, k)
         dA = 1.0 - A * A - (d - 1.0) * A / k
         step = (A - R) / dA
+        s = abs(float(step))
+        # Newton's steps shrink quadratically until A_d's rounding; a step no
+        # smaller than the one before means that floor is reached (iterates
+        # 2 and on: kappa_1 and kappa_2 are always formed)
+        if it >= 2 and s >= prev:
+            break
         k = k - step
         hist.append(float(k))
-        if abs(float(step)) <= tol * abs(float(k)):
+        if s <= tol * abs(float(k)):
             break
+        prev = s
     return {"kappa": hist[-1], "iterations": len(hist) - 1, "kappa0": hist[0],
             "kappa1": hist[1] if len(hist) > 1 else math.nan,
             "kappa2": hist[2] if len(hist) > 2 else math.nan, "history": hist}

@@ -59,6 +59,16 @@ static dfloat P(int k, dfloat p) {
 extern "C" void df_debye(int k, const double* p, double* out, long n) {
   for (long i = 0; i < n; ++i) out[i] = lb::df_to_double(P(k, lb::df_from_double(p[i])));
 }
+// the same loop over the Q_k table (debye_Q_df)
+static dfloat Q(int k, dfloat p) {
+  const float(*c)[2] = lb_debye_qdf + lb_debye_df_off[k];
+  dfloat r = lb::df_make(c[k][0], c[k][1]);
+  for (int i = k - 1; i >= 0; --i) r = lb::df_mul_add(r, p, lb::df_make(c[i][0], c[i][1]));
+  return r;
+}
+extern "C" void df_debye_q(int k, const double* p, double* out, long n) {
+  for (long i = 0; i < n; ++i) out[i] = lb::df_to_double(Q(k, lb::df_from_double(p[i])));
+}
 '''
 _lib = None
 
@@ -146,15 +156,17 @@ def test_mul_and_add():
         assert abs(_frac(o[2]) + _frac(o[3]) - (a + b)) <= (abs(a) + abs(b)) * Fraction(4, 2 ** 48)
 
 
+@pytest.mark.parametrize("which", ["P", "Q"])
 @pytest.mark.parametrize("k", [2, 5, 9, 13])
-def test_debye_polynomials_in_double_float(k):
-    """P_k(p) in double-float against the exact rational polynomial at the
-    double-float input; the error bound scales with sum |c_i| p^i, the size of
-    the terms that cancel near p = 1."""
-    cs = gen_debye.p_coeffs(k)
+def test_debye_polynomials_in_double_float(k, which):
+    """P_k(p) and Q_k(p) = k P_k + 2 p P_k' (the derivative's polynomials) in
+    double-float against the exact rational polynomial at the double-float
+    input; the error bound scales with sum |c_i| p^i, the size of the terms
+    that cancel near p = 1."""
+    cs = gen_debye.p_coeffs(k) if which == "P" else gen_debye.q_coeffs(k)
     p = np.concatenate([np.linspace(0.0, 1.0, 101), np.random.default_rng(k).uniform(0, 1, 200)])
     out = np.empty_like(p)
-    lib().df_debye(ctypes.c_int(k), _p(p), _p(out), ctypes.c_long(p.size))
+    getattr(lib(), "df_debye" if which == "P" else "df_debye_q")(ctypes.c_int(k), _p(p), _p(out), ctypes.c_long(p.size))
     h, l, back = np.empty(p.size, np.float32), np.empty(p.size, np.float32), np.empty_like(p)
     lib().df_conv(_p(p), _p(h), _p(l), _p(back), ctypes.c_long(p.size))
     for pi, hi, li, oi in zip(p, h, l, out):
