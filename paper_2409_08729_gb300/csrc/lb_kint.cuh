@@ -126,101 +126,6 @@ __device__ __forceinline__ void kint_scalar_setup(KintScalar& ks, double v) {
   __syncthreads();
 }
 
-// One pair, fixed Gauss rules (g: 32 or 64 nodes in u; h: rule hr), all
-// lanes of the warp: returns on every lane its part of the shifted sums
-// s0 = sum_j e^{L_j - mm} and s1 = sum_j e^{L_j - mm} / (s_j + 2x) (DX), with
-// the common shift mm (the warp maximum of L, taken on the integer pipe).
-// The node exps, logs and the derivative's reciprocals 1/(s + 2x) run on the
-// integer pipes (lb_intmath.cuh); log beta,
-// common to the g nodes, multiplies their partial sums instead of entering
-// every node (any shift is exact, and beta <= 16 cannot overflow them).
-template <bool DX>
-__device__ __forceinline__ void kint_sums_fixed(double v, double x, double beta, int ng, int hr,
-                                                int lane, double& mm, double& s0, double& s1,
-                                                const KintScalar* ks) {
-  const double vm = v - 0.5, tx = 2.0 * x;
-  const double* gu = ng == 32 ? lb_kq_g32_logu : lb_kq_g64_logu;
-  const double* gc = ng == 32 ? lb_kq_g32_c : lb_kq_g64_c;
-  const double* hs = hr == 0 ? lb_kq_hl32_s : (hr == 1 ? lb_kq_hl48_s : lb_kq_hq32_s);
-  const double* hy = hr == 0 ? lb_kq_hl32_y : (hr == 1 ? lb_kq_hl48_y : lb_kq_hq32_y);
-  const double* hc = hr == 0 ? lb_kq_hl32_c : (hr == 1 ? lb_kq_hl48_c : lb_kq_hq32_c);
-  const int nh = hr == 1 ? 48 : 32;
-  double L[4], A[4];
-  int key = (int)0x800fffff;                       // order_key(-inf)
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    L[k] = 0.0;
-    A[k] = 0.0;
-    if (32 * k < ng) {                             // g node: log w + 7 log u - u^beta + (v-1/2) log(2x + u^beta)
-      const int j = lane + 32 * k;
-      const double ub = ks ? (ng == 32 ? ks->ub32[j] : ks->ub64[j]) : ix_exp(beta * __ldg(gu + j));
-      L[k] = fma(vm, ix_log(tx + ub), __ldg(gc + j)) - ub;
-      if (DX) A[k] = ix_rcp(tx + ub);
-      key = max(key, order_key(L[k]));
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int j = lane + 32 * k;
-    L[2 + k] = 0.0;
-    A[2 + k] = 0.0;
-    if (j < nh) {                                  // h node: c + (v-1/2)(log s + log(s + 2x))
-      const double sj = __ldg(hs + j);
-      L[2 + k] = fma(vm, __ldg(hy + j) + ix_log(sj + tx), __ldg(hc + j));
-      if (DX) A[2 + k] = ix_rcp(sj + tx);
-      key = max(key, order_key(L[2 + k]));
-    }
-  }
-  mm = key_to_double(__reduce_max_sync(0xffffffffu, key));
-  double g0 = 0.0, g1 = 0.0, h0 = 0.0, h1 = 0.0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const bool live = (k < 2) ? (32 * k < ng) : (lane + 32 * (k - 2) < nh);
-    if (live) {
-      const double t = ix_exp(L[k] - mm);
-      if (k < 2) {
-        g0 += t;
-        if (DX) g1 = fma(t, A[k], g1);
-      } else {
-        h0 += t;
-        if (DX) h1 = fma(t, A[k], h1);
-      }
-    }
-  }
-  s0 = fma(beta, g0, h0);
-  s1 = DX ? fma(beta, g1, h1) : 0.0;
-}
-
-// One pair, 24 g nodes and 40 h nodes (h rule 3) in two slots: slot 0 holds
-// the g nodes on lanes 0-23 and h nodes 0-7 on lanes 24-31, slot 1 h nodes
-// 8-39.  A g node is c + (v-1/2) log(2x + s) - s with s = u^beta; an h node
-// c + (v-1/2)(y + log(s + 2x)) with s, y = log s and -s folded into c; the
-// exp of s runs on the g lanes only.  Sums as in kint_sums_fixed.
-template <bool DX>
-__device__ __forceinline__ void kint_sums_g24h40(double v, double x, double beta, int lane,
-                                                 double& mm, double& s0, double& s1, const KintScalar* ks) {
-  const double vm = v - 0.5, tx = 2.0 * x;
-  const bool isg = lane < 24;
-  const int jh = isg ? 0 : lane - 24;
-  double s;
-  if (isg) s = ks ? ks->ub24[lane] : ix_exp(beta * __ldg(lb_kq_g24_logu + lane));
-  else s = __ldg(lb_kq_hl40_s + jh);
-  const double y0 = isg ? 0.0 : __ldg(lb_kq_hl40_y + jh);
-  const double c0 = isg ? __ldg(lb_kq_g24_c + lane) : __ldg(lb_kq_hl40_c + jh);
-  const double L0 = fma(vm, ix_log(tx + s) + y0, c0) - (isg ? s : 0.0);
-  const double sh = __ldg(lb_kq_hl40_s + 8 + lane);
-  const double L1 = fma(vm, __ldg(lb_kq_hl40_y + 8 + lane) + ix_log(sh + tx), __ldg(lb_kq_hl40_c + 8 + lane));
-  mm = key_to_double(__reduce_max_sync(0xffffffffu, max(order_key(L0), order_key(L1))));
-  const double t0 = ix_exp(L0 - mm), t1 = ix_exp(L1 - mm);
-  const double g0 = isg ? t0 : 0.0, h0 = (isg ? 0.0 : t0) + t1;
-  s0 = fma(beta, g0, h0);
-  s1 = 0.0;
-  if (DX) {
-    const double a0 = t0 * ix_rcp(tx + s), a1 = t1 * ix_rcp(sh + tx);
-    s1 = fma(beta, isg ? a0 : 0.0, (isg ? 0.0 : a0) + a1);
-  }
-}
-
 // Warp sum of values below 2^63 (the result must stay below 2^64), exact,
 // on the integer pipe: three limbs of 20, 20 and 23 bits, one warp
 // reduction each (a limb sum stays below 2^28).
@@ -348,9 +253,13 @@ __device__ __forceinline__ uint64_t kq_exp(typename KqLog<FX>::type L, typename 
   if constexpr (FX) return ix_exp_q58_fx(L - mm); else return ix_exp_q58(L - mm);
 }
 
-template <bool FX>
+// W (the x-derivative): also w1 = sum_j t_j / (s_j + 2x) over the lane's
+// terms t_j (the Q58 or Q56 integers, as doubles), so that the F-weighted
+// mean of 1/(s + 2x) is w1 / (the integer sum).
+template <bool FX, bool W = false>
 __device__ __forceinline__ uint64_t kint_sumq_fixed(const KqPair& p, int ng, int hr, int lane,
-                                                    typename KqLog<FX>::type& mm, const KintScalar* ks) {
+                                                    typename KqLog<FX>::type& mm, const KintScalar* ks,
+                                                    double* w1 = nullptr) {
   typedef typename KqLog<FX>::type LT;
   const double* gu = ng == 32 ? lb_kq_g32_logu : lb_kq_g64_logu;
   const double* gc = ng == 32 ? lb_kq_g32_c : lb_kq_g64_c;
@@ -364,13 +273,16 @@ __device__ __forceinline__ uint64_t kint_sumq_fixed(const KqPair& p, int ng, int
   const double* gtab = ks ? (ng == 32 ? ks->ub32 : ks->ub64) : nullptr;
   const long long* gtabq = ks ? (ng == 32 ? ks->ubq32 : ks->ubq64) : nullptr;
   LT L[4];
+  double A[4];                                     // W: 1/(s + 2x)
   long long key = (long long)0x8000000000000000ull;   // below every key
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     L[k] = 0;
     if (32 * k < ng) {
       const int j = lane + 32 * k;
-      L[k] = kq_eval<FX>(p, kq_g<FX>(p, __ldg(gu + j), 0.0, gtab, gtabq, j, gc, gcq));
+      const KqNode n = kq_g<FX>(p, __ldg(gu + j), 0.0, gtab, gtabq, j, gc, gcq);
+      L[k] = kq_eval<FX>(p, n);
+      if (W) A[k] = ix_rcp(n.z);
       key = max(key, kq_key<FX>(L[k]));
     }
   }
@@ -379,33 +291,43 @@ __device__ __forceinline__ uint64_t kint_sumq_fixed(const KqPair& p, int ng, int
     const int j = lane + 32 * k;
     L[2 + k] = 0;
     if (j < nh) {
-      L[2 + k] = kq_eval<FX>(p, kq_h<FX>(p, hs, hy, hyq, hc, hcq, j));
+      const KqNode n = kq_h<FX>(p, hs, hy, hyq, hc, hcq, j);
+      L[2 + k] = kq_eval<FX>(p, n);
+      if (W) A[2 + k] = ix_rcp(n.z);
       key = max(key, kq_key<FX>(L[2 + k]));
     }
   }
   mm = kq_max<FX>(key);
   uint64_t q = 0;
+  double w = 0.0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const bool live = (k < 2) ? (32 * k < ng) : (lane + 32 * (k - 2) < nh);
-    if (live) q += kq_exp<FX>(L[k], mm) >> 2;
+    if (live) {
+      const uint64_t t = kq_exp<FX>(L[k], mm) >> 2;
+      q += t;
+      if (W) w = fma(__ull2double_rn(t), A[k], w);
+    }
   }
+  if (W) *w1 = w;
   return warp_sum_u64(q);
 }
 
-template <bool FX>
+template <bool FX, bool W = false>
 __device__ __forceinline__ uint64_t kint_sumq_g24h40(const KqPair& p, int lane, typename KqLog<FX>::type& mm,
-                                                     const KintScalar* ks) {
+                                                     const KintScalar* ks, double* w1 = nullptr) {
   typedef typename KqLog<FX>::type LT;
   const KqNode n0 = lane < 24 ? kq_g<FX>(p, __ldg(lb_kq_g24_logu + lane), 0.0, ks ? ks->ub24 : nullptr,
                                          ks ? ks->ubq24 : nullptr, lane, lb_kq_g24_c, lb_kq_g24_c_q)
                               : kq_h<FX>(p, lb_kq_hl40_s, lb_kq_hl40_y, lb_kq_hl40_y_q, lb_kq_hl40_c, lb_kq_hl40_c_q,
                                          lane - 24);
+  const KqNode n1 = kq_h<FX>(p, lb_kq_hl40_s, lb_kq_hl40_y, lb_kq_hl40_y_q, lb_kq_hl40_c, lb_kq_hl40_c_q, lane + 8);
   const LT L0 = kq_eval<FX>(p, n0);
-  const LT L1 = kq_eval<FX>(p, kq_h<FX>(p, lb_kq_hl40_s, lb_kq_hl40_y, lb_kq_hl40_y_q, lb_kq_hl40_c, lb_kq_hl40_c_q,
-                                        lane + 8));
+  const LT L1 = kq_eval<FX>(p, n1);
   mm = kq_max<FX>(max(kq_key<FX>(L0), kq_key<FX>(L1)));
-  return warp_sum_u64((kq_exp<FX>(L0, mm) >> 2) + (kq_exp<FX>(L1, mm) >> 2));
+  const uint64_t t0 = kq_exp<FX>(L0, mm) >> 2, t1 = kq_exp<FX>(L1, mm) >> 2;
+  if (W) *w1 = fma(__ull2double_rn(t0), ix_rcp(n0.z), __ull2double_rn(t1) * ix_rcp(n1.z));
+  return warp_sum_u64(t0 + t1);
 }
 
 // One pair, one lane slot (values, 2 <= v <= 16.5).  int_0^inf F(s) ds is
@@ -439,10 +361,12 @@ __device__ __forceinline__ uint64_t kint_sum_one(const KqPair& p, int hr, int la
 // The pairs of one values rule group (lanes in grp), one at a time: the
 // pair's arguments broadcast from its lane, its sum by the warp, and the
 // sum and shift kept on its lane.
-template <bool FX, int CLS>
+// W (the x-derivative): also the warp sum of the weighted terms, in s1_i.
+template <bool FX, int CLS, bool W = false>
 __device__ __forceinline__ void kint_q_group(unsigned grp, int ng, int hr, int lane, long long vmq_i, long long gkq_i,
                                              double vm_i, double gk_i, double tx_i, double beta_i, double& m_i,
-                                             long long& mq_i, uint64_t& q_i, const KintScalar* ks) {
+                                             long long& mq_i, uint64_t& q_i, const KintScalar* ks,
+                                             double* s1_i = nullptr) {
   for (; grp; grp &= grp - 1) {
     const int e = __ffs(grp) - 1;
     KqPair p;
@@ -457,7 +381,12 @@ __device__ __forceinline__ void kint_q_group(unsigned grp, int ng, int hr, int l
     p.beta = ks ? 0.0 : __shfl_sync(0xffffffffu, beta_i, e);
     typename KqLog<FX>::type mm = 0;
     uint64_t q = 0;
-    if constexpr (CLS == 1 || CLS == 2) {
+    double w = 0.0;
+    if constexpr (W) {                             // the derivative's rules: fixed and packed only
+      if (ng == 24) q = kint_sumq_g24h40<FX, true>(p, lane, mm, ks, &w);
+      else q = kint_sumq_fixed<FX, true>(p, ng, hr, lane, mm, ks, &w);
+      w = warp_sum(w);
+    } else if constexpr (CLS == 1 || CLS == 2) {
       q = kint_sum_one<FX>(p, hr, lane, mm, ks);
     } else if constexpr (CLS == 3) {
       q = kint_sumq_g24h40<FX>(p, lane, mm, ks);
@@ -472,6 +401,7 @@ __device__ __forceinline__ void kint_q_group(unsigned grp, int ng, int hr, int l
       if constexpr (FX) mq_i = mm;                 // to a double once, after the batch
       else m_i = mm;
       q_i = q;
+      if constexpr (W) *s1_i = w;
     }
   }
 }
@@ -630,11 +560,11 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
   // (v + 1/2) log s0 = (v - 1/2) log s0 + log s0 for the one-slot rules),
   // added to their log terms; in the fixed-point domain (v <= 16.5, x <= 32)
   // in Q53 with v - 1/2 in Q58, else as doubles
-  const bool fx_i = !DX && LB_LE(vi, 16.5) && LB_LE(xi, 32.0);
+  const bool fx_i = LB_LE(vi, 16.5) && LB_LE(xi, 32.0);
   long long vmq_i = 0, gkq_i = 0;
   double vm_i = 0.0, gk_i = 0.0;
-  if (!DX) {
-    const int hr_i = rule_i >> 8;
+  {
+    const int hr_i = rule_i >> 8;                  // one-slot rules (hr >= 4) for values only
     if (fx_i) {
       vmq_i = ix_fix(vi - 0.5, 58);
       gkq_i = ix_log_q53(beta_i);
@@ -667,13 +597,15 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
     rem &= ~grp;
     const int rule = key & 0xffff;
     const int ng = rule & 0xff, hr = rule >> 8;
-    if (!DX && CLS != 0 && ng != 0) {
+    if (CLS != 0 && ng != 0) {
       const int qb = hr >= 4 ? 58 : 56;
       if ((grp >> lane) & 1u) qb_i = qb;
       if ((key >> 16) == 0)
-        kint_q_group<true, CLS>(grp, ng, hr, lane, vmq_i, gkq_i, vm_i, gk_i, tx_i, beta_i, m_i, mq_i, q_i, ks);
+        kint_q_group<true, CLS, DX>(grp, ng, hr, lane, vmq_i, gkq_i, vm_i, gk_i, tx_i, beta_i, m_i, mq_i, q_i, ks,
+                                    &s1_i);
       else
-        kint_q_group<false, CLS>(grp, ng, hr, lane, vmq_i, gkq_i, vm_i, gk_i, tx_i, beta_i, m_i, mq_i, q_i, ks);
+        kint_q_group<false, CLS, DX>(grp, ng, hr, lane, vmq_i, gkq_i, vm_i, gk_i, tx_i, beta_i, m_i, mq_i, q_i, ks,
+                                     &s1_i);
       continue;
     }
     for (; grp; grp &= grp - 1) {
@@ -682,12 +614,7 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
       const double x = __shfl_sync(0xffffffffu, xi, e);
       const double beta = __shfl_sync(0xffffffffu, beta_i, e);
       double mm, s0, s1 = 0.0;
-      if (CLS == 0 || (CLS < 0 && ng == 0)) {
-        kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);
-      } else if constexpr (DX) {                 // values take the fixed-point sums above
-        if (ng == 24) kint_sums_g24h40<DX>(v, x, beta, lane, mm, s0, s1, ks);
-        else kint_sums_fixed<DX>(v, x, beta, ng, hr, lane, mm, s0, s1, ks);
-      }
+      kint_sums_split<DX>(v, x, beta, lane, mm, s0, s1, ks);   // the other rules take the sums above
       s0 = warp_sum(s0);
       if (DX) s1 = warp_sum(s1);
       if (lane == e) {
@@ -697,7 +624,10 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
       }
     }
   }
-  if (DX) return -(vi / xi + 1.0) + (2.0 * vi - 1.0) * (s1_i / s0_i);
+  if (DX) {
+    if (qb_i) s0_i = __ull2double_rn(q_i);        // the weighted sum is in the same units
+    return -(vi / xi + 1.0) + (2.0 * vi - 1.0) * (s1_i / s0_i);
+  }
   if (qb_i) {
     s0_i = __ull2double_rn(q_i) * (qb_i == 58 ? 0x1p-58 : 0x1p-56);   // exact scalings
     if (fx_i) m_i = __ll2double_rn(mq_i) * 0x1p-53;
