@@ -174,8 +174,8 @@ def _h_dx(v, x, tag):
     return s0, s1
 
 
-# The x-derivative's rules (they keep the fixed and packed rules; no one-slot
-# rule): d/dx log K = -(v/x + 1) + (2v - 1) <1/(s + 2x)>, the mean weighted by
+# The x-derivative's fixed and packed rules (the one-slot rules: below):
+# d/dx log K = -(v/x + 1) + (2v - 1) <1/(s + 2x)>, the mean weighted by
 # F over the nodes (dF/dx = F (2v - 1)/(s + 2x)), with the orders and
 # arguments each rule serves, including the small orders at 0.25 <= x < 0.6
 # that take 64 g nodes for the derivative.
@@ -206,6 +206,43 @@ def test_derivative_rule_error_map(name):
             d = -(vm / xm + 1) + (2 * vm - 1) * (a1 + b1) / (a0 + b0)
             err = float(abs(d - mp.mpf(r)) / abs(mp.mpf(r)))
             assert err < 2e-16, (name, v, x, err)
+
+
+def _one_dx(v, x, N, htag, ls0):
+    """A one-slot rule and its x-derivative's weighted sum (s = s0 u^beta on [0, s0])."""
+    beta = mp.mpf(16) / (2 * v + 1)
+    a0 = a1 = mp.mpf(0)
+    for lu, c in zip(T["lb_kq_g%d_logu" % N], T["lb_kq_g%d_c" % N]):
+        s = mp.exp(beta * lu + ls0)
+        t = mp.exp(c + (v + mp.mpf(0.5)) * ls0 + (v - mp.mpf(0.5)) * mp.log(2 * x + s) - s)
+        a0 += beta * t
+        a1 += beta * t / (s + 2 * x)
+    b0, b1 = _h_dx(v, x, htag)
+    return a0 + b0, a1 + b1
+
+
+@pytest.mark.parametrize("rule", ["s0 = 8", "s0 = 3"])
+def test_derivative_one_slot_rules(rule):
+    """The one-slot rules serve the x-derivative too (2 <= v <= 16.5): their
+    weighted mean of 1/(s + 2x), summed from the double tables in 30 digits,
+    against the oracle's d/dx log K, below 2e-16 relative (the map over
+    x in [1e-300, 30] measured at most 1.1e-16, the reference's own
+    rounding)."""
+    if rule == "s0 = 8":
+        N, tag, ls0, vs = 22, "hq10o8", mp.mpf(T["LB_KQ_LOG8"]), [2.0, 2.2, 3.9, 5.5, 6.99]
+    else:
+        N, tag, ls0, vs = 12, "hq20o3", mp.mpf(T["LB_KQ_LOG3"]), [7.0, 9.3, 12.71, 16.0, 16.5]
+    xs = [1e-300, 1e-8, 1e-3, 0.0128, 0.3, 1.0, 4.7, 13.0, 25.0, 30.0]
+    V, X = np.meshgrid(np.array(vs), np.array(xs), indexing="ij")
+    V, X = V.ravel(), X.ravel()
+    ref = oracle.dlog_k_dx(V, X)
+    with mp.workdps(30):
+        for v, x, r in zip(V, X, ref):
+            vm, xm = mp.mpf(v), mp.mpf(x)
+            a0, a1 = _one_dx(vm, xm, N, tag, ls0)
+            d = -(vm / xm + 1) + (2 * vm - 1) * a1 / a0
+            err = float(abs(d - mp.mpf(r)) / abs(mp.mpf(r)))
+            assert err < 2e-16, (rule, v, x, err)
 
 
 def test_derivative_needs_64_nodes_below_x_0_6():
