@@ -63,9 +63,9 @@ CASES = {
 }
 
 
-def _fixed_log_integral(v, x, rule):
-    """m + log(sum) of the rule in the kernel's fixed-point arithmetic, as
-    an exact rational m plus a 40-digit log of the integer sum."""
+def _fixed_terms(v, x, rule):
+    """The rule's node log terms L (Q53), node arguments z = s + 2x, and the
+    right shift of the Q58 terms (2 where a lane holds up to four terms)."""
     ng, htag, s0 = RULES[rule]
     vmq = int(ix_fix(np.array([v - 0.5]), 58)[0])
     beta = 16.0 / (2.0 * v + 1.0)
@@ -83,10 +83,15 @@ def _fixed_log_integral(v, x, rule):
     hs = T["lb_kq_%s_s" % htag]
     Lh = T["lb_kq_%s_c_q" % htag] + ix_mul_q58(np.full(hs.size, vmq, dtype=np.int64),
                                                T["lb_kq_%s_y_q" % htag] + ix_log_q53(hs + tx))
-    L = np.concatenate([Lg, Lh])
+    return np.concatenate([Lg, Lh]), np.concatenate([tx + s, hs + tx]), (0 if s0 is not None else 2)
+
+
+def _fixed_log_integral(v, x, rule):
+    """m + log(sum) of the rule in the kernel's fixed-point arithmetic, as
+    an exact rational m plus a 40-digit log of the integer sum."""
+    L, _, sh = _fixed_terms(v, x, rule)
     assert np.abs(L).max() < 2 ** 61                  # |L| < 2^8 in value: far inside Q53's range
     m = int(L.max())
-    sh = 0 if s0 is not None else 2
     q = sum(int(t) >> sh for t in ix_exp_q58_fx(L - m))
     assert q < 2 ** 64
     return mp.mpf(m) / mp.mpf(2) ** 53 + mp.log(mp.mpf(q) / mp.mpf(2) ** (58 - sh))
@@ -106,6 +111,25 @@ def test_fixed_point_sums_against_oracle(rule):
             pre = mp.log(mp.pi) / 2 - mp.loggamma(vm + mp.mpf(0.5)) - vm * mp.log(2 * xm) - xm
             err = float(abs(pre + _fixed_log_integral(v, x, rule) - (mp.mpf(h) + mp.mpf(l)))) / max(abs(h), cc)
             assert err < bound, (rule, v, x, err)
+
+
+@pytest.mark.parametrize("rule", list(RULES))
+def test_fixed_point_derivative_sums_against_oracle(rule):
+    """The x-derivative from the same integer terms t_j: d/dx log K =
+    -(v/x + 1) + (2v - 1) sum_j t_j / (s_j + 2x) / sum_j t_j (the weights in
+    double precision, as the kernel forms them), against the oracle's Bessel
+    ratio: below 4e-16 relative."""
+    vs, xs = CASES[rule]
+    V, X = np.meshgrid(np.array(vs), np.array(xs), indexing="ij")
+    V, X = V.ravel(), X.ravel()
+    ref = oracle.dlog_k_dx(V, X)
+    for v, x, r in zip(V, X, ref):
+        L, z, sh = _fixed_terms(v, x, rule)
+        t = ix_exp_q58_fx(L - L.max()) >> np.uint64(sh)
+        w1 = float(np.sum(t.astype(np.float64) / z))
+        s0 = float(sum(int(u) for u in t))
+        d = -(v / x + 1.0) + (2.0 * v - 1.0) * (w1 / s0)
+        assert abs(d - r) <= 4e-16 * abs(r) + 1e-300, (rule, v, x, abs(d - r) / abs(r))
 
 
 def test_fixed_point_shift_is_exact():
