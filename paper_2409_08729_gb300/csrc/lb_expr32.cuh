@@ -202,7 +202,7 @@ __device__ __forceinline__ float kint_gauss32(float v, float x, float beta, floa
     return m + logf(sum);
   }
   if (v > 1.2f && v <= 5.0f) {
-    // 24 g + 40 h nodes in two lane slots (as kint_sums_g24h40)
+    // 24 g + 40 h nodes in two lane slots (as kint_sumq_g24h40)
     const bool isg = lane < 24;
     const int jh = isg ? 0 : lane - 24;
     const float s = isg ? (ks ? ks->ub24[lane] : expf(beta * __ldg(lb_kqf_g24_logu + lane))) : __ldg(lb_kqf_hl40_s + jh);
