@@ -388,9 +388,17 @@ __device__ __forceinline__ void kint_q_group(unsigned grp, int ng, int hr, int l
     uint64_t q = 0;
     double w = 0.0;
     if constexpr (W) {                             // the derivative: one-slot, packed and fixed rules
-      if (hr >= 4) q = kint_sum_one<FX, true>(p, hr, lane, mm, ks, &w);
-      else if (ng == 24) q = kint_sumq_g24h40<FX, true>(p, lane, mm, ks, &w);
-      else q = kint_sumq_fixed<FX, true>(p, ng, hr, lane, mm, ks, &w);
+      if constexpr (CLS == 1 || CLS == 2) {
+        q = kint_sum_one<FX, true>(p, hr, lane, mm, ks, &w);
+      } else if constexpr (CLS == 3) {
+        q = kint_sumq_g24h40<FX, true>(p, lane, mm, ks, &w);
+      } else if constexpr (CLS == 4 || CLS == 5) {
+        q = kint_sumq_fixed<FX, true>(p, ng, hr, lane, mm, ks, &w);
+      } else {
+        if (hr >= 4) q = kint_sum_one<FX, true>(p, hr, lane, mm, ks, &w);
+        else if (ng == 24) q = kint_sumq_g24h40<FX, true>(p, lane, mm, ks, &w);
+        else q = kint_sumq_fixed<FX, true>(p, ng, hr, lane, mm, ks, &w);
+      }
       w = warp_sum(w);
     } else if constexpr (CLS == 1 || CLS == 2) {
       q = kint_sum_one<FX>(p, hr, lane, mm, ks);
@@ -553,13 +561,12 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
 // pair e (DX = false) or d/dx log K (DX = true: the prefactor derivative
 // -v/x - 1 plus (2v - 1) <1/(s + 2x)>, the F-weighted mean over the nodes,
 // since dF/dx = F (2v - 1)/(s + 2x)).
-// CLS >= 0 (values only): every pair of the batch is of rule class CLS
-// (kint_class), and only that class's code is compiled, so a kernel built
-// for one class holds the registers of its own rule only.
+// CLS >= 0: every pair of the batch is of rule class CLS (kint_class), and
+// only that class's code is compiled, so a kernel built for one class holds
+// the registers of its own rule only.
 template <bool DX, int CLS = -1>
 __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane,
                                                    const KintScalar* ks = nullptr) {
-  static_assert(CLS < 0 || !DX, "class-specialized batches are built for values only");
   const double beta_i = 16.0 * ix_rcp(2.0 * vi + 1.0);   // the reciprocal on the integer pipe
   const int rule_i = kint_rule(vi, xi, DX);
   // values: the g nodes' common factor as a log, log beta (plus

@@ -75,8 +75,10 @@ namespace {
 #endif
 constexpr int kKintCtasCls[6] = {LB_KINT_CTAS_C0, LB_KINT_CTAS_C12, LB_KINT_CTAS_C12,
                                  LB_KINT_CTAS_C3, LB_KINT_CTAS_C45, LB_KINT_CTAS_C45};
-__host__ __device__ constexpr int kint_ctas_per_sm(int cls) {
-  return cls < 0 ? LB_KINT_CTAS_PER_SM : kKintCtasCls[cls];
+// The x-derivative's class kernels carry the weighted sum besides the
+// integer one and keep the general kernel's budget (64 registers).
+__host__ __device__ constexpr int kint_ctas_per_sm(int cls, bool dx = false) {
+  return (cls < 0 || dx) ? LB_KINT_CTAS_PER_SM : kKintCtasCls[cls];
 }
 
 // K-integral queue entries: the pair's offset within its chunk (chunks hold
@@ -149,7 +151,7 @@ lb_tiles_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__
 // only, with that class's code alone compiled in (the kernel returns at once
 // when the queue holds none of them).
 template <bool GAUSS, bool DX, typename T, int CLS = -1>
-__global__ void __launch_bounds__(LB_THREADS, kint_ctas_per_sm(CLS))
+__global__ void __launch_bounds__(LB_THREADS, kint_ctas_per_sm(CLS, DX))
 lb_kint_kernel(const T* __restrict__ v, int64_t v_stride, const T* __restrict__ x, T* __restrict__ out,
                const unsigned int* __restrict__ qcount, const uint32_t* __restrict__ queue, int64_t n,
                int64_t qcap) {
@@ -422,25 +424,26 @@ lb_status validate(lb_dtype dtype, const void* v, int64_t v_stride, const void* 
   return LB_OK;
 }
 
-template <typename T, int CLS>
+template <bool DX, typename T, int CLS>
 lb_status launch_kint_class(int sms, cudaStream_t st, const T* v, int64_t v_stride, const T* x, T* out,
                             const unsigned int* qcount, const uint32_t* queue, int64_t n, int64_t qcap) {
-  const int grid = sms * 2 * kint_ctas_per_sm(CLS);
+  const int grid = sms * 2 * kint_ctas_per_sm(CLS, DX);
   return launch(PS_KINT, st, [&] {
-    lb_kint_kernel<true, false, T, CLS><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, qcount, queue, n, qcap);
+    lb_kint_kernel<true, DX, T, CLS><<<grid, LB_THREADS, 0, st>>>(v, v_stride, x, out, qcount, queue, n, qcap);
   });
 }
 
-// The six class kernels of the FP64 Gauss values, in the order of the phases.
-template <typename T>
+// The six class kernels of the FP64 Gauss rules (values or x-derivatives),
+// in the order of the phases.
+template <bool DX, typename T>
 lb_status launch_kint_classes(int sms, cudaStream_t st, const T* v, int64_t v_stride, const T* x, T* out,
                               const unsigned int* qcount, const uint32_t* queue, int64_t n, int64_t qcap) {
-  lb_status s = launch_kint_class<T, 0>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
-  if (s == LB_OK) s = launch_kint_class<T, 5>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
-  if (s == LB_OK) s = launch_kint_class<T, 4>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
-  if (s == LB_OK) s = launch_kint_class<T, 3>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
-  if (s == LB_OK) s = launch_kint_class<T, 2>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
-  if (s == LB_OK) s = launch_kint_class<T, 1>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  lb_status s = launch_kint_class<DX, T, 0>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<DX, T, 5>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<DX, T, 4>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<DX, T, 3>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<DX, T, 2>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
+  if (s == LB_OK) s = launch_kint_class<DX, T, 1>(sms, st, v, v_stride, x, out, qcount, queue, n, qcap);
   return s;
 }
 
@@ -505,10 +508,10 @@ lb_status run_impl(const T* v, int64_t v_stride, const T* x, T* out, int64_t n, 
     });
     if (status != LB_OK) break;
     bool done = false;
-    if constexpr (sizeof(T) == 8 && !DX) {
+    if constexpr (sizeof(T) == 8) {
       if (mode == MODE_TIGHT) {
         // one kernel per rule class, costliest first (the phases of a mixed queue)
-        status = launch_kint_classes<T>(sms, st, vc, v_stride, xc, oc, qcount, queue, cn, cap);
+        status = launch_kint_classes<DX, T>(sms, st, vc, v_stride, xc, oc, qcount, queue, cn, cap);
         done = true;
       }
     }
