@@ -261,7 +261,10 @@ lb_status logbessel_measure_fp64(double* rates, void* cuda_stream);
  * order-0/1 functions, the comparison system of paper Sec. 6.1), 6 the
  * table-driven exp without the low table part (quadrature terms; y <= 708),
  * 7 exp, 8 log, 9 reciprocal and 10 1/sqrt in fixed-point integer
- * arithmetic (exp: y <= 708).  in/out are device arrays of n doubles.
+ * arithmetic (exp: y <= 708), 11 the Q53 log (out holds the int64 result's
+ * bits) and 12 the Q58 exponential of a Q53 shift d <= 0 (in holds d's
+ * int64 bits, out the uint64 result's bits), the K integral's node
+ * functions.  in/out are device arrays of n doubles (8-byte words).
  * LB_EINVAL for a bad which, size or pointer.
  */
 lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t n, void* cuda_stream);

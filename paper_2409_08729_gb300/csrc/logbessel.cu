@@ -312,7 +312,9 @@ __global__ void lb_math_kernel(int which, const double* __restrict__ in, double*
       case 7: r = ix_exp(a); break;
       case 8: r = ix_log(a); break;
       case 9: r = ix_rcp(a); break;
-      default: r = ix_rsqrt(a); break;
+      case 10: r = ix_rsqrt(a); break;
+      case 11: r = __longlong_as_double(ix_log_q53(a)); break;          // the Q53 integer's bits
+      default: r = __longlong_as_double((long long)ix_exp_q58_fx(__double_as_longlong(a))); break;
     }
     out[i] = r;
   }
@@ -733,7 +735,7 @@ lb_status logbessel_vmf_log_c(lb_dtype dtype, double d, const void* kappa, void*
 }
 
 lb_status logbessel_math_eval(int which, const double* in, double* out, int64_t n, void* cuda_stream) {
-  if (which < 0 || which > 10) return fail(LB_EINVAL, "which must be 0..10 (got %s%lld)", "", (long long)which);
+  if (which < 0 || which > 12) return fail(LB_EINVAL, "which must be 0..12 (got %s%lld)", "", (long long)which);
   if (n < 0 || (n > 0 && (!in || !out))) return fail(LB_EINVAL, "bad buffer or size %s%lld", "", (long long)n);
   if (n == 0) return LB_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;

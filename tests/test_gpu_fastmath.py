@@ -103,3 +103,18 @@ def test_integer_pipe_rcp_rsqrt_bit_exact(cuda):
                         [1.0, 2.0, 0.5, 3.0, 1e-300, 1e300, 2.0 ** 1023, 0.0, np.inf]])
     np.testing.assert_array_equal(_eval(9, z, cuda), ix_rcp(z))
     np.testing.assert_array_equal(_eval(10, z, cuda), ix_rsqrt(z))
+
+
+def test_fixed_point_node_functions_bit_equal_to_host(cuda):
+    """The Q53 log and the Q58 exponential of a Q53 shift (the K integral's
+    node functions) give the same bits on the GPU as in the host build that
+    tests/test_intmath.py checks against exact references."""
+    from intmath_host import ix_exp_q58_fx, ix_log_q53
+    rng = np.random.default_rng(12)
+    z = np.concatenate([np.exp(rng.uniform(-700, 700, 3000)), rng.uniform(1e-3, 200.0, 3000),
+                        1.0 + np.arange(512) / 512.0, [0.0, -1.0, 5e-324, np.inf, np.nan]])
+    got = _eval(11, z, cuda).view(np.int64)
+    assert np.array_equal(got, ix_log_q53(z))
+    d = np.concatenate([-rng.integers(0, 42 * 2 ** 53, 5000, dtype=np.int64), np.array([0, -1, -(2 ** 62)], dtype=np.int64)])
+    got = _eval(12, d.view(np.float64), cuda).view(np.uint64)
+    assert np.array_equal(got, ix_exp_q58_fx(d))
