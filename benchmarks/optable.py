@@ -94,11 +94,13 @@ def series_terms(v, x, eps=1.4e-17):
     return n
 
 
-def kint_nodes(v, x, one_slot=True):
+def kint_nodes(v, x, one_slot=True, low_slot=True):
     """g and h nodes of the tight K-integral rule of each pair (values; |v|
     given).  The split g rule (v < 0.4, x < 1e-3) has 64 + 32 + 32 nodes,
     plus 32 more below x ~ 4e-21; 1.2 < v <= 5 takes 24 g + 40 h nodes;
-    2 <= v <= 16.5 the one-slot rules, 22 + 10 (v < 7) or 12 + 20."""
+    2 <= v <= 16.5 the one-slot rules, 22 + 10 (v < 7) or 12 + 20, and
+    0.9 <= v < 2 with x >= 0.8 the one-slot rule of 24 + 8 nodes (FP64 only:
+    low_slot False for the FP32 form)."""
     v = np.asarray(v, dtype=np.float64)
     x = np.asarray(x, dtype=np.float64)
     split = np.where(np.log(128 * np.maximum(x, 1e-320)) + 40 < -4, 160, 128)
@@ -109,6 +111,8 @@ def kint_nodes(v, x, one_slot=True):
     one = (v >= 2.0) & (v <= 16.5) & one_slot
     ng = np.where(one, np.where(v < 7.0, 22, 12), ng)
     nh = np.where(one, np.where(v < 7.0, 10, 20), nh)
+    low = (v >= 0.9) & (v < 2.0) & (x >= 0.8) & one_slot & low_slot
+    ng, nh = np.where(low, 24, ng), np.where(low, 8, nh)
     return ng, nh
 
 
@@ -131,7 +135,7 @@ def region_ops(region, v, x, shared=False, fp32=False):
 def kint_ops(v, x, shared=False, fp32=False):
     """Operations per pair of the K integral (Gauss rules; the FP32 form takes
     the same rules, in single precision)."""
-    ng, nh = kint_nodes(v, x)
+    ng, nh = kint_nodes(v, x, low_slot=not fp32)
     return ng * (7 if shared else 8) + nh * 6 + (10 if shared else 11)
 
 

@@ -18,11 +18,13 @@ N = 600.  These tables hold Gauss rules for the same two pieces instead:
   h piece: Gauss-Legendre in y = log s on [0, log 100] (s in [1, 100]),
            32, 40 or 48 nodes, for orders v <= 5;
            Gauss-Laguerre in t = s - 1, 32 nodes, for orders v > 5.
-  one-slot rules (values, 2 <= v <= 16.5): the split moved from s = 1 to
-           s0, so that the branch point s = 0 of (s (s + 2x))^(v-1/2) lies
-           s0 away from the Gauss-Laguerre nodes of [s0, inf) (t = s - s0);
-           [0, s0] with s = s0 u^beta and Gauss-Legendre in u.  s0 = 8 with
-           22 + 10 nodes (2 <= v < 7), s0 = 3 with 12 + 20 (7 <= v <= 16.5).
+  one-slot rules (2 <= v <= 16.5, and 0.9 <= v < 2 for x >= 0.8): the
+           split moved from s = 1 to s0, so that the branch point s = 0 of
+           (s (s + 2x))^(v-1/2) lies s0 away from the Gauss-Laguerre nodes
+           of [s0, inf) (t = s - s0); [0, s0] with s = s0 u^beta and
+           Gauss-Legendre in u.  s0 = 8 with 22 + 10 nodes (2 <= v < 7),
+           s0 = 3 with 12 + 20 (7 <= v <= 16.5); s0 = 10 with 24 + 8 and
+           n = 6 (beta = 12/(2v+1), 0.9 <= v < 2, x >= 0.8).
 
 Writes kquad_tables.h beside this file.  Nodes and weights are computed in
 40-digit arithmetic and rounded to double.  The log terms that the values'
@@ -100,6 +102,10 @@ def main():
         parts.append("// log w_j + (n - 1) log u_j with n = 8 (the u^(n-1) factor of g folded in)")
         parts.append(arr("lb_kq_g%d_c" % N, [mp.log(b) + 7 * mp.log(a) for a, b in zip(u, w)]))
         parts.append(arrq("lb_kq_g%d_c" % N, [mp.log(b) + 7 * mp.log(a) for a, b in zip(u, w)]))
+        if N == 24:
+            parts.append("// the same with n = 6 (the one-slot rule with s0 = 10)")
+            parts.append(arr("lb_kq_g24n6_c", [mp.log(b) + 5 * mp.log(a) for a, b in zip(u, w)]))
+            parts.append(arrq("lb_kq_g24n6_c", [mp.log(b) + 5 * mp.log(a) for a, b in zip(u, w)]))
     for N in (16, 32):
         t, w = gauss_legendre01(N)
         parts.append("// plain Gauss-Legendre on [0,1], %d nodes: t_j and log w_j (panels placed per pair)" % N)
@@ -123,7 +129,7 @@ def main():
     parts.append(arr("lb_kq_hq32_c", [mp.log(a) - 1 for a in lam]))
     parts.append(arrq("lb_kq_hq32_y", [mp.log(1 + a) for a in t]))
     parts.append(arrq("lb_kq_hq32_c", [mp.log(a) - 1 for a in lam]))
-    for N, s0 in ((10, 8), (20, 3)):
+    for N, s0 in ((10, 8), (20, 3), (8, 10)):
         t, lam = gauss_laguerre(N)
         tag = "hq%do%d" % (N, s0)
         parts.append("// one-slot rule: Gauss-Laguerre in t = s - %d, %d nodes: %d + t_j, log(%d + t_j), log(lambda_j) - %d"
@@ -133,11 +139,11 @@ def main():
         parts.append(arr("lb_kq_%s_c" % tag, [mp.log(a) - s0 for a in lam]))
         parts.append(arrq("lb_kq_%s_y" % tag, [mp.log(s0 + a) for a in t]))
         parts.append(arrq("lb_kq_%s_c" % tag, [mp.log(a) - s0 for a in lam]))
-    parts.append("// log 8 and log 3, the split points of the one-slot rules")
-    parts.append("#define LB_KQ_LOG8 %r" % float(mp.log(8)))
-    parts.append("#define LB_KQ_LOG3 %r" % float(mp.log(3)))
-    parts.append("#define LB_KQ_LOG8_Q53 %dll" % int(mp.nint(mp.log(8) * mp.mpf(2) ** 53)))
-    parts.append("#define LB_KQ_LOG3_Q53 %dll" % int(mp.nint(mp.log(3) * mp.mpf(2) ** 53)))
+    parts.append("// log 8, log 3 and log 10, the split points of the one-slot rules")
+    for s0 in (8, 3, 10):
+        parts.append("#define LB_KQ_LOG%d %r" % (s0, float(mp.log(s0))))
+    for s0 in (8, 3, 10):
+        parts.append("#define LB_KQ_LOG%d_Q53 %dll" % (s0, int(mp.nint(mp.log(s0) * mp.mpf(2) ** 53))))
     with open(out, "w") as f:
         f.write("\n".join(parts) + "\n")
 

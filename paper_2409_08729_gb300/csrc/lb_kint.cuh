@@ -60,12 +60,13 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
 // g rule 24 goes with h rule 3 (40 nodes in log s): for 1.2 < v <= 5 the
 // 24 + 40 nodes fill two 32-lane slots (the 32 + 48 of the general rule take
 // three), error map below 4e-17 over x in [1e-300, 30].
-// h rules 4 and 5 are the one-slot rules of kint_sum_one (22 g + 10 h
-// nodes, s0 = 8, for 2 <= v < 7; 12 + 20, s0 = 3, for 7 <= v <= 16.5), for
-// values and x-derivatives: their error maps (30-digit sums of the double
-// tables against the oracle) stay below 1.5e-17 of the error scale for
-// log K and below 1.1e-16 relative (the reference's own rounding) for
-// d/dx log K over x in [1e-300, 30].
+// h rules 4, 5 and 6 are the one-slot rules of kint_sum_one (22 g + 10 h
+// nodes, s0 = 8, for 2 <= v < 7; 12 + 20, s0 = 3, for 7 <= v <= 16.5;
+// 24 + 8, s0 = 10 and n = 6 (beta = 12/(2v+1)), for 0.9 <= v < 2 and
+// x >= 0.8), for values and x-derivatives: their error maps (30-digit sums
+// of the double tables against the oracle) stay below 1.5e-17 of the error
+// scale for log K (over x in [1e-300, 30]; [0.8, 30] for rule 6) and below
+// 1.1e-16 relative (the reference's own rounding) for d/dx log K.
 // The x-derivative, a weighted mean of 1/(s + 2x) over the nodes, moves both
 // boundaries up for v < 0.1: 64 g nodes up to x = 0.6 and the split rule up
 // to x = 5e-3.  There the 32-node rule leaves up to 7e-15 relative error in
@@ -75,6 +76,7 @@ __device__ __forceinline__ double kint_prefactor(double v, double x) {
 // (v, x >= 0: the compares run on the bit patterns, integer instructions.)
 __device__ __forceinline__ int kint_rule(double v, double x, bool dx) {
   if (LB_GE(v, 2.0) && LB_LE(v, 16.5)) return LB_LT(v, 7.0) ? (22 | (4 << 8)) : (12 | (5 << 8));
+  if (LB_GE(v, 0.9) && LB_LT(v, 2.0) && LB_GE(x, 0.8)) return 24 | (6 << 8);
   if (LB_GT(v, 1.2) && LB_LE(v, 5.0)) return 24 | (3 << 8);
   const bool dsmall = dx && LB_LT(v, 0.1);
   const double x32 = dsmall ? 0.6 : 0.25, xsplit = dsmall ? 5e-3 : 1e-3;
@@ -84,13 +86,13 @@ __device__ __forceinline__ int kint_rule(double v, double x, bool dx) {
 }
 
 // Code path of a pair's rule, for sorting pairs by rule: 0 the split rule,
-// 1 and 2 the one-slot rules, 3 the packed rule, 4 and 5 the fixed rules
-// with 32 and 64 g nodes.
+// 1 the one-slot rules with s0 = 8 and s0 = 10, 2 the one-slot rule with
+// s0 = 3, 3 the packed rule, 4 and 5 the fixed rules with 32 and 64 g nodes.
 __device__ __forceinline__ int kint_class(double v, double x, bool dx) {
   const int rule = kint_rule(v, x, dx);
   const int ng = rule & 0xff, hr = rule >> 8;
   if (ng == 0) return 0;
-  if (hr >= 4) return hr - 3;
+  if (hr >= 4) return hr == 5 ? 2 : 1;
   return ng == 24 ? 3 : (ng == 32 ? 4 : 5);
 }
 
@@ -100,8 +102,8 @@ __device__ __forceinline__ int kint_class(double v, double x, bool dx) {
 // operations as the per-pair path: the results do not change).
 struct KintScalar {
   double ub24[24], ub32[32], ub64[64];
-  double sg[22];                                   // s0 u_j^beta of the one-slot rule of v (if any)
-  long long ubq24[24], ubq32[32], ubq64[64], sgq[22];   // the same in Q53 (values' fixed-point terms)
+  double sg[24];                                   // s0 u_j^beta of the one-slot rule of v (if any)
+  long long ubq24[24], ubq32[32], ubq64[64], sgq[24];   // the same in Q53 (values' fixed-point terms)
   double pre;                                      // log(sqrt(pi)) - lgamma(v + 1/2)
 };
 
@@ -120,11 +122,15 @@ __device__ __forceinline__ void kint_scalar_setup(KintScalar& ks, double v) {
     ks.ubq64[tid - 56] = ix_fix(ks.ub64[tid - 56], 53);
   } else if (tid == 120) {
     ks.pre = kHalfLogPi - lgamma(v + 0.5);
-  } else if (tid >= 128 && tid < 150 && v >= 2.0 && v <= 16.5) {
+  } else if (tid >= 128 && tid < 152) {
     const int j = tid - 128;
-    if (v < 7.0) ks.sg[j] = ix_exp(fma(beta, __ldg(lb_kq_g22_logu + j), LB_KQ_LOG8));
-    else if (j < 12) ks.sg[j] = ix_exp(fma(beta, __ldg(lb_kq_g12_logu + j), LB_KQ_LOG3));
-    if (v < 7.0 || j < 12) ks.sgq[j] = ix_fix(ks.sg[j], 53);
+    bool set = true;
+    if (v >= 2.0 && v <= 16.5 && v < 7.0 && j < 22) ks.sg[j] = ix_exp(fma(beta, __ldg(lb_kq_g22_logu + j), LB_KQ_LOG8));
+    else if (v >= 7.0 && v <= 16.5 && j < 12) ks.sg[j] = ix_exp(fma(beta, __ldg(lb_kq_g12_logu + j), LB_KQ_LOG3));
+    else if (v >= 0.9 && v < 2.0)                  // the rule with n = 6 (beta = 12/(2v+1))
+      ks.sg[j] = ix_exp(fma(0.75 * beta, __ldg(lb_kq_g24_logu + j), LB_KQ_LOG10));
+    else set = false;
+    if (set) ks.sgq[j] = ix_fix(ks.sg[j], 53);
   }
   __syncthreads();
 }
@@ -348,14 +354,20 @@ template <bool FX, bool W = false>
 __device__ __forceinline__ uint64_t kint_sum_one(const KqPair& p, int hr, int lane, typename KqLog<FX>::type& mm,
                                                  const KintScalar* ks, double* w1 = nullptr) {
   typedef typename KqLog<FX>::type LT;
-  const bool r4 = hr == 4;
-  const int ng = r4 ? 22 : 12;
-  const KqNode n = lane < ng ? kq_g<FX>(p, __ldg((r4 ? lb_kq_g22_logu : lb_kq_g12_logu) + lane),
-                                        r4 ? LB_KQ_LOG8 : LB_KQ_LOG3, ks ? ks->sg : nullptr, ks ? ks->sgq : nullptr,
-                                        lane, r4 ? lb_kq_g22_c : lb_kq_g12_c, r4 ? lb_kq_g22_c_q : lb_kq_g12_c_q)
-                             : kq_h<FX>(p, r4 ? lb_kq_hq10o8_s : lb_kq_hq20o3_s, r4 ? lb_kq_hq10o8_y : lb_kq_hq20o3_y,
-                                        r4 ? lb_kq_hq10o8_y_q : lb_kq_hq20o3_y_q, r4 ? lb_kq_hq10o8_c : lb_kq_hq20o3_c,
-                                        r4 ? lb_kq_hq10o8_c_q : lb_kq_hq20o3_c_q, lane - ng);
+  const bool r4 = hr == 4, r6 = hr == 6;
+  const int ng = r4 ? 22 : (r6 ? 24 : 12);
+  const double* gu = r4 ? lb_kq_g22_logu : (r6 ? lb_kq_g24_logu : lb_kq_g12_logu);
+  const double* gc = r4 ? lb_kq_g22_c : (r6 ? lb_kq_g24n6_c : lb_kq_g12_c);
+  const long long* gcq = r4 ? lb_kq_g22_c_q : (r6 ? lb_kq_g24n6_c_q : lb_kq_g12_c_q);
+  const double ls0 = r4 ? LB_KQ_LOG8 : (r6 ? LB_KQ_LOG10 : LB_KQ_LOG3);
+  const double* hs = r4 ? lb_kq_hq10o8_s : (r6 ? lb_kq_hq8o10_s : lb_kq_hq20o3_s);
+  const double* hy = r4 ? lb_kq_hq10o8_y : (r6 ? lb_kq_hq8o10_y : lb_kq_hq20o3_y);
+  const long long* hyq = r4 ? lb_kq_hq10o8_y_q : (r6 ? lb_kq_hq8o10_y_q : lb_kq_hq20o3_y_q);
+  const double* hc = r4 ? lb_kq_hq10o8_c : (r6 ? lb_kq_hq8o10_c : lb_kq_hq20o3_c);
+  const long long* hcq = r4 ? lb_kq_hq10o8_c_q : (r6 ? lb_kq_hq8o10_c_q : lb_kq_hq20o3_c_q);
+  const KqNode n = lane < ng ? kq_g<FX>(p, __ldg(gu + lane), ls0, ks ? ks->sg : nullptr, ks ? ks->sgq : nullptr,
+                                        lane, gc, gcq)
+                             : kq_h<FX>(p, hs, hy, hyq, hc, hcq, lane - ng);
   const LT L = kq_eval<FX>(p, n);
   mm = kq_max<FX>(kq_key<FX>(L));
   const uint64_t t = kq_exp<FX>(L, mm);
@@ -567,8 +579,9 @@ __device__ __forceinline__ void kint_sums_split(double v, double x, double beta,
 template <bool DX, int CLS = -1>
 __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npairs, int lane,
                                                    const KintScalar* ks = nullptr) {
-  const double beta_i = 16.0 * ix_rcp(2.0 * vi + 1.0);   // the reciprocal on the integer pipe
   const int rule_i = kint_rule(vi, xi, DX);
+  // beta = 2n/(2v+1): n = 8, or 6 for the one-slot rule of 0.9 <= v < 2
+  const double beta_i = ((rule_i >> 8) == 6 ? 12.0 : 16.0) * ix_rcp(2.0 * vi + 1.0);   // reciprocal on the integer pipe
   // values: the g nodes' common factor as a log, log beta (plus
   // (v + 1/2) log s0 = (v - 1/2) log s0 + log s0 for the one-slot rules),
   // added to their log terms; in the fixed-point domain (v <= 16.5, x <= 32)
@@ -582,13 +595,13 @@ __device__ __forceinline__ double kint_batch_gauss(double vi, double xi, int npa
       vmq_i = ix_fix(vi - 0.5, 58);
       gkq_i = ix_log_q53(beta_i);
       if (hr_i >= 4) {
-        const long long ls0 = hr_i == 4 ? LB_KQ_LOG8_Q53 : LB_KQ_LOG3_Q53;
+        const long long ls0 = hr_i == 4 ? LB_KQ_LOG8_Q53 : (hr_i == 6 ? LB_KQ_LOG10_Q53 : LB_KQ_LOG3_Q53);
         gkq_i += ix_mul_q58(vmq_i, ls0) + ls0;
       }
     } else {
       vm_i = vi - 0.5;
       gk_i = ix_log(beta_i);
-      if (hr_i >= 4) gk_i = fma(vi + 0.5, hr_i == 4 ? LB_KQ_LOG8 : LB_KQ_LOG3, gk_i);
+      if (hr_i >= 4) gk_i = fma(vi + 0.5, hr_i == 4 ? LB_KQ_LOG8 : (hr_i == 6 ? LB_KQ_LOG10 : LB_KQ_LOG3), gk_i);
     }
   }
   const double tx_i = 2.0 * xi;
