@@ -44,7 +44,8 @@ NCU_PIPES = {
                         "launch": "log I, mixed orders, 11M pairs"},
     "lb_kint_kernel": {"fp64": 0.355, "alu": 0.635, "fma": 0.193, "xu": 0.015, "issue_active": 0.662,
                        "launch": "one-slot class kernel of a mixed-order log K call (class 4: fp64 0.257, "
-                                 "alu 0.611, issue 0.634); FMA-heavy pipe (integer multiplies) 0.48"},
+                                 "alu 0.611, issue 0.634); FMA-heavy pipe (integer multiplies) 0.48; captured "
+                                 "before the one-slot rule for orders 0.9-2 was added"},
 }
 NCU_PIPES_FP32 = {
     "lb_tiles_kernel": {"fp64": 0.0, "alu": 0.450, "fma": 0.235, "xu": 0.111, "issue_active": 0.760,
